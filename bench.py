@@ -1,0 +1,415 @@
+"""Benchmark of the GPU join path.
+
+Default workload: the large equi-join, R = S = 2^28 rows of (int32 key,
+int32 payload = row id), keys Zipf(theta) over 2^28 values (theta = 0 by
+default), run as the pre-filtered, radix-partitioned hash join with the exact
+count pass and one exact output allocation.  A step is one full jn_hash call
+(pre-filter, two partition passes, count pass, scan, allocation, emit).
+
+Prints one JSON line.  `value` = (|R| + |S| + M) / time per step, in
+tuples/s ("join tuples/s in+out"), with the inputs already in device memory.
+`e2e` repeats the step through the C ABI with host buffers: the library
+copies the host columns in and the pairs out inside the timed region.
+
+Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+                       [--workload hash|hash_int64|band|nlj] [--theta T]
+Under torchrun (N > 1) every rank runs its own replica of the workload
+(the join does not shard without a collective); value sums all ranks.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import torch  # noqa: E402
+
+PEAKS_FALLBACK = {"hbm_gbs": 6800.0}
+
+
+def peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
+            p = json.load(fh)
+        return p, "measured"
+    except Exception:
+        return PEAKS_FALLBACK, "fallback"
+
+
+# ------------------------------------------------------------- workloads --
+
+def make_workload(name, theta, device, small=False):
+    from paper_1904_11201_gb300 import datagen as D
+    if name in ("hash", "hash_int64"):
+        i64 = name == "hash_int64"
+        n = (1 << 27) if i64 else (1 << 28)
+        if small:
+            n = 1 << 20
+        dbits = 28 if not small else 20
+        dt = torch.int64 if i64 else torch.int32
+        cdf = None
+        if theta != 0:
+            cdf = D.zipf_cdf(theta, 1 << dbits, device)
+        r = D.zipf_keys(n, theta, dbits, seed=0, stream=0, device=device, dtype=dt, cdf=cdf)
+        s = D.zipf_keys(n, theta, dbits, seed=0, stream=1, device=device, dtype=dt, cdf=cdf)
+        del cdf
+        return {"kind": "hash", "R": (r, None, D.row_ids(n, device)), "S": (s, None, D.row_ids(n, device)),
+                "config": {"workload": "equi hash join %dM x %dM %s keys, Zipf theta=%g over 2^%d"
+                           % (n >> 20, n >> 20, "int64" if i64 else "int32", theta, dbits),
+                           "R_rows": n, "S_rows": n, "key": "int64" if i64 else "int32",
+                           "zipf_theta": theta, "key_domain": 1 << dbits, "payload": "int32 row id",
+                           "algo": "jn_hash (pre-filter, 2-pass radix partition, count, emit)"}}
+    if name == "band":
+        nr, ns = (1 << 20, 1 << 24) if not small else (1 << 16, 1 << 20)
+        ra, rk = D.band_columns(nr, 24, seed=0, stream=0, device=device)
+        sa, sk = D.band_columns(ns, 24, seed=0, stream=1, device=device)
+        return {"kind": "band", "band": 95, "op": 2,
+                "R": (ra, rk, D.row_ids(nr, device)), "S": (sa, sk, D.row_ids(ns, device)),
+                "config": {"workload": "band join R.a < S.a and |R.k - S.k| <= 95, 1M x 16M int32",
+                           "R_rows": nr, "S_rows": ns, "key": "int32", "band": 95,
+                           "algo": "jn_theta(op <, band 95)"}}
+    if name == "nlj":
+        nr, ns = 1 << 14, 1 << 16
+        r = D.uniform_keys(nr, 0, 65536, seed=0, stream=0, device=device)
+        s = D.uniform_keys(ns, 0, 65536, seed=0, stream=1, device=device)
+        return {"kind": "nlj", "R": (r, None, D.row_ids(nr, device)), "S": (s, None, D.row_ids(ns, device)),
+                "config": {"workload": "equi nested-loop join 16K x 64K int32 uniform [0, 65536)",
+                           "R_rows": nr, "S_rows": ns, "key": "int32", "algo": "jn_nested_loop"}}
+    raise ValueError(name)
+
+
+def run_step(jn, ctx, w, R, S, out=None):
+    if w["kind"] == "hash":
+        return jn.jn_hash(ctx, R, S, out=out)
+    if w["kind"] == "band":
+        return jn.jn_theta(ctx, R, S, w["op"], w["band"], out=out)
+    return jn.jn_nested_loop(ctx, R, S, out=out)
+
+
+# ------------------------------------------------------------ roofline --
+
+def algorithmic_bytes(kind, info, nr, ns, m, ksize):
+    """Algorithmic bytes per kernel for one step (measurement)."""
+    sr, ss = info["r_survivors"], info["s_survivors"]
+    surv = sr + ss
+    row = ksize + 4
+    if kind == "hash":
+        return {
+            "presence": ksize * (nr + ns),
+            "scatter": row * (nr + ns) + row * surv + 2 * row * surv,
+            "histogram": ksize * surv,
+            "hash_count": row * surv,
+            "hash_emit": row * surv + 8 * m,
+        }
+    if kind == "band":
+        return {
+            "minmax": 4 * (nr + ns),
+            "histogram": 4 * (nr + ns),
+            "scatter": 2 * 12 * (nr + ns),
+            "theta_count": 12 * (nr + ns),
+            "theta_emit": 12 * (nr + ns) + 8 * m,
+        }
+    return {}
+
+
+class ClockSampler:
+    FIELDS = "index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active," \
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown," \
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap"
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), "--query-gpu=" + self.FIELDS,
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except Exception:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if not self.proc:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        mhz, mx, reasons = [], None, set()
+        for ln in self.lines:
+            f = [x.strip() for x in ln.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                mhz.append(float(f[1]))
+                mx = float(f[2])
+            except ValueError:
+                continue
+            for name, v in zip(["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"],
+                               f[5:9]):
+                if v.lower() == "active":
+                    reasons.add(name)
+        if not mhz:
+            return None
+        mhz.sort()
+        return {"sm_mhz": mhz[len(mhz) // 2], "sm_max_mhz": mx, "reasons": sorted(reasons),
+                "samples": len(mhz)}
+
+
+# ------------------------------------------------------------ cpu baseline --
+
+def cpu_baseline(kind, budget_s=12.0):
+    """The CPU oracle timed on a bounded sample of the same workload shape."""
+    import numpy as np
+    import oracle as O
+    from paper_1904_11201_gb300 import datagen as D
+    if kind == "hash":
+        n = 1 << 22
+        r = D.uniform_keys(n, 0, n, seed=0, stream=0).numpy()
+        s = D.uniform_keys(n, 0, n, seed=0, stream=1).numpy()
+        rp = np.arange(n, dtype=np.int32)
+        t0 = time.perf_counter()
+        reps, units = 0, 0
+        while True:
+            m = O.hash_join(r, s, rp, rp, count_only=False).shape[0]
+            reps += 1
+            units += 2 * n + m
+            if time.perf_counter() - t0 > budget_s or reps >= 8:
+                break
+        dt = time.perf_counter() - t0
+        return {"value": units / dt, "unit": "tuples/s", "cores": 1, "kind": "oracle",
+                "sample": "chained hash join (oracle O2), R = S = 2^22 rows, uniform keys over 2^22 "
+                          "(same rows-per-key density as the 2^28 workload), %d run(s), %.1f s" % (reps, dt)}
+    if kind == "band":
+        nr, ns = 1 << 16, 1 << 20
+        ra, rk = D.band_columns(nr, 20, seed=0, stream=0)
+        sa, sk = D.band_columns(ns, 20, seed=0, stream=1)
+        t0 = time.perf_counter()
+        m = O.band_join_sorted(ra.numpy(), rk.numpy(), sa.numpy(), sk.numpy(), O.LT, 95).shape[0]
+        dt = time.perf_counter() - t0
+        return {"value": (nr + ns + m) / dt, "unit": "tuples/s", "cores": 1, "kind": "oracle",
+                "sample": "sorted band join (oracle O4), 64K x 1M over 2^20 with w = 95, %.1f s" % dt}
+    r = D.uniform_keys(4096, 0, 65536, seed=0, stream=0).numpy()
+    s = D.uniform_keys(65536, 0, 65536, seed=0, stream=1).numpy()
+    t0 = time.perf_counter()
+    m = O.nested_loop(r, s, count_only=False).shape[0]
+    dt = time.perf_counter() - t0
+    return {"value": (r.shape[0] + s.shape[0] + m) / dt, "unit": "tuples/s", "cores": 1, "kind": "oracle",
+            "sample": "nested loop (oracle O1), 4K x 64K, %.1f s" % dt}
+
+
+# ------------------------------------------------------------------ main --
+
+def dist_setup(args):
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        import torch.distributed as dist
+        backend = "nccl" if torch.cuda.is_available() else "gloo"
+        dist.init_process_group(backend, init_method="env://")
+    return world, rank, local
+
+
+def barrier(world):
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def max_over_ranks(x, world, dev):
+    if world <= 1:
+        return x
+    import torch.distributed as dist
+    t = torch.tensor([x], dtype=torch.float64, device=dev)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def reference_arm(args, world, rank):
+    """The oracle, as it stands, on the host cores: each step a bounded sample."""
+    if rank != 0:
+        return
+    kind = {"hash": "hash", "hash_int64": "hash", "band": "band", "nlj": "nlj"}[args.workload]
+    import oracle as O  # noqa: F401
+    for _ in range(args.warmup):
+        cpu_baseline(kind, budget_s=0.0)
+    t0 = time.perf_counter()
+    vals = []
+    for _ in range(args.steps):
+        vals.append(cpu_baseline(kind, budget_s=0.0))
+    dt = time.perf_counter() - t0
+    v = sum(x["value"] for x in vals) / len(vals)
+    cb = dict(vals[0])
+    cb["value"] = v
+    w = {"hash": "equi hash join 256M x 256M int32 keys, Zipf theta=%g over 2^28" % args.theta,
+         "band": "band join R.a < S.a and |R.k - S.k| <= 95, 1M x 16M int32",
+         "nlj": "equi nested-loop join 16K x 64K int32 uniform [0, 65536)"}[kind]
+    print(json.dumps({"impl": "reference", "metric": "join tuples/s in+out", "value": v, "unit": "tuples/s",
+                      "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+                      "ms_per_step": 1000.0 * dt / max(args.steps, 1), "higher_is_better": True,
+                      "scaling": "weak", "vs_baseline": None, "dtype": "int32", "data": "synthetic",
+                      "config": {"workload": w, "sample": cb["sample"]},
+                      "cpu_baseline": cb,
+                      "e2e": {"value": v, "unit": "tuples/s", "h2d_bytes_per_step": 0,
+                              "d2h_bytes_per_step": 0}}), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="jn")
+    ap.add_argument("--workload", default="hash")
+    ap.add_argument("--theta", type=float, default=0.0)
+    ap.add_argument("--small", action="store_true", help="small inputs (profiling runs)")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu", action="store_true")
+    args = ap.parse_args()
+    world, rank, local = dist_setup(args)
+    if args.impl == "reference":
+        reference_arm(args, world, rank)
+        return
+    args.warmup = max(args.warmup, 3) if not args.small else args.warmup
+
+    from paper_1904_11201_gb300 import build as B
+    from paper_1904_11201_gb300 import jn
+    if rank == 0 or world == 1:
+        B.build()
+    barrier(world)
+    torch.cuda.set_device(local)
+    dev = "cuda:%d" % local
+    stream = torch.cuda.current_stream(local)
+    ctx = jn.Context(local, stream)
+    w = make_workload(args.workload, args.theta, dev, args.small)
+    (rk, rk2, rp), (sk, sk2, sp) = w["R"], w["S"]
+    R = jn.table(rk, rk2, rp)
+    S = jn.table(sk, sk2, sp)
+    nr, ns = rk.shape[0], sk.shape[0]
+    ksize = rk.element_size()
+    torch.cuda.synchronize()
+
+    for _ in range(args.warmup):
+        out = run_step(jn, ctx, w, R, S)
+        m = out.shape[0]
+        del out
+    info = ctx.run_info()
+
+    ctx.reset_stats()
+    ctx.set_profiling(True)
+    l0 = ctx.launch_count()
+    clk = ClockSampler(local)
+    clk.start()
+    barrier(world)
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(args.steps):
+        out = run_step(jn, ctx, w, R, S)
+        del out
+    e1.record(stream)
+    torch.cuda.synchronize()
+    barrier(world)
+    clocks = clk.stop()
+    launches = ctx.launch_count() - l0
+    ms = e0.elapsed_time(e1) / args.steps
+    ms = max_over_ranks(ms, world, dev)
+    stats = ctx.kernel_stats()
+    ctx.set_profiling(False)
+
+    units = nr + ns + m
+    value = world * units / (ms * 1e-3)
+    pk, pk_kind = peaks()
+    hbm = pk.get("hbm_gbs", 6800.0)
+    abytes = algorithmic_bytes(w["kind"], info, nr, ns, m, ksize)
+    kern = {}
+    for name, (cnt, tms) in stats.items():
+        per_launch = tms / max(cnt, 1)
+        kern[name] = {"launches_per_step": cnt / args.steps, "ms_per_step": tms / args.steps,
+                      "share": 0.0}
+        if name in abytes:
+            gbs = abytes[name] / (tms / args.steps * 1e-3) / 1e9 if tms > 0 else 0.0
+            kern[name]["algorithmic_gb_per_step"] = abytes[name] / 1e9
+            kern[name]["achieved_gbs"] = gbs
+        kern[name]["avg_launch_ms"] = per_launch
+    tot = sum(v["ms_per_step"] for v in kern.values()) or 1.0
+    for v in kern.values():
+        v["share"] = v["ms_per_step"] / tot
+    dom = max((k for k in kern if k in abytes), key=lambda k: kern[k]["ms_per_step"], default=None)
+    roof = None
+    if dom:
+        a = kern[dom]["achieved_gbs"]
+        roof = {"bound": "hbm", "kernel": dom, "achieved": a, "peak": hbm, "unit": "GB/s",
+                "frac": a / hbm, "peak_kind": pk_kind + " (copy bandwidth, MEASURED_PEAKS.json hbm_gbs)",
+                "traffic": None,
+                "algorithmic_bytes_per_launch": abytes[dom] / max(kern[dom]["launches_per_step"], 1)}
+    floor = None
+    if w["kind"] in ("hash", "band"):
+        fb = 24 * (nr + ns) + 8 * m
+        floor = {"bytes": fb, "frac_of_hbm_peak": fb / (ms * 1e-3) / (hbm * 1e9)}
+
+    # ---- end to end: host columns in, host pairs out, through the C ABI ----
+    e2e = None
+    if not args.no_e2e:
+        hr = tuple(None if t is None else t.cpu().pin_memory() for t in w["R"])
+        hs = tuple(None if t is None else t.cpu().pin_memory() for t in w["S"])
+        HR, HS = jn.table(*hr), jn.table(*hs)
+        hout = torch.empty((m, 2), dtype=torch.int32).pin_memory()
+        run_step(jn, ctx, w, HR, HS, out=hout)  # warm-up of the staging path
+        torch.cuda.synchronize()
+        barrier(world)
+        t0 = time.perf_counter()
+        for _ in range(max(1, min(args.steps, 3))):
+            got = run_step(jn, ctx, w, HR, HS, out=hout)
+        torch.cuda.synchronize()
+        te = (time.perf_counter() - t0) / max(1, min(args.steps, 3))
+        te = max_over_ranks(te, world, dev)
+        hb = sum(t.numel() * t.element_size() for t in hr + hs if t is not None)
+        e2e = {"value": world * units / te, "unit": "tuples/s", "h2d_bytes_per_step": hb,
+               "d2h_bytes_per_step": 8 * m, "ms_per_step": te * 1e3}
+        del got, hout, hr, hs
+
+    cb = None
+    if rank == 0 and world == 1 and not args.no_cpu:
+        cb = cpu_baseline(w["kind"])
+    if rank == 0:
+        line = {"metric": "join tuples/s in+out", "value": value, "unit": "tuples/s", "n_gpus": world,
+                "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
+                "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "int32",
+                "data": "synthetic",
+                "config": dict(w["config"], l2="inputs larger than L2 (no flush needed)"
+                               if (nr + ns) * (ksize + 4) > (129 << 20) else "inputs fit in L2",
+                               parallelism="replicas" if world > 1 else "1 GPU"),
+                "input_tuples_per_s": world * (nr + ns) / (ms * 1e-3),
+                "output_tuples_per_s": world * m / (ms * 1e-3),
+                "result_pairs": m, "join_floor": floor, "roofline": roof, "cpu_baseline": cb,
+                "e2e": e2e, "clocks": clocks, "gpu_launches": launches,
+                "run_info": {k: int(v) for k, v in info.items()}, "kernels": kern}
+        print(json.dumps(line), flush=True)
+    ctx.close()
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

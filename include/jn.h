@@ -1,0 +1,219 @@
+/*
+ * jn.h -- GPU joins over integer key columns (GB300, sm_103a).
+ *
+ * C ABI of libjn.so.  It follows the paper's statement of the problem
+ * (H. Wang et al., "GPU-based Efficient Join Algorithms on Hadoop",
+ * arXiv 1904.11201):
+ *   - a table arrives as column buffers in one row order, and a match of row
+ *     m of R with row n of S yields the pair (m, n) -- here (payload_R[m],
+ *     payload_S[n]) -- (Sec. 3.2.2, row and column transformation);
+ *   - the GPU entry points take the two tables and their sizes, as
+ *     Join_GPU(T', S', NB_T, NB_S) of Algorithm 1 and GPU_theta_join(S, T) of
+ *     Algorithm 3 do;
+ *   - the output is sized exactly by a count pass before it is written, in
+ *     place of the Cartesian-product bound of Eq. (rsize) (Sec. 3.3.3).
+ * R is the build side (the paper's T, "the smaller table", Sec. 2.3) and S the
+ * probe side.
+ *
+ * General rules for every entry point:
+ *   - Errors are returned as jn_status; nothing throws or aborts.  A CUDA
+ *     error maps to JN_ERR_CUDA and jn_last_error() gives its text.
+ *   - Column pointers may be device memory or host memory (pinned or
+ *     pageable).  Host columns are copied to device scratch owned by the
+ *     context before the join; device columns are read in place.  The caller
+ *     keeps every column valid and unchanged until the call returns.
+ *   - All work runs on the context's stream, in stream order.  Calls that
+ *     size an output (jn_count, jn_aggregate and the three joins) read the
+ *     8-byte count back to the host and therefore synchronise that stream.
+ *   - A context is used by one host thread at a time.
+ *   - Row counts are limited to 2^31 - 1 per table (JN_ERR_INVALID beyond).
+ *   - Output order is unspecified; the multiset of pairs is exact.
+ */
+#ifndef JN_H
+#define JN_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    JN_OK = 0,
+    JN_ERR_INVALID = 1,      /* bad argument: NULL pointer, key type mismatch, n out of range */
+    JN_ERR_OOM = 2,          /* device allocation failed */
+    JN_ERR_CAPACITY = 3,     /* caller buffer too small: *n_out = required pairs, nothing written */
+    JN_ERR_CUDA = 4,         /* a CUDA call failed (see jn_last_error) */
+    JN_ERR_TIMEOUT = 5,      /* a bounded device-side wait ran out */
+    JN_ERR_UNSUPPORTED = 6   /* predicate or mode not implemented for this algorithm */
+} jn_status;
+
+typedef enum { JN_KEY_I32 = 4, JN_KEY_I64 = 8 } jn_key_type;
+
+/* R.col op S.col.  Sec. 2.3 names =, >, <, >=, <= "and so on"; Sec. 4.2's
+ * region figure adds !=.  JN_ANY is the always-true predicate. */
+typedef enum {
+    JN_EQ = 0, JN_NE = 1, JN_LT = 2, JN_LE = 3, JN_GT = 4, JN_GE = 5, JN_ANY = 6
+} jn_op;
+
+typedef enum { JN_ALGO_NLJ = 0, JN_ALGO_HASH = 1, JN_ALGO_THETA = 2 } jn_algo;
+
+/* One table as column buffers (Sec. 3.2.2).  Signed integers; all key columns
+ * of one call share key_type. */
+typedef struct {
+    const void* key;          /* n values: the join column (theta: column a)            */
+    const void* key2;         /* n values: second compared column (band: column k), or NULL */
+    const int32_t* payload;   /* n int32 values emitted in the pairs, or NULL = row index */
+    int64_t n;                /* rows, 0 .. 2^31-1                                       */
+    int32_t key_type;         /* JN_KEY_I32 or JN_KEY_I64                                */
+    int32_t reserved;         /* must be 0                                               */
+} jn_table;
+
+/* One result: (R.payload[m], S.payload[n]); (m, n) when payloads are NULL. */
+typedef struct {
+    int32_t r;
+    int32_t s;
+} jn_pair;
+
+/* Two-column conjunctive predicate:
+ *     (R.key op_a S.key) AND (band >= 0 ? |R.key2 - S.key2| <= band
+ *                                       : R.key2 op_k S.key2)
+ * The second conjunct is dropped (true) when either key2 is NULL.  |R.key2 -
+ * S.key2| is evaluated exactly (no overflow).  NULL pred = equality on key. */
+typedef struct {
+    int32_t op_a;
+    int32_t op_k;
+    int64_t band;
+} jn_pred;
+
+/* Tuning knobs; 0 (or -1 where noted) lets the library choose.  The result
+ * never depends on them. */
+typedef struct {
+    int32_t prefilter;     /* -1 auto, 0 off, 1 on: Algorithm 1's common-key filter     */
+    int32_t radix_bits;    /* total partition bits of the hash join (0 = auto, <= 16)   */
+    int32_t radix_bits1;   /* bits of the first partition pass (0 = auto)               */
+    int32_t filter_bits;   /* log2 of the key-presence bitmap size (0 = auto, <= 30)    */
+    int32_t heavy;         /* -1 auto, 0 off, 1 on: frequent keys joined as cross products */
+    int32_t theta_groups;  /* log2 of the theta/band group count (0 = auto, <= 10)      */
+    int32_t nlj_tile_r;    /* R rows per nested-loop tile (0 = auto; multiple of 256)   */
+    int32_t reserved[9];
+} jn_tuning;
+
+/* Per-kernel launch statistics (profiling mode). */
+typedef struct {
+    char name[32];
+    uint64_t launches;
+    double ms;             /* summed device time between CUDA events around each launch */
+} jn_kernel_stat;
+
+/* What the last join on a context did (for benchmarks and tests). */
+typedef struct {
+    uint64_t result;            /* pairs produced (or counted)                      */
+    uint64_t r_survivors;       /* R rows kept by the pre-filter (all when off)     */
+    uint64_t s_survivors;
+    uint64_t partitions;        /* partitions / groups / tiles of the join phase    */
+    uint64_t work_items;        /* count/emit work items                            */
+    uint64_t heavy_keys;        /* keys routed to the cross-product path            */
+    uint64_t kernel_launches;   /* kernels launched by the call                     */
+    int32_t prefilter;          /* 1 if the pre-filter ran                          */
+    int32_t radix_bits;
+    int32_t radix_bits1;
+    int32_t filter_bits;
+    uint64_t reserved[6];
+} jn_run_info;
+
+typedef struct jn_ctx jn_ctx;
+
+/* ------------------------------------------------------------ context --- */
+
+/* Create a context on CUDA device `device` issuing work on `stream` (a
+ * cudaStream_t; NULL = the legacy default stream).  The context owns its
+ * scratch memory and a device memory pool for outputs. */
+jn_status jn_create(jn_ctx** ctx, int device, void* stream);
+void jn_destroy(jn_ctx* ctx);
+jn_status jn_set_stream(jn_ctx* ctx, void* stream);
+jn_status jn_set_tuning(jn_ctx* ctx, const jn_tuning* t);   /* NULL = defaults */
+jn_status jn_get_tuning(const jn_ctx* ctx, jn_tuning* t);
+const char* jn_status_str(jn_status s);
+const char* jn_last_error(const jn_ctx* ctx);               /* text of the last failure */
+const char* jn_version(void);
+
+/* ------------------------------------------------------------ joins --- */
+
+/* Exact result size of a join without writing pairs (the count pass that
+ * replaces Eq. (rsize)'s estimate, Sec. 3.3.3).
+ *   algo JN_ALGO_HASH : equality on key (pred must be NULL or op_a = JN_EQ
+ *                       with no second conjunct);
+ *   algo JN_ALGO_NLJ  : any jn_pred;
+ *   algo JN_ALGO_THETA: pred->op_a on key, and, when pred->band >= 0, the band
+ *                       on key2 (the jn_theta predicate).
+ * *count (host) receives the number of pairs. */
+jn_status jn_count(jn_ctx* ctx, int32_t algo, const jn_table* R, const jn_table* S,
+                   const jn_pred* pred, uint64_t* count);
+
+/* As jn_count, and also the separable checksum of the result multiset:
+ *   checksum = sum over result pairs (r, s) of f(r) * g(s) mod 2^64,
+ *   f(x) = mix(0x243F6A8885A308D3 ^ (uint32)x), g(x) = mix(0x13198A2E03707344 ^ (uint32)x),
+ *   mix = the SplitMix64 output mixer.
+ * This is the "results not stored" mode of Sec. 5.3 for outputs too large to
+ * materialise.  checksum may be NULL. */
+jn_status jn_aggregate(jn_ctx* ctx, int32_t algo, const jn_table* R, const jn_table* S,
+                       const jn_pred* pred, uint64_t* count, uint64_t* checksum);
+
+/* Output convention of the three joins:
+ *   *out == NULL : the library allocates exactly *n_out pairs of device memory
+ *                  (one allocation, after the count pass) and stores the
+ *                  pointer in *out; release it with jn_free.  capacity is ignored.
+ *   *out != NULL : a caller buffer of `capacity` pairs, device or host memory.
+ *                  If the result has more pairs than capacity the call returns
+ *                  JN_ERR_CAPACITY with *n_out = the required count and writes
+ *                  nothing.  A host buffer is filled by a copy before return.
+ * *n_out (host) receives the number of pairs written. */
+
+/* Nested-loop join (Sec. 3.3.1): every (R, S) pair is tested with `pred`
+ * (NULL = equality on key).  Tiles of R are staged in shared memory and
+ * compared against S rows held in registers. */
+jn_status jn_nested_loop(jn_ctx* ctx, const jn_table* R, const jn_table* S, const jn_pred* pred,
+                         jn_pair** out, uint64_t capacity, uint64_t* n_out);
+
+/* Equi hash join (Sec. 3.3.2) with Algorithm 1's pre-filter (Sec. 3.1):
+ * key-presence filters of both tables drop tuples whose key is absent from
+ * the other table, a two-pass radix partition replaces the Map-Reduce
+ * shuffle on key/alpha, and each partition is joined through a
+ * shared-memory hash table built on its R rows. */
+jn_status jn_hash(jn_ctx* ctx, const jn_table* R, const jn_table* S,
+                  jn_pair** out, uint64_t capacity, uint64_t* n_out);
+
+/* Theta join (Sec. 4.2, Algorithm 3).
+ *   band < 0 : predicate R.key op S.key.  Both tables are cut into ranges with
+ *              shared boundaries; off-diagonal regions whose ranges already
+ *              decide the predicate are emitted as cross products without
+ *              comparisons, diagonal regions are compared pair by pair, the
+ *              rest are skipped.
+ *   band >= 0: predicate (R.key op S.key) AND |R.key2 - S.key2| <= band.  The
+ *              ranges are cut on key2; only region pairs within the band are
+ *              compared.
+ * Both tables need key2 when band >= 0. */
+jn_status jn_theta(jn_ctx* ctx, const jn_table* R, const jn_table* S, int32_t op, int64_t band,
+                   jn_pair** out, uint64_t capacity, uint64_t* n_out);
+
+/* Release an output allocated by a join (stream ordered on the context's
+ * stream; with ctx == NULL, on the legacy default stream, so results may
+ * outlive their context). */
+void jn_free(jn_ctx* ctx, jn_pair* p);
+
+/* ------------------------------------------------------- introspection --- */
+
+jn_status jn_set_profiling(jn_ctx* ctx, int32_t on);  /* CUDA events around each launch */
+/* Copies up to max entries (kernels with at least one launch) into out; *n =
+ * entries written.  Synchronises the stream to resolve pending events. */
+jn_status jn_kernel_stats(jn_ctx* ctx, jn_kernel_stat* out, int32_t max, int32_t* n);
+jn_status jn_reset_stats(jn_ctx* ctx);
+jn_status jn_last_run_info(const jn_ctx* ctx, jn_run_info* info);
+uint64_t jn_launch_count(const jn_ctx* ctx);           /* kernels launched since creation */
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* JN_H */

@@ -1,0 +1,51 @@
+// Internal entry points of the join algorithms (device-resident columns).
+#pragma once
+
+#include "jn_common.cuh"
+
+namespace jnx {
+
+enum RunMode { MODE_COUNT = 0, MODE_AGG = 1, MODE_EMIT = 2 };
+
+// One table with every column already in device memory.
+template <typename K>
+struct Cols {
+    const K* key;
+    const K* key2;
+    const int32_t* pay;  // NULL = row index
+    int64_t n;
+};
+
+// Where the pairs of an emitting run go (see jn.h's output convention).
+struct OutPlan {
+    jn_pair** user_out = nullptr;
+    uint64_t capacity = 0;
+    uint64_t* n_out = nullptr;
+    jn_pair* dev = nullptr;      // device buffer the kernels write
+    bool host_copy = false;      // caller buffer is host memory
+    bool lib_alloc = false;      // library allocated the result
+};
+
+// Sizes the output for `m` pairs (allocating or checking the caller buffer).
+jn_status out_prepare(jn_ctx* c, Scratch& s, uint64_t m, OutPlan& plan);
+// Copies to a host buffer when needed and publishes the result.
+jn_status out_finish(jn_ctx* c, uint64_t m, OutPlan& plan);
+
+struct RunResult {
+    uint64_t count = 0;
+    uint64_t checksum = 0;
+};
+
+template <typename K>
+jn_status run_hash(jn_ctx* c, const Cols<K>& R, const Cols<K>& S, int mode, OutPlan* plan,
+                   RunResult* res);
+
+template <typename K>
+jn_status run_nlj(jn_ctx* c, const Cols<K>& R, const Cols<K>& S, const jn_pred& pred, int mode,
+                  OutPlan* plan, RunResult* res);
+
+template <typename K>
+jn_status run_theta(jn_ctx* c, const Cols<K>& R, const Cols<K>& S, int op, int64_t band, int mode,
+                    OutPlan* plan, RunResult* res);
+
+}  // namespace jnx

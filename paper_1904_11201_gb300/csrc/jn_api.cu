@@ -1,0 +1,166 @@
+// extern "C" entry points of libjn: argument checks, host-column staging,
+// dispatch on key type, and the output convention of jn.h.
+#include <string.h>
+
+#include "jn_algos.h"
+
+namespace jnx {
+
+jn_status out_prepare(jn_ctx* c, Scratch& s, uint64_t m, OutPlan& plan) {
+    jn_pair* user = *plan.user_out;
+    plan.host_copy = false;
+    plan.lib_alloc = false;
+    if (user == nullptr) {
+        plan.lib_alloc = true;
+        plan.dev = nullptr;
+        if (m > 0) {
+            void* p = nullptr;
+            JN_TRY(dalloc(c, &p, m * sizeof(jn_pair)));
+            plan.dev = static_cast<jn_pair*>(p);
+        }
+        return JN_OK;
+    }
+    if (m > plan.capacity) {
+        *plan.n_out = m;
+        return fail(c, JN_ERR_CAPACITY, "output buffer holds fewer pairs than the result");
+    }
+    if (m == 0 || is_device_pointer(user)) {
+        plan.dev = user;
+        return JN_OK;
+    }
+    plan.host_copy = true;
+    return s.get(&plan.dev, m);
+}
+
+jn_status out_finish(jn_ctx* c, uint64_t m, OutPlan& plan) {
+    if (plan.host_copy && m > 0) {
+        JN_CUDA(c, cudaMemcpyAsync(*plan.user_out, plan.dev, m * sizeof(jn_pair), cudaMemcpyDeviceToHost,
+                                   c->stream));
+        JN_CUDA(c, cudaStreamSynchronize(c->stream));
+    }
+    if (plan.lib_alloc) *plan.user_out = plan.dev;
+    *plan.n_out = m;
+    return JN_OK;
+}
+
+static jn_status check_table(jn_ctx* c, const jn_table* t, const char* name, bool need_key2) {
+    if (!t) return fail(c, JN_ERR_INVALID, std::string(name) + ": NULL table");
+    if (t->key_type != JN_KEY_I32 && t->key_type != JN_KEY_I64)
+        return fail(c, JN_ERR_INVALID, std::string(name) + ": key_type must be JN_KEY_I32 or JN_KEY_I64");
+    if (t->n < 0 || t->n > INT32_MAX)
+        return fail(c, JN_ERR_INVALID, std::string(name) + ": row count out of range");
+    if (t->reserved != 0) return fail(c, JN_ERR_INVALID, std::string(name) + ": reserved must be 0");
+    if (t->n > 0 && t->key == nullptr) return fail(c, JN_ERR_INVALID, std::string(name) + ": NULL key");
+    if (need_key2 && t->n > 0 && t->key2 == nullptr)
+        return fail(c, JN_ERR_INVALID, std::string(name) + ": key2 required");
+    return JN_OK;
+}
+
+static bool valid_op(int op) { return op >= JN_EQ && op <= JN_ANY; }
+
+template <typename K>
+static jn_status stage(jn_ctx* c, Scratch& s, const jn_table* t, bool use_key2, Cols<K>* out) {
+    const size_t kb = (size_t)t->n * sizeof(K);
+    const void *k = nullptr, *k2 = nullptr, *p = nullptr;
+    JN_TRY(device_column(c, s, t->key, kb, &k));
+    if (use_key2 && t->key2) JN_TRY(device_column(c, s, t->key2, kb, &k2));
+    if (t->payload) JN_TRY(device_column(c, s, t->payload, (size_t)t->n * 4, &p));
+    out->key = static_cast<const K*>(k);
+    out->key2 = static_cast<const K*>(k2);
+    out->pay = static_cast<const int32_t*>(p);
+    out->n = t->n;
+    return JN_OK;
+}
+
+template <typename K>
+static jn_status dispatch(jn_ctx* c, int algo, const jn_table* R, const jn_table* S, const jn_pred& pr,
+                          int mode, OutPlan* plan, RunResult* res) {
+    Scratch s(c);
+    Cols<K> r, q;
+    const bool use2 = algo != JN_ALGO_HASH;
+    JN_TRY(stage<K>(c, s, R, use2, &r));
+    JN_TRY(stage<K>(c, s, S, use2, &q));
+    switch (algo) {
+        case JN_ALGO_HASH: return run_hash<K>(c, r, q, mode, plan, res);
+        case JN_ALGO_NLJ: return run_nlj<K>(c, r, q, pr, mode, plan, res);
+        case JN_ALGO_THETA: return run_theta<K>(c, r, q, pr.op_a, pr.band, mode, plan, res);
+    }
+    return fail(c, JN_ERR_INVALID, "unknown algorithm");
+}
+
+static jn_status run(jn_ctx* c, int algo, const jn_table* R, const jn_table* S, const jn_pred* pred,
+                     int mode, jn_pair** out, uint64_t capacity, uint64_t* n_out, uint64_t* count,
+                     uint64_t* checksum) {
+    if (!c) return JN_ERR_INVALID;
+    c->err.clear();
+    jn_pred pr;
+    pr.op_a = JN_EQ;
+    pr.op_k = JN_ANY;
+    pr.band = -1;
+    if (pred) pr = *pred;
+    if (!valid_op(pr.op_a) || !valid_op(pr.op_k)) return fail(c, JN_ERR_INVALID, "unknown predicate op");
+    if (algo == JN_ALGO_HASH) {
+        const bool second = pred && (pr.band >= 0 || pr.op_k != JN_ANY);
+        if (pr.op_a != JN_EQ || second)
+            return fail(c, JN_ERR_UNSUPPORTED, "the hash join takes the equality predicate only");
+    }
+    const bool need2 = algo == JN_ALGO_THETA && pr.band >= 0;
+    JN_TRY(check_table(c, R, "R", need2));
+    JN_TRY(check_table(c, S, "S", need2));
+    if (R->key_type != S->key_type) return fail(c, JN_ERR_INVALID, "R and S key types differ");
+    if (mode == MODE_EMIT && (!out || !n_out)) return fail(c, JN_ERR_INVALID, "NULL output pointer");
+    if (mode != MODE_EMIT && !count) return fail(c, JN_ERR_INVALID, "NULL count pointer");
+    JN_CUDA(c, cudaSetDevice(c->device));
+    c->info = jn_run_info();
+    const uint64_t l0 = c->launches_total;
+    OutPlan plan;
+    plan.user_out = out;
+    plan.capacity = capacity;
+    plan.n_out = n_out;
+    RunResult res;
+    jn_status st = (R->key_type == JN_KEY_I32)
+                       ? dispatch<int32_t>(c, algo, R, S, pr, mode, &plan, &res)
+                       : dispatch<int64_t>(c, algo, R, S, pr, mode, &plan, &res);
+    c->info.kernel_launches = c->launches_total - l0;
+    if (st != JN_OK) return st;
+    if (count) *count = res.count;
+    if (checksum) *checksum = res.checksum;
+    return JN_OK;
+}
+
+}  // namespace jnx
+
+using namespace jnx;
+
+extern "C" {
+
+jn_status jn_count(jn_ctx* ctx, int32_t algo, const jn_table* R, const jn_table* S, const jn_pred* pred,
+                   uint64_t* count) {
+    return run(ctx, algo, R, S, pred, MODE_COUNT, nullptr, 0, nullptr, count, nullptr);
+}
+
+jn_status jn_aggregate(jn_ctx* ctx, int32_t algo, const jn_table* R, const jn_table* S,
+                       const jn_pred* pred, uint64_t* count, uint64_t* checksum) {
+    return run(ctx, algo, R, S, pred, MODE_AGG, nullptr, 0, nullptr, count, checksum);
+}
+
+jn_status jn_nested_loop(jn_ctx* ctx, const jn_table* R, const jn_table* S, const jn_pred* pred,
+                         jn_pair** out, uint64_t capacity, uint64_t* n_out) {
+    return run(ctx, JN_ALGO_NLJ, R, S, pred, MODE_EMIT, out, capacity, n_out, nullptr, nullptr);
+}
+
+jn_status jn_hash(jn_ctx* ctx, const jn_table* R, const jn_table* S, jn_pair** out, uint64_t capacity,
+                  uint64_t* n_out) {
+    return run(ctx, JN_ALGO_HASH, R, S, nullptr, MODE_EMIT, out, capacity, n_out, nullptr, nullptr);
+}
+
+jn_status jn_theta(jn_ctx* ctx, const jn_table* R, const jn_table* S, int32_t op, int64_t band,
+                   jn_pair** out, uint64_t capacity, uint64_t* n_out) {
+    jn_pred p;
+    p.op_a = op;
+    p.op_k = JN_ANY;
+    p.band = band;
+    return run(ctx, JN_ALGO_THETA, R, S, &p, MODE_EMIT, out, capacity, n_out, nullptr, nullptr);
+}
+
+}  // extern "C"

@@ -1,0 +1,351 @@
+// libjn runtime: contexts, errors, memory, scans, statistics.
+#include <stdio.h>
+#include <string.h>
+
+#include <algorithm>
+#include <mutex>
+#include <set>
+
+#include "jn_common.cuh"
+
+namespace jnx {
+
+static const char* kKernelNames[K_COUNT_IDS] = {
+    "memset",       "presence",     "histogram",   "scatter",     "segments",
+    "work_items",   "hash_count",   "hash_emit",   "heavy_sample", "heavy_select",
+    "cross_emit",   "scan_reduce",  "scan_top",    "scan_down",   "nlj_count",
+    "nlj_emit",     "minmax",       "theta_count", "theta_emit",  "gather",
+    "batch",        "misc"};
+
+const char* kernel_name(int kid) {
+    return (kid >= 0 && kid < K_COUNT_IDS) ? kKernelNames[kid] : "?";
+}
+
+jn_status fail(jn_ctx* c, jn_status s, const std::string& msg) {
+    if (c) c->err = msg;
+    return s;
+}
+
+jn_status cuda_fail(jn_ctx* c, cudaError_t e, const char* what) {
+    char buf[512];
+    snprintf(buf, sizeof(buf), "%s: %s (%s)", what, cudaGetErrorName(e), cudaGetErrorString(e));
+    if (e == cudaErrorMemoryAllocation) {
+        cudaGetLastError();  // not sticky: clear it
+        return fail(c, JN_ERR_OOM, buf);
+    }
+    return fail(c, JN_ERR_CUDA, buf);
+}
+
+jn_status dalloc(jn_ctx* c, void** p, size_t bytes) {
+    cudaError_t e = cudaMallocFromPoolAsync(p, bytes, c->pool, c->stream);
+    if (e != cudaSuccess) {
+        *p = nullptr;
+        return cuda_fail(c, e, "device allocation");
+    }
+    return JN_OK;
+}
+
+void dfree(jn_ctx* c, void* p) {
+    if (p) cudaFreeAsync(p, c->stream);
+}
+
+jn_status zero(jn_ctx* c, void* p, size_t bytes) {
+    if (bytes == 0) return JN_OK;
+    JN_CUDA(c, cudaMemsetAsync(p, 0, bytes, c->stream));
+    return JN_OK;
+}
+
+cudaEvent_t take_event(jn_ctx* c) {
+    if (!c->spare_events.empty()) {
+        cudaEvent_t e = c->spare_events.back();
+        c->spare_events.pop_back();
+        return e;
+    }
+    cudaEvent_t e = nullptr;
+    cudaEventCreate(&e);
+    return e;
+}
+
+void ensure_smem(const void* fn, size_t smem) {
+    static std::mutex mu;
+    static std::set<std::pair<const void*, size_t>> done;
+    std::lock_guard<std::mutex> g(mu);
+    auto key = std::make_pair(fn, smem);
+    if (done.count(key)) return;
+    cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    done.insert(key);
+}
+
+jn_status read_back(jn_ctx* c, const uint64_t* dsrc, uint64_t* hdst, int n) {
+    JN_CUDA(c, cudaMemcpyAsync(c->h_small, dsrc, sizeof(uint64_t) * n, cudaMemcpyDeviceToHost,
+                               c->stream));
+    JN_CUDA(c, cudaStreamSynchronize(c->stream));
+    for (int i = 0; i < n; i++) hdst[i] = c->h_small[i];
+    return JN_OK;
+}
+
+bool is_device_pointer(const void* p) {
+    cudaPointerAttributes a;
+    cudaError_t e = cudaPointerGetAttributes(&a, p);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+}
+
+jn_status device_column(jn_ctx* c, Scratch& s, const void* p, size_t bytes, const void** dp) {
+    if (p == nullptr || bytes == 0 || is_device_pointer(p)) {
+        *dp = p;
+        return JN_OK;
+    }
+    uint8_t* d = nullptr;
+    JN_TRY(s.get(&d, bytes));
+    JN_CUDA(c, cudaMemcpyAsync(d, p, bytes, cudaMemcpyHostToDevice, c->stream));
+    *dp = d;
+    return JN_OK;
+}
+
+// ------------------------------------------------------------------ scan --
+// Three-phase exclusive scan: per-block sums, one block scanning the sums,
+// then each block scanning its chunk from its carry.  4096 values per block.
+constexpr int SCAN_T = 1024;
+constexpr int SCAN_V = 4;
+constexpr int SCAN_CHUNK = SCAN_T * SCAN_V;
+
+template <typename T>
+__global__ void k_scan_reduce(const T* __restrict__ in, int64_t n, uint64_t* __restrict__ sums) {
+    __shared__ uint64_t tmp[33];
+    int64_t base = (int64_t)blockIdx.x * SCAN_CHUNK;
+    uint64_t v = 0;
+#pragma unroll
+    for (int j = 0; j < SCAN_V; j++) {
+        int64_t i = base + (int64_t)threadIdx.x * SCAN_V + j;
+        if (i < n) v += (uint64_t)in[i];
+    }
+    uint64_t t = block_sum(v, tmp);
+    if (threadIdx.x == 0) sums[blockIdx.x] = t;
+}
+
+// One block scans in[0..n) with a running carry; out[n] = total.  With
+// `carry_in` != nullptr, each block's carry comes from carry_in[blockIdx.x]
+// (the down-sweep over chunks of SCAN_CHUNK).
+template <typename T>
+__global__ void k_scan_chunks(const T* __restrict__ in, int64_t n, uint64_t* __restrict__ out,
+                              const uint64_t* __restrict__ carry_in) {
+    __shared__ uint64_t tmp[33];
+    uint64_t carry = carry_in ? carry_in[blockIdx.x] : 0;
+    int64_t begin = carry_in ? (int64_t)blockIdx.x * SCAN_CHUNK : 0;
+    int64_t end = carry_in ? min(n, begin + SCAN_CHUNK) : n;
+    for (int64_t base = begin; base < end; base += SCAN_CHUNK) {
+        uint64_t v[SCAN_V];
+        uint64_t local = 0;
+#pragma unroll
+        for (int j = 0; j < SCAN_V; j++) {
+            int64_t i = base + (int64_t)threadIdx.x * SCAN_V + j;
+            v[j] = (i < end) ? (uint64_t)in[i] : 0;
+            local += v[j];
+        }
+        uint64_t total;
+        uint64_t pre = block_excl_scan(local, tmp, &total) + carry;
+#pragma unroll
+        for (int j = 0; j < SCAN_V; j++) {
+            int64_t i = base + (int64_t)threadIdx.x * SCAN_V + j;
+            if (i < end) out[i] = pre;
+            pre += v[j];
+        }
+        carry += total;
+    }
+    if (threadIdx.x == 0 && end == n) out[n] = carry;
+}
+
+template <typename T>
+static jn_status scan_impl(jn_ctx* c, const T* in, uint64_t* out, int64_t n) {
+    if (n <= 8 * SCAN_CHUNK) {
+        return launch(c, K_SCAN_TOP, k_scan_chunks<T>, dim3(1), dim3(SCAN_T), 0, in, n, out,
+                      (const uint64_t*)nullptr);
+    }
+    int64_t nb = (int64_t)ceil_div(n, SCAN_CHUNK);
+    Scratch s(c);
+    uint64_t *sums = nullptr, *pre = nullptr;
+    JN_TRY(s.get(&sums, nb));
+    JN_TRY(s.get(&pre, nb + 1));
+    JN_TRY(launch(c, K_SCAN_REDUCE, k_scan_reduce<T>, dim3((unsigned)nb), dim3(SCAN_T), 0, in, n,
+                  sums));
+    JN_TRY(scan_impl<uint64_t>(c, sums, pre, nb));
+    JN_TRY(launch(c, K_SCAN_DOWN, k_scan_chunks<T>, dim3((unsigned)nb), dim3(SCAN_T), 0, in, n,
+                  out, (const uint64_t*)pre));
+    return JN_OK;
+}
+
+jn_status scan_u32(jn_ctx* c, const uint32_t* in, uint64_t* out, int64_t n) {
+    return scan_impl<uint32_t>(c, in, out, n);
+}
+jn_status scan_u64(jn_ctx* c, const uint64_t* in, uint64_t* out, int64_t n) {
+    return scan_impl<uint64_t>(c, in, out, n);
+}
+
+static void resolve_pending(jn_ctx* c) {
+    for (auto& p : c->pending) {
+        float ms = 0.f;
+        if (cudaEventElapsedTime(&ms, p.start, p.stop) == cudaSuccess) c->stats[p.kid].ms += ms;
+        c->spare_events.push_back(p.start);
+        c->spare_events.push_back(p.stop);
+    }
+    c->pending.clear();
+    cudaGetLastError();
+}
+
+}  // namespace jnx
+
+using namespace jnx;
+
+extern "C" {
+
+const char* jn_version(void) { return "jn 0.1 (sm_103a)"; }
+
+const char* jn_status_str(jn_status s) {
+    switch (s) {
+        case JN_OK: return "ok";
+        case JN_ERR_INVALID: return "invalid argument";
+        case JN_ERR_OOM: return "out of device memory";
+        case JN_ERR_CAPACITY: return "output buffer too small";
+        case JN_ERR_CUDA: return "CUDA error";
+        case JN_ERR_TIMEOUT: return "device wait timed out";
+        case JN_ERR_UNSUPPORTED: return "unsupported predicate or mode";
+    }
+    return "unknown status";
+}
+
+const char* jn_last_error(const jn_ctx* ctx) { return ctx ? ctx->err.c_str() : "no context"; }
+
+static void default_tuning(jn_tuning* t) {
+    memset(t, 0, sizeof(*t));
+    t->prefilter = -1;
+    t->heavy = -1;
+}
+
+jn_status jn_create(jn_ctx** out, int device, void* stream) {
+    if (!out) return JN_ERR_INVALID;
+    *out = nullptr;
+    int ndev = 0;
+    if (cudaGetDeviceCount(&ndev) != cudaSuccess || device < 0 || device >= ndev) {
+        cudaGetLastError();
+        return JN_ERR_INVALID;
+    }
+    jn_ctx* c = new jn_ctx();
+    c->device = device;
+    c->stream = (cudaStream_t)stream;
+    default_tuning(&c->tune);
+    cudaError_t e = cudaSetDevice(device);
+    if (e == cudaSuccess) {
+        cudaDeviceProp prop;
+        e = cudaGetDeviceProperties(&prop, device);
+        c->num_sms = prop.multiProcessorCount;
+        c->smem_optin = prop.sharedMemPerBlockOptin;
+    }
+    if (e == cudaSuccess) {
+        cudaMemPoolProps props;
+        memset(&props, 0, sizeof(props));
+        props.allocType = cudaMemAllocationTypePinned;
+        props.handleTypes = cudaMemHandleTypeNone;
+        props.location.type = cudaMemLocationTypeDevice;
+        props.location.id = device;
+        e = cudaMemPoolCreate(&c->pool, &props);
+    }
+    if (e == cudaSuccess) {
+        uint64_t keep = UINT64_MAX;  // keep freed blocks for reuse by later calls
+        e = cudaMemPoolSetAttribute(c->pool, cudaMemPoolAttrReleaseThreshold, &keep);
+    }
+    if (e == cudaSuccess) e = cudaMallocHost((void**)&c->h_small, 64 * sizeof(uint64_t));
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        if (c->pool) cudaMemPoolDestroy(c->pool);
+        delete c;
+        return JN_ERR_CUDA;
+    }
+    *out = c;
+    return JN_OK;
+}
+
+void jn_destroy(jn_ctx* c) {
+    if (!c) return;
+    cudaStreamSynchronize(c->stream);
+    resolve_pending(c);
+    for (cudaEvent_t e : c->spare_events) cudaEventDestroy(e);
+    if (c->h_small) cudaFreeHost(c->h_small);
+    if (c->pool) cudaMemPoolDestroy(c->pool);
+    cudaGetLastError();
+    delete c;
+}
+
+jn_status jn_set_stream(jn_ctx* c, void* stream) {
+    if (!c) return JN_ERR_INVALID;
+    c->stream = (cudaStream_t)stream;
+    return JN_OK;
+}
+
+jn_status jn_set_tuning(jn_ctx* c, const jn_tuning* t) {
+    if (!c) return JN_ERR_INVALID;
+    if (!t) {
+        default_tuning(&c->tune);
+        return JN_OK;
+    }
+    if (t->radix_bits < 0 || t->radix_bits > 16 || t->radix_bits1 < 0 || t->radix_bits1 > 10 ||
+        t->filter_bits < 0 || t->filter_bits > 30 || t->theta_groups < 0 || t->theta_groups > 10 ||
+        t->nlj_tile_r < 0 || (t->nlj_tile_r % 256) != 0 || t->nlj_tile_r > 4096)
+        return fail(c, JN_ERR_INVALID, "tuning value out of range");
+    c->tune = *t;
+    return JN_OK;
+}
+
+jn_status jn_get_tuning(const jn_ctx* c, jn_tuning* t) {
+    if (!c || !t) return JN_ERR_INVALID;
+    *t = c->tune;
+    return JN_OK;
+}
+
+void jn_free(jn_ctx* c, jn_pair* p) {
+    if (p) cudaFreeAsync(p, c ? c->stream : (cudaStream_t)0);
+}
+
+jn_status jn_set_profiling(jn_ctx* c, int32_t on) {
+    if (!c) return JN_ERR_INVALID;
+    c->profiling = on != 0;
+    return JN_OK;
+}
+
+jn_status jn_kernel_stats(jn_ctx* c, jn_kernel_stat* out, int32_t max, int32_t* n) {
+    if (!c || !n || (max > 0 && !out)) return JN_ERR_INVALID;
+    JN_CUDA(c, cudaStreamSynchronize(c->stream));
+    resolve_pending(c);
+    int k = 0;
+    for (int i = 0; i < K_COUNT_IDS && k < max; i++) {
+        if (c->stats[i].launches == 0) continue;
+        memset(&out[k], 0, sizeof(out[k]));
+        strncpy(out[k].name, kernel_name(i), sizeof(out[k].name) - 1);
+        out[k].launches = c->stats[i].launches;
+        out[k].ms = c->stats[i].ms;
+        k++;
+    }
+    *n = k;
+    return JN_OK;
+}
+
+jn_status jn_reset_stats(jn_ctx* c) {
+    if (!c) return JN_ERR_INVALID;
+    JN_CUDA(c, cudaStreamSynchronize(c->stream));
+    resolve_pending(c);
+    for (int i = 0; i < K_COUNT_IDS; i++) c->stats[i] = KernelStat();
+    return JN_OK;
+}
+
+jn_status jn_last_run_info(const jn_ctx* c, jn_run_info* info) {
+    if (!c || !info) return JN_ERR_INVALID;
+    *info = c->info;
+    return JN_OK;
+}
+
+uint64_t jn_launch_count(const jn_ctx* c) { return c ? c->launches_total : 0; }
+
+}  // extern "C"

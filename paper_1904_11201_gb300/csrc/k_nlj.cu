@@ -1,0 +1,189 @@
+// Nested-loop join (Sec. 3.3.1): every (R, S) pair is tested.
+//
+// The paper's grid gives each thread NB_S = |S|/(m x) + 1 rows of S and
+// NB_T = |T|/(n y) + 1 rows of T (Eqs. NBS, NBT, IDS, IDT) and a private
+// result buffer of NB_S * NB_T pairs.  Here a block holds a tile of R rows in
+// shared memory and a tile of S rows in registers (NLJ_SPT per thread), so
+// every R value read from shared memory is compared against NLJ_SPT S rows.
+// The predicate of each S row is turned, once, into an interval test on the
+// R value ("R.x op s" <=> R.x in [lo, hi], possibly negated), which makes the
+// inner loop a subtract and an unsigned compare per column.  A count pass
+// writes one count per tile; an exclusive scan gives each tile its exact
+// output offset (replacing the NB_S * NB_T per-thread buffers); the emit pass
+// repeats the comparisons and writes pairs.
+#include "jn_algos.h"
+
+namespace jnx {
+
+constexpr int NLJ_T = 256;
+constexpr int NLJ_SPT = 4;
+constexpr int NLJ_STILE = NLJ_T * NLJ_SPT;
+
+template <typename K, bool HAS2, int MODE>
+__global__ void __launch_bounds__(NLJ_T)
+k_nlj(const K* __restrict__ rk, const K* __restrict__ rk2, const int32_t* __restrict__ rp, int64_t nr,
+      const K* __restrict__ sk, const K* __restrict__ sk2, const int32_t* __restrict__ sp, int64_t ns,
+      int op_a, int op_k, long long band, int tr, unsigned long long* __restrict__ tile_val,
+      unsigned long long* __restrict__ chk, const uint64_t* __restrict__ tile_off,
+      jn_pair* __restrict__ out) {
+    extern __shared__ __align__(16) unsigned char smem[];
+    K* s_a = reinterpret_cast<K*>(smem);
+    K* s_b = s_a + tr;
+    int32_t* s_p = reinterpret_cast<int32_t*>(s_b + (HAS2 ? tr : 0));
+    __shared__ unsigned long long tmp64[33];
+    __shared__ uint32_t s_cur;
+
+    const uint64_t tile = (uint64_t)blockIdx.y * gridDim.x + blockIdx.x;
+    if (MODE == MODE_EMIT) {
+        // tiles without results have nothing to write
+        if (tile_off[tile + 1] == tile_off[tile]) return;
+    }
+    const int64_t r0 = (int64_t)blockIdx.y * tr;
+    const int rn = (int)min((int64_t)tr, nr - r0);
+    for (int i = threadIdx.x; i < rn; i += NLJ_T) {
+        s_a[i] = rk[r0 + i];
+        if (HAS2) s_b[i] = rk2[r0 + i];
+        s_p[i] = rp ? rp[r0 + i] : (int32_t)(r0 + i);
+    }
+    if (threadIdx.x == 0) s_cur = 0;
+
+    Interval<K> ia[NLJ_SPT], ib[NLJ_SPT];
+    int32_t spay[NLJ_SPT];
+    bool valid[NLJ_SPT];
+    const int64_t s0 = (int64_t)blockIdx.x * NLJ_STILE;
+#pragma unroll
+    for (int j = 0; j < NLJ_SPT; j++) {
+        const int64_t s = s0 + j * NLJ_T + threadIdx.x;
+        valid[j] = s < ns;
+        K a = valid[j] ? sk[s] : (K)0;
+        ia[j] = op_interval<K>(valid[j] ? op_a : JN_ANY, a);
+        if (!valid[j]) {  // an empty set: never matches
+            ia[j].inv = true;
+            ia[j].lo = sizeof(K) == 4 ? (K)INT32_MIN : (K)INT64_MIN;
+            ia[j].span = ~(decltype(ia[j].span))0;
+        }
+        if (HAS2) {
+            K b = valid[j] ? sk2[s] : (K)0;
+            ib[j] = band >= 0 ? band_interval<K>(b, band) : op_interval<K>(op_k, b);
+        }
+        spay[j] = valid[j] ? (sp ? sp[s] : (int32_t)s) : 0;
+    }
+    __syncthreads();
+
+    unsigned long long acc = 0, csum = 0;
+    for (int i = 0; i < rn; i++) {
+        const K a = s_a[i];
+        K b = 0;
+        if (HAS2) b = s_b[i];
+#pragma unroll
+        for (int j = 0; j < NLJ_SPT; j++) {
+            bool m = iv_test(ia[j], a);
+            if (HAS2) m = m && iv_test(ib[j], b);
+            if (MODE == MODE_EMIT) {
+                if (m) {
+                    const uint32_t slot = atomicAdd(&s_cur, 1u);
+                    jn_pair q;
+                    q.r = s_p[i];
+                    q.s = spay[j];
+                    out[tile_off[tile] + slot] = q;
+                }
+            } else {
+                acc += m;
+                if (MODE == MODE_AGG && m) csum += chk_f(s_p[i]) * chk_g(spay[j]);
+            }
+        }
+    }
+    if (MODE != MODE_EMIT) {
+        const unsigned long long t = block_sum(acc, tmp64);
+        if (MODE == MODE_AGG) {
+            const unsigned long long c = block_sum(csum, tmp64);
+            if (threadIdx.x == 0 && c) atomicAdd(chk, c);
+        }
+        if (threadIdx.x == 0) tile_val[tile] = t;
+    }
+}
+
+template <typename K, bool HAS2>
+static jn_status nlj_launch(jn_ctx* c, int mode, dim3 grid, size_t smem, const Cols<K>& R,
+                            const Cols<K>& S, const jn_pred& pr, int tr, unsigned long long* val,
+                            unsigned long long* chk, const uint64_t* off, jn_pair* out) {
+    const int kid = mode == MODE_EMIT ? K_NLJ_EMIT : K_NLJ_COUNT;
+    if (mode == MODE_EMIT)
+        return launch(c, kid, k_nlj<K, HAS2, MODE_EMIT>, grid, dim3(NLJ_T), smem, R.key, R.key2, R.pay,
+                      R.n, S.key, S.key2, S.pay, S.n, pr.op_a, pr.op_k, (long long)pr.band, tr, val,
+                      chk, off, out);
+    if (mode == MODE_AGG)
+        return launch(c, kid, k_nlj<K, HAS2, MODE_AGG>, grid, dim3(NLJ_T), smem, R.key, R.key2, R.pay,
+                      R.n, S.key, S.key2, S.pay, S.n, pr.op_a, pr.op_k, (long long)pr.band, tr, val,
+                      chk, off, out);
+    return launch(c, kid, k_nlj<K, HAS2, MODE_COUNT>, grid, dim3(NLJ_T), smem, R.key, R.key2, R.pay,
+                  R.n, S.key, S.key2, S.pay, S.n, pr.op_a, pr.op_k, (long long)pr.band, tr, val, chk,
+                  off, out);
+}
+
+template <typename K>
+jn_status run_nlj(jn_ctx* c, const Cols<K>& R, const Cols<K>& S, const jn_pred& pred, int mode,
+                  OutPlan* plan, RunResult* res) {
+    jn_run_info& info = c->info;
+    if (R.n == 0 || S.n == 0) {
+        res->count = res->checksum = 0;
+        if (mode == MODE_EMIT) {
+            Scratch s0(c);
+            JN_TRY(out_prepare(c, s0, 0, *plan));
+            JN_TRY(out_finish(c, 0, *plan));
+        }
+        return JN_OK;
+    }
+    const bool has2 = R.key2 != nullptr && S.key2 != nullptr;
+    int tr = c->tune.nlj_tile_r ? c->tune.nlj_tile_r : 1024;
+    if (ceil_div(R.n, tr) > 65535)
+        return fail(c, JN_ERR_UNSUPPORTED, "nested loop: R has more than 65535 tiles; use a larger nlj_tile_r");
+    const dim3 grid((unsigned)ceil_div(S.n, NLJ_STILE), (unsigned)ceil_div(R.n, tr));
+    const uint64_t tiles = (uint64_t)grid.x * grid.y;
+    const size_t smem = (size_t)tr * (sizeof(K) * (has2 ? 2 : 1) + 4);
+    Scratch s(c);
+    unsigned long long *val, *chk;
+    uint64_t *off, *d_small;
+    JN_TRY(s.get(&val, tiles));
+    JN_TRY(s.get(&off, tiles + 1));
+    JN_TRY(s.get(&chk, 1));
+    JN_TRY(s.get(&d_small, 2));
+    JN_TRY(zero(c, chk, 8));
+    const int cm = mode == MODE_AGG ? MODE_AGG : MODE_COUNT;
+    if (has2)
+        JN_TRY((nlj_launch<K, true>(c, cm, grid, smem, R, S, pred, tr, val, chk, nullptr, nullptr)));
+    else
+        JN_TRY((nlj_launch<K, false>(c, cm, grid, smem, R, S, pred, tr, val, chk, nullptr, nullptr)));
+    JN_TRY(scan_u64(c, reinterpret_cast<const uint64_t*>(val), off, (int64_t)tiles));
+    JN_CUDA(c, cudaMemcpyAsync(d_small, off + tiles, 8, cudaMemcpyDeviceToDevice, c->stream));
+    JN_CUDA(c, cudaMemcpyAsync(d_small + 1, chk, 8, cudaMemcpyDeviceToDevice, c->stream));
+    uint64_t h[2];
+    JN_TRY(read_back(c, d_small, h, 2));
+    res->count = h[0];
+    res->checksum = h[1];
+    info.result = h[0];
+    info.partitions = tiles;
+    info.work_items = tiles;
+    info.r_survivors = (uint64_t)R.n;
+    info.s_survivors = (uint64_t)S.n;
+    info.prefilter = 0;
+    if (mode != MODE_EMIT) return JN_OK;
+    JN_TRY(out_prepare(c, s, h[0], *plan));
+    if (h[0] > 0) {
+        if (has2)
+            JN_TRY((nlj_launch<K, true>(c, MODE_EMIT, grid, smem, R, S, pred, tr, nullptr, nullptr, off,
+                                        plan->dev)));
+        else
+            JN_TRY((nlj_launch<K, false>(c, MODE_EMIT, grid, smem, R, S, pred, tr, nullptr, nullptr,
+                                         off, plan->dev)));
+    }
+    JN_TRY(out_finish(c, h[0], *plan));
+    return JN_OK;
+}
+
+template jn_status run_nlj<int32_t>(jn_ctx*, const Cols<int32_t>&, const Cols<int32_t>&,
+                                    const jn_pred&, int, OutPlan*, RunResult*);
+template jn_status run_nlj<int64_t>(jn_ctx*, const Cols<int64_t>&, const Cols<int64_t>&,
+                                    const jn_pred&, int, OutPlan*, RunResult*);
+
+}  // namespace jnx

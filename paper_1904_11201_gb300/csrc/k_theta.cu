@@ -1,0 +1,564 @@
+// Theta join after Algorithm 3 (Sec. 4.2), on one GPU.
+//
+// Both tables are cut into ranges ("groups") of one column with the same
+// boundaries for R and S (equal-width, power-of-two wide, from the minimum
+// over both tables), by a one-pass range partition.  A pair of groups
+// (x = R group, y = S group) is a region of the paper's matrix:
+//   - band >= 0 (predicate (R.a op S.a) AND |R.k - S.k| <= band, groups on k):
+//     only regions with |x - y| <= ceil(band / width) can hold results.  For
+//     each S group y the R rows of those groups are contiguous after the
+//     partition (the "window"); they are staged in shared memory, sorted
+//     into fine k-buckets, and each S row scans only the buckets that
+//     intersect [k - band, k + band] before testing both conjuncts exactly.
+//   - band < 0 (predicate R.a op S.a, groups on a): the diagonal region
+//     (x == y) is compared pair by pair (the paper's GPU_theta_join);
+//     regions whose ranges already decide the predicate (x < y for <, <=;
+//     x > y for >, >=; x != y for != and ANY) are written as cross products
+//     without any comparison; the others are skipped.
+// Each work item is (S group, R chunk, S chunk).  Count pass -> scan ->
+// one exact allocation -> emit pass, as in the other joins.
+#include "jn_algos.h"
+#include "jn_partition.cuh"
+
+namespace jnx {
+
+constexpr int TH_T = 256;
+constexpr int TH_RCAP = 4096;   // R rows per shared-memory chunk
+constexpr int TH_SCH = 4096;    // S rows per work item
+constexpr int TH_NFB = 2048;    // fine k-buckets per window
+constexpr uint64_t CE_CHUNK = 1u << 16;  // cross-product pairs per work item
+
+template <typename K>
+__global__ void k_minmax(const K* __restrict__ col, int64_t n, long long* __restrict__ mm) {
+    long long lo = LLONG_MAX, hi = LLONG_MIN;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        long long v = (long long)col[i];
+        lo = v < lo ? v : lo;
+        hi = v > hi ? v : hi;
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        long long a = __shfl_xor_sync(0xffffffffu, lo, o);
+        long long b = __shfl_xor_sync(0xffffffffu, hi, o);
+        lo = a < lo ? a : lo;
+        hi = b > hi ? b : hi;
+    }
+    if ((threadIdx.x & 31) == 0) {
+        atomicMin(&mm[0], lo);
+        atomicMax(&mm[1], hi);
+    }
+}
+
+__global__ void k_mm_init(long long* mm) {
+    mm[0] = LLONG_MAX;
+    mm[1] = LLONG_MIN;
+}
+
+// Group width 2^shift: the smallest power of two with (hi - lo) >> shift < G.
+__global__ void k_range_setup(const long long* __restrict__ mm, int G, RangeParams* __restrict__ p) {
+    long long lo = mm[0], hi = mm[1];
+    if (lo > hi) { lo = 0; hi = 0; }  // both tables empty in this column
+    const uint64_t span = (uint64_t)hi - (uint64_t)lo;
+    int s = 0;
+    while (s < 63 && (span >> s) >= (uint64_t)G) s++;
+    p->lo = lo;
+    p->hi = hi;
+    p->shift = s;
+    p->groups = (int)(span >> s) + 1;
+    p->fshift = 0;
+    p->pad = 0;
+}
+
+// Offset of value k from lo (k must lie in [lo, hi]).
+template <typename K>
+__device__ __forceinline__ uint64_t uoff(K k, long long lo) {
+    return (uint64_t)(long long)k - (uint64_t)lo;
+}
+
+// Window of S group y in offset space: [y*w - band, (y+1)*w - 1 + band] ∩ [0, span].
+__device__ __forceinline__ void window_of(const RangeParams& p, int y, long long band, uint64_t* wlo,
+                                          uint64_t* whi) {
+    const uint64_t span = (uint64_t)p.hi - (uint64_t)p.lo;
+    const uint64_t g0 = (uint64_t)y << p.shift;
+    const uint64_t g1 = ((uint64_t)(y + 1) << p.shift) - 1;
+    const uint64_t b = band < 0 ? 0 : (uint64_t)band;
+    *wlo = g0 > b ? g0 - b : 0;
+    *whi = (b > span || g1 + b > span || g1 + b < g1) ? span : g1 + b;
+}
+
+// Number of neighbouring groups a band reaches: ceil(band / width).
+__device__ __forceinline__ int band_groups(const RangeParams& p, long long band, int G) {
+    if (band <= 0) return 0;
+    const uint64_t w = (uint64_t)1 << p.shift;
+    const uint64_t d = ((uint64_t)band + w - 1) >> p.shift;
+    return d > (uint64_t)G ? G : (int)d;
+}
+
+// items[y] = R chunks of y's window x S chunks of group y.
+__global__ void k_theta_items(const uint64_t* __restrict__ roff, const uint64_t* __restrict__ soff,
+                              const RangeParams* __restrict__ prm, int G, long long band,
+                              uint64_t* __restrict__ items) {
+    int y = blockIdx.x * blockDim.x + threadIdx.x;
+    if (y >= G) return;
+    const int dg = band_groups(*prm, band, G);
+    const int x0 = max(0, y - dg), x1 = min(G - 1, y + dg);
+    const uint64_t nrw = roff[x1 + 1] - roff[x0];
+    const uint64_t ns = soff[y + 1] - soff[y];
+    items[y] = (nrw && ns) ? ((nrw + TH_RCAP - 1) / TH_RCAP) * ((ns + TH_SCH - 1) / TH_SCH) : 0;
+}
+
+// BAND: window + fine buckets; !BAND: diagonal group, every pair compared.
+// ka = compared column (a), kk = grouped column (k; equals ka when !BAND).
+template <typename K, int MODE, bool BAND>
+__global__ void __launch_bounds__(TH_T)
+k_theta_join(const K* __restrict__ rkk, const K* __restrict__ rka, const int32_t* __restrict__ rp,
+             const uint64_t* __restrict__ roff, const K* __restrict__ skk, const K* __restrict__ ska,
+             const int32_t* __restrict__ sp, const uint64_t* __restrict__ soff,
+             const RangeParams* __restrict__ prm, const uint64_t* __restrict__ item_prefix, int G, int op,
+             long long band, unsigned long long* __restrict__ item_val, unsigned long long* __restrict__ chk,
+             const uint64_t* __restrict__ item_off, jn_pair* __restrict__ out, unsigned int* __restrict__ work) {
+    extern __shared__ __align__(16) unsigned char smem[];
+    K* s_k = reinterpret_cast<K*>(smem);
+    K* s_a = s_k + TH_RCAP;
+    int32_t* s_p = reinterpret_cast<int32_t*>(s_a + TH_RCAP);
+    uint32_t* s_off = reinterpret_cast<uint32_t*>(s_p + TH_RCAP);
+    __shared__ unsigned long long tmp64[33];
+    __shared__ uint32_t tmp32[33];
+    __shared__ unsigned int s_item;
+    __shared__ uint32_t s_cursor, s_rows;
+
+    const RangeParams P = *prm;
+    const uint64_t nitems = item_prefix[G];
+    const int lane = threadIdx.x & 31;
+    const int dg = BAND ? band_groups(P, band, G) : 0;
+    while (true) {
+        if (threadIdx.x == 0) {
+            s_item = atomicAdd(work, 1u);
+            s_cursor = 0;
+            s_rows = 0;
+        }
+        __syncthreads();
+        const uint64_t it = s_item;
+        if (it >= nitems) break;
+        const int y = find_segment(item_prefix, G, it);
+        const int x0 = max(0, y - dg), x1 = min(G - 1, y + dg);
+        const uint64_t wbeg = roff[x0], nrw = roff[x1 + 1] - wbeg;
+        const uint64_t ns = soff[y + 1] - soff[y];
+        const uint64_t nrc = (nrw + TH_RCAP - 1) / TH_RCAP;
+        const uint64_t local = it - item_prefix[y];
+        const uint64_t rc = local % nrc, sc = local / nrc;
+        const uint64_t rbeg = wbeg + rc * TH_RCAP;
+        const int rn = (int)min((uint64_t)TH_RCAP, nrw - rc * TH_RCAP);
+        const uint64_t sbeg = soff[y] + sc * TH_SCH;
+        const int sn = (int)min((uint64_t)TH_SCH, ns - sc * TH_SCH);
+
+        uint64_t wlo = 0, whi = 0;
+        int fs = 0, nfb = 1;
+        if (BAND) {
+            window_of(P, y, band, &wlo, &whi);
+            while (((whi - wlo) >> fs) >= (uint64_t)TH_NFB) fs++;
+            nfb = (int)((whi - wlo) >> fs) + 1;
+            for (int i = threadIdx.x; i < nfb; i += TH_T) s_off[i] = 0;
+            __syncthreads();
+            for (int i = threadIdx.x; i < rn; i += TH_T) {
+                const uint64_t u = uoff(rkk[rbeg + i], P.lo);
+                if (u >= wlo && u <= whi) atomicAdd(&s_off[(u - wlo) >> fs], 1u);
+            }
+            __syncthreads();
+            uint32_t v[8];
+            uint32_t sum = 0;
+#pragma unroll
+            for (int j = 0; j < 8; j++) {
+                const int i = threadIdx.x * 8 + j;
+                v[j] = i < nfb ? s_off[i] : 0u;
+                sum += v[j];
+            }
+            uint32_t tot;
+            uint32_t pre = block_excl_scan(sum, tmp32, &tot);
+#pragma unroll
+            for (int j = 0; j < 8; j++) {
+                const int i = threadIdx.x * 8 + j;
+                if (i < nfb) s_off[i] = pre;
+                pre += v[j];
+            }
+            __syncthreads();
+            for (int i = threadIdx.x; i < rn; i += TH_T) {
+                const K kk = rkk[rbeg + i];
+                const uint64_t u = uoff(kk, P.lo);
+                if (u >= wlo && u <= whi) {
+                    const uint32_t pos = atomicAdd(&s_off[(u - wlo) >> fs], 1u);
+                    s_k[pos] = kk;
+                    s_a[pos] = rka[rbeg + i];
+                    s_p[pos] = rp[rbeg + i];
+                }
+            }
+            // bucket b now holds [b ? s_off[b-1] : 0, s_off[b])
+        } else {
+            for (int i = threadIdx.x; i < rn; i += TH_T) {
+                s_a[i] = rka[rbeg + i];
+                s_p[i] = rp[rbeg + i];
+            }
+            if (threadIdx.x == 0) s_rows = (uint32_t)rn;
+        }
+        __syncthreads();
+
+        unsigned long long acc = 0, csum = 0;
+        const int rounds = (sn + TH_T - 1) / TH_T;
+        for (int r = 0; r < rounds; r++) {
+            const int j = r * TH_T + threadIdx.x;
+            uint32_t lo = 0, hi = 0;
+            Interval<K> ia, ib;
+            int32_t pay = 0;
+            if (j < sn) {
+                const K a = ska[sbeg + j];
+                pay = sp[sbeg + j];
+                ia = op_interval<K>(op, a);
+                if (BAND) {
+                    const K kk = skk[sbeg + j];
+                    ib = band_interval<K>(kk, band);
+                    const uint64_t u = uoff(kk, P.lo);
+                    const uint64_t b = (uint64_t)band;
+                    uint64_t ql = (u > b) ? u - b : 0;
+                    uint64_t qh = (b > whi || u + b > whi || u + b < u) ? whi : u + b;
+                    if (ql < wlo) ql = wlo;
+                    const uint32_t b0 = (uint32_t)((ql - wlo) >> fs), b1 = (uint32_t)((qh - wlo) >> fs);
+                    lo = b0 ? s_off[b0 - 1] : 0u;
+                    hi = s_off[b1];
+                } else {
+                    lo = 0;
+                    hi = s_rows;
+                }
+            }
+            uint32_t m = 0;
+            unsigned long long fs_sum = 0;
+            for (uint32_t e = lo; e < hi; e++) {
+                bool ok = iv_test(ia, s_a[e]);
+                if (BAND) ok = ok && iv_test(ib, s_k[e]);
+                if (ok) {
+                    m++;
+                    if (MODE == MODE_AGG) fs_sum += chk_f(s_p[e]);
+                }
+            }
+            if (MODE == MODE_EMIT) {
+                const uint32_t incl = warp_incl_scan(m);
+                const uint32_t wt = __shfl_sync(0xffffffffu, incl, 31);
+                uint32_t base = 0;
+                if (lane == 0 && wt) base = atomicAdd(&s_cursor, wt);
+                base = __shfl_sync(0xffffffffu, base, 0);
+                if (m) {
+                    uint64_t o = item_off[it] + base + (incl - m);
+                    for (uint32_t e = lo; e < hi; e++) {
+                        bool ok = iv_test(ia, s_a[e]);
+                        if (BAND) ok = ok && iv_test(ib, s_k[e]);
+                        if (ok) {
+                            jn_pair q;
+                            q.r = s_p[e];
+                            q.s = pay;
+                            out[o++] = q;
+                        }
+                    }
+                }
+            } else {
+                acc += m;
+                if (MODE == MODE_AGG && m) csum += fs_sum * chk_g(pay);
+            }
+        }
+        if (MODE != MODE_EMIT) {
+            const unsigned long long t = block_sum(acc, tmp64);
+            if (MODE == MODE_AGG) {
+                const unsigned long long cs = block_sum(csum, tmp64);
+                if (threadIdx.x == 0 && cs) atomicAdd(chk, cs);
+            }
+            if (threadIdx.x == 0) item_val[it] = t;
+        }
+        __syncthreads();
+    }
+}
+
+// ----------------------------------------------------- cross regions --
+// R rows whose group already decides "R.a op S.a" for S group y: up to two
+// contiguous ranges of the partitioned R ([0, roff[y]) and [roff[y+1], nr)).
+__device__ __forceinline__ void cross_ranges(int op, const uint64_t* roff, int y, int G, uint64_t* b0,
+                                             uint64_t* l0, uint64_t* b1, uint64_t* l1) {
+    const uint64_t below = roff[y], above_b = roff[y + 1], nr = roff[G];
+    *b0 = 0; *l0 = 0; *b1 = above_b; *l1 = 0;
+    switch (op) {
+        case JN_LT: case JN_LE: *l0 = below; break;
+        case JN_GT: case JN_GE: *l1 = nr - above_b; break;
+        case JN_NE: case JN_ANY: *l0 = below; *l1 = nr - above_b; break;
+        default: break;
+    }
+}
+
+// cross[y] = pairs of y's cross regions; chunks[y] = ceil(cross[y] / CE_CHUNK).
+__global__ void k_cross_counts(const uint64_t* __restrict__ roff, const uint64_t* __restrict__ soff,
+                               int G, int op, uint64_t* __restrict__ cross, uint64_t* __restrict__ chunks) {
+    int y = blockIdx.x * blockDim.x + threadIdx.x;
+    if (y >= G) return;
+    uint64_t b0, l0, b1, l1;
+    cross_ranges(op, roff, y, G, &b0, &l0, &b1, &l1);
+    const uint64_t c = (l0 + l1) * (soff[y + 1] - soff[y]);
+    cross[y] = c;
+    chunks[y] = (c + CE_CHUNK - 1) / CE_CHUNK;
+}
+
+// Checksum of the cross regions: sum_y (sum of f over the ranges) * (sum of g over S_y),
+// using fpre = prefix sums of f over the partitioned R payloads.
+__global__ void k_cross_checksum(const uint64_t* __restrict__ roff, const uint64_t* __restrict__ soff,
+                                 const int32_t* __restrict__ sp, const uint64_t* __restrict__ fpre, int G,
+                                 int op, unsigned long long* __restrict__ chk) {
+    __shared__ unsigned long long tmp[33];
+    const int y = blockIdx.x;
+    uint64_t b0, l0, b1, l1;
+    cross_ranges(op, roff, y, G, &b0, &l0, &b1, &l1);
+    if (l0 + l1 == 0) return;
+    unsigned long long g = 0;
+    for (uint64_t i = soff[y] + threadIdx.x; i < soff[y + 1]; i += blockDim.x) g += chk_g(sp[i]);
+    g = block_sum(g, tmp);
+    if (threadIdx.x == 0) {
+        const uint64_t f = (fpre[b0 + l0] - fpre[b0]) + (fpre[b1 + l1] - fpre[b1]);
+        atomicAdd(chk, (unsigned long long)(f * g));
+    }
+}
+
+__global__ void k_fvals(const int32_t* __restrict__ p, int64_t n, uint64_t* __restrict__ f) {
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) f[i] = chk_f(p[i]);
+}
+
+// Writes the cross products: pair q of group y is (R[range(q % len)], S_y[q / len]).
+__global__ void __launch_bounds__(256)
+k_cross_emit(const int32_t* __restrict__ rp, const uint64_t* __restrict__ roff, const int32_t* __restrict__ sp,
+             const uint64_t* __restrict__ soff, const uint64_t* __restrict__ cross_off,
+             const uint64_t* __restrict__ chunk_prefix, int G, int op, uint64_t base,
+             jn_pair* __restrict__ out, unsigned int* __restrict__ work) {
+    __shared__ unsigned int s_item;
+    const uint64_t nchunks = chunk_prefix[G];
+    while (true) {
+        if (threadIdx.x == 0) s_item = atomicAdd(work, 1u);
+        __syncthreads();
+        const uint64_t it = s_item;
+        __syncthreads();
+        if (it >= nchunks) break;
+        const int y = find_segment(chunk_prefix, G, it);
+        uint64_t b0, l0, b1, l1;
+        cross_ranges(op, roff, y, G, &b0, &l0, &b1, &l1);
+        const uint64_t len = l0 + l1;
+        const uint64_t total = len * (soff[y + 1] - soff[y]);
+        const uint64_t q0 = (it - chunk_prefix[y]) * CE_CHUNK;
+        const uint64_t q1 = min(total, q0 + CE_CHUNK);
+        const uint64_t obase = base + cross_off[y];
+        for (uint64_t q = q0 + threadIdx.x; q < q1; q += blockDim.x) {
+            const uint64_t si = q / len, ri = q - si * len;
+            const uint64_t r = ri < l0 ? b0 + ri : b1 + (ri - l0);
+            jn_pair v;
+            v.r = rp[r];
+            v.s = sp[soff[y] + si];
+            out[obase + q] = v;
+        }
+    }
+}
+
+template <typename K>
+static jn_status range_partition(jn_ctx* c, Scratch& s, const Cols<K>& T, const K* grp, const K* carry,
+                                 const RangeParams* prm, int G, unsigned int* work, K** okk, K** oka,
+                                 int32_t** op, uint64_t** off) {
+    const uint64_t n = (uint64_t)T.n;
+    uint64_t *sb, *scn, *tp, *start;
+    unsigned long long *hist, *cur;
+    JN_TRY(s.get(&sb, 2));
+    JN_TRY(s.get(&scn, 2));
+    JN_TRY(s.get(&tp, 3));
+    JN_TRY(s.get(&start, G + 1));
+    JN_TRY(s.get(&hist, G));
+    JN_TRY(s.get(&cur, G));
+    JN_TRY(zero(c, hist, sizeof(unsigned long long) * G));
+    JN_TRY(launch(c, K_SEGMENTS, k_one_segment, dim3(1), dim3(32), 0, sb, scn, tp, n));
+    RangeDigit dg{prm};
+    auto kh = k_seg_hist<K, RangeDigit>;
+    const size_t smh = sizeof(uint32_t) * G;
+    int per = 0;
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, kh, SC_T, smh);
+    JN_TRY(zero(c, work, 4));
+    JN_TRY(launch(c, K_HIST, kh, dim3(max(per, 1) * c->num_sms), dim3(SC_T), smh, grp,
+                  (const uint64_t*)sb, (const uint64_t*)scn, (const uint64_t*)tp, 1, dg, G, hist, work));
+    JN_TRY(scan_u64(c, reinterpret_cast<const uint64_t*>(hist), start, G));
+    JN_TRY(launch(c, K_MISC, k_init_cursor, dim3((G + 255) / 256), dim3(256), 0, (const uint64_t*)start,
+                  cur, (int64_t)G));
+    K *kk, *ka = nullptr;
+    int32_t* pp;
+    JN_TRY(s.get(&kk, n));
+    if (carry) JN_TRY(s.get(&ka, n));
+    JN_TRY(s.get(&pp, n));
+    auto ks = k_scatter<K, false, RangeDigit>;
+    const size_t sm = scatter_smem<K>(carry != nullptr);
+    per = 0;
+    ensure_smem((const void*)ks, sm);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, ks, SC_T, sm);
+    JN_TRY(zero(c, work, 4));
+    JN_TRY(launch(c, K_SCATTER, ks, dim3(max(per, 1) * c->num_sms), dim3(SC_T), sm, grp, carry, T.pay,
+                  (const uint64_t*)sb, (const uint64_t*)scn, (const uint64_t*)tp, 1, dg, G,
+                  (const uint32_t*)nullptr, 0u, cur, kk, ka, pp, work));
+    *okk = kk;
+    *oka = carry ? ka : kk;
+    *op = pp;
+    *off = start;
+    return JN_OK;
+}
+
+template <typename K>
+jn_status run_theta(jn_ctx* c, const Cols<K>& R, const Cols<K>& S, int op, int64_t band, int mode,
+                    OutPlan* plan, RunResult* res) {
+    jn_run_info& info = c->info;
+    const bool B = band >= 0;
+    if (R.n == 0 || S.n == 0) {
+        res->count = res->checksum = 0;
+        if (mode == MODE_EMIT) {
+            Scratch s0(c);
+            JN_TRY(out_prepare(c, s0, 0, *plan));
+            JN_TRY(out_finish(c, 0, *plan));
+        }
+        return JN_OK;
+    }
+    int g = c->tune.theta_groups;
+    if (g == 0) {
+        const uint64_t base = B ? (uint64_t)R.n : (uint64_t)max(R.n, S.n);
+        g = ceil_log2(ceil_div(base, B ? 1024 : 2048));
+        if (g < 2) g = 2;
+        if (g > 10) g = 10;
+    }
+    const int G = 1 << g;
+    Scratch s(c);
+    unsigned int* work;
+    long long* mm;
+    RangeParams* prm;
+    uint64_t* d_small;
+    JN_TRY(s.get(&work, 4));
+    JN_TRY(s.get(&mm, 2));
+    JN_TRY(s.get(&prm, 1));
+    JN_TRY(s.get(&d_small, 4));
+    const K* rg = B ? R.key2 : R.key;
+    const K* sg = B ? S.key2 : S.key;
+    JN_TRY(launch(c, K_MINMAX, k_mm_init, dim3(1), dim3(1), 0, mm));
+    JN_TRY(launch(c, K_MINMAX, k_minmax<K>, dim3(2 * c->num_sms), dim3(512), 0, rg, R.n, mm));
+    JN_TRY(launch(c, K_MINMAX, k_minmax<K>, dim3(2 * c->num_sms), dim3(512), 0, sg, S.n, mm));
+    JN_TRY(launch(c, K_MINMAX, k_range_setup, dim3(1), dim3(1), 0, (const long long*)mm, G, prm));
+    K *rkk, *rka, *skk, *ska;
+    int32_t *rp, *sp;
+    uint64_t *roff, *soff;
+    JN_TRY(range_partition<K>(c, s, R, rg, B ? R.key : nullptr, prm, G, work, &rkk, &rka, &rp, &roff));
+    JN_TRY(range_partition<K>(c, s, S, sg, B ? S.key : nullptr, prm, G, work, &skk, &ska, &sp, &soff));
+    // ---- compared regions (band window or diagonal) ----
+    uint64_t *items, *ipre;
+    JN_TRY(s.get(&items, G));
+    JN_TRY(s.get(&ipre, G + 1));
+    JN_TRY(launch(c, K_ITEMS, k_theta_items, dim3((G + 255) / 256), dim3(256), 0, (const uint64_t*)roff,
+                  (const uint64_t*)soff, (const RangeParams*)prm, G, (long long)(B ? band : -1), items));
+    JN_TRY(scan_u64(c, items, ipre, G));
+    // ---- cross regions (one-column predicate only) ----
+    uint64_t *cross = nullptr, *coff = nullptr, *chunks = nullptr, *cpre = nullptr;
+    const bool has_cross = !B && op != JN_EQ;
+    if (has_cross) {
+        JN_TRY(s.get(&cross, G));
+        JN_TRY(s.get(&coff, G + 1));
+        JN_TRY(s.get(&chunks, G));
+        JN_TRY(s.get(&cpre, G + 1));
+        JN_TRY(launch(c, K_ITEMS, k_cross_counts, dim3((G + 255) / 256), dim3(256), 0,
+                      (const uint64_t*)roff, (const uint64_t*)soff, G, op, cross, chunks));
+        JN_TRY(scan_u64(c, cross, coff, G));
+        JN_TRY(scan_u64(c, chunks, cpre, G));
+    }
+    JN_CUDA(c, cudaMemcpyAsync(d_small, ipre + G, 8, cudaMemcpyDeviceToDevice, c->stream));
+    uint64_t nitems = 0;
+    JN_TRY(read_back(c, d_small, &nitems, 1));
+    unsigned long long *ival, *chk;
+    uint64_t* ioff;
+    JN_TRY(s.get(&ival, nitems + 1));
+    JN_TRY(s.get(&ioff, nitems + 1));
+    JN_TRY(s.get(&chk, 1));
+    JN_TRY(zero(c, chk, 8));
+    const size_t smj = (size_t)TH_RCAP * (2 * sizeof(K) + 4) + sizeof(uint32_t) * TH_NFB;
+    const int cm = mode == MODE_AGG ? MODE_AGG : MODE_COUNT;
+    auto pick = [&](int m) -> void (*)(const K*, const K*, const int32_t*, const uint64_t*, const K*,
+                                       const K*, const int32_t*, const uint64_t*, const RangeParams*,
+                                       const uint64_t*, int, int, long long, unsigned long long*,
+                                       unsigned long long*, const uint64_t*, jn_pair*, unsigned int*) {
+        if (B) {
+            if (m == MODE_EMIT) return k_theta_join<K, MODE_EMIT, true>;
+            if (m == MODE_AGG) return k_theta_join<K, MODE_AGG, true>;
+            return k_theta_join<K, MODE_COUNT, true>;
+        }
+        if (m == MODE_EMIT) return k_theta_join<K, MODE_EMIT, false>;
+        if (m == MODE_AGG) return k_theta_join<K, MODE_AGG, false>;
+        return k_theta_join<K, MODE_COUNT, false>;
+    };
+    auto grid_of = [&](const void* fn) {
+        int per = 0;
+        ensure_smem(fn, smj);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, fn, TH_T, smj);
+        return max(per, 1) * c->num_sms;
+    };
+    if (nitems) {
+        auto kc = pick(cm);
+        JN_TRY(zero(c, work, 4));
+        JN_TRY(launch(c, K_THETA_COUNT, kc, dim3(grid_of((const void*)kc)), dim3(TH_T), smj,
+                      (const K*)rkk, (const K*)rka, (const int32_t*)rp, (const uint64_t*)roff, (const K*)skk,
+                      (const K*)ska, (const int32_t*)sp, (const uint64_t*)soff, (const RangeParams*)prm,
+                      (const uint64_t*)ipre, G, op, (long long)(B ? band : -1), ival, chk,
+                      (const uint64_t*)nullptr, (jn_pair*)nullptr, work));
+    }
+    JN_TRY(scan_u64(c, reinterpret_cast<const uint64_t*>(ival), ioff, (int64_t)nitems));
+    if (has_cross && mode == MODE_AGG) {
+        uint64_t *fv, *fpre;
+        JN_TRY(s.get(&fv, R.n));
+        JN_TRY(s.get(&fpre, R.n + 1));
+        JN_TRY(launch(c, K_MISC, k_fvals, dim3((unsigned)ceil_div(R.n, 256)), dim3(256), 0,
+                      (const int32_t*)rp, (int64_t)R.n, fv));
+        JN_TRY(scan_u64(c, fv, fpre, R.n));
+        JN_TRY(launch(c, K_MISC, k_cross_checksum, dim3(G), dim3(256), 0, (const uint64_t*)roff,
+                      (const uint64_t*)soff, (const int32_t*)sp, (const uint64_t*)fpre, G, op, chk));
+    }
+    JN_CUDA(c, cudaMemcpyAsync(d_small, ioff + nitems, 8, cudaMemcpyDeviceToDevice, c->stream));
+    JN_CUDA(c, cudaMemcpyAsync(d_small + 1, chk, 8, cudaMemcpyDeviceToDevice, c->stream));
+    if (has_cross) JN_CUDA(c, cudaMemcpyAsync(d_small + 2, coff + G, 8, cudaMemcpyDeviceToDevice, c->stream));
+    uint64_t h[3] = {0, 0, 0};
+    JN_TRY(read_back(c, d_small, h, has_cross ? 3 : 2));
+    const uint64_t diag = h[0], crossn = has_cross ? h[2] : 0;
+    const uint64_t total = diag + crossn;
+    res->count = total;
+    res->checksum = h[1];
+    info.result = total;
+    info.partitions = (uint64_t)G;
+    info.work_items = nitems;
+    info.r_survivors = (uint64_t)R.n;
+    info.s_survivors = (uint64_t)S.n;
+    info.prefilter = 0;
+    if (mode != MODE_EMIT) return JN_OK;
+    JN_TRY(out_prepare(c, s, total, *plan));
+    if (diag) {
+        auto ke = pick(MODE_EMIT);
+        JN_TRY(zero(c, work, 4));
+        JN_TRY(launch(c, K_THETA_EMIT, ke, dim3(grid_of((const void*)ke)), dim3(TH_T), smj,
+                      (const K*)rkk, (const K*)rka, (const int32_t*)rp, (const uint64_t*)roff, (const K*)skk,
+                      (const K*)ska, (const int32_t*)sp, (const uint64_t*)soff, (const RangeParams*)prm,
+                      (const uint64_t*)ipre, G, op, (long long)(B ? band : -1),
+                      (unsigned long long*)nullptr, (unsigned long long*)nullptr, (const uint64_t*)ioff,
+                      plan->dev, work));
+    }
+    if (crossn) {
+        JN_TRY(zero(c, work, 4));
+        JN_TRY(launch(c, K_CROSS_EMIT, k_cross_emit, dim3(4 * c->num_sms), dim3(256), 0, (const int32_t*)rp,
+                      (const uint64_t*)roff, (const int32_t*)sp, (const uint64_t*)soff, (const uint64_t*)coff,
+                      (const uint64_t*)cpre, G, op, diag, plan->dev, work));
+    }
+    JN_TRY(out_finish(c, total, *plan));
+    return JN_OK;
+}
+
+template jn_status run_theta<int32_t>(jn_ctx*, const Cols<int32_t>&, const Cols<int32_t>&, int, int64_t,
+                                      int, OutPlan*, RunResult*);
+template jn_status run_theta<int64_t>(jn_ctx*, const Cols<int64_t>&, const Cols<int64_t>&, int, int64_t,
+                                      int, OutPlan*, RunResult*);
+
+}  // namespace jnx

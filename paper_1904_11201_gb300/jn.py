@@ -1,0 +1,293 @@
+"""Python binding of libjn (include/jn.h): argument marshalling only.
+
+Every join step runs in the CUDA library; this module converts torch
+tensors into ``jn_table`` structures, calls the C entry points of the same
+names, and wraps library-allocated results as torch tensors.  It never
+computes a join itself and fails loudly when the library is missing.
+
+Columns may be CUDA tensors or CPU tensors (the library stages host
+columns to the device).  Pairs come back as an (n, 2) int32 tensor of
+(r, s) = (R.payload, S.payload).
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import torch
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "_build", "libjn.so")
+
+JN_OK, JN_ERR_INVALID, JN_ERR_OOM, JN_ERR_CAPACITY, JN_ERR_CUDA, JN_ERR_TIMEOUT, \
+    JN_ERR_UNSUPPORTED = range(7)
+JN_KEY_I32, JN_KEY_I64 = 4, 8
+JN_EQ, JN_NE, JN_LT, JN_LE, JN_GT, JN_GE, JN_ANY = range(7)
+JN_ALGO_NLJ, JN_ALGO_HASH, JN_ALGO_THETA = range(3)
+OPS = {"=": JN_EQ, "!=": JN_NE, "<": JN_LT, "<=": JN_LE, ">": JN_GT, ">=": JN_GE, "any": JN_ANY}
+
+
+class JoinError(RuntimeError):
+    def __init__(self, status, msg, required=None):
+        super().__init__("%s (status %d)" % (msg, status))
+        self.status = status
+        self.required = required
+
+
+class Table(ctypes.Structure):
+    _fields_ = [("key", ctypes.c_void_p), ("key2", ctypes.c_void_p), ("payload", ctypes.c_void_p),
+                ("n", ctypes.c_int64), ("key_type", ctypes.c_int32), ("reserved", ctypes.c_int32)]
+
+
+class Pred(ctypes.Structure):
+    _fields_ = [("op_a", ctypes.c_int32), ("op_k", ctypes.c_int32), ("band", ctypes.c_int64)]
+
+
+class Tuning(ctypes.Structure):
+    _fields_ = [("prefilter", ctypes.c_int32), ("radix_bits", ctypes.c_int32),
+                ("radix_bits1", ctypes.c_int32), ("filter_bits", ctypes.c_int32),
+                ("heavy", ctypes.c_int32), ("theta_groups", ctypes.c_int32),
+                ("nlj_tile_r", ctypes.c_int32), ("reserved", ctypes.c_int32 * 9)]
+
+
+class KernelStat(ctypes.Structure):
+    _fields_ = [("name", ctypes.c_char * 32), ("launches", ctypes.c_uint64), ("ms", ctypes.c_double)]
+
+
+class RunInfo(ctypes.Structure):
+    _fields_ = [("result", ctypes.c_uint64), ("r_survivors", ctypes.c_uint64),
+                ("s_survivors", ctypes.c_uint64), ("partitions", ctypes.c_uint64),
+                ("work_items", ctypes.c_uint64), ("heavy_keys", ctypes.c_uint64),
+                ("kernel_launches", ctypes.c_uint64), ("prefilter", ctypes.c_int32),
+                ("radix_bits", ctypes.c_int32), ("radix_bits1", ctypes.c_int32),
+                ("filter_bits", ctypes.c_int32), ("reserved", ctypes.c_uint64 * 6)]
+
+
+class Pair(ctypes.Structure):
+    _fields_ = [("r", ctypes.c_int32), ("s", ctypes.c_int32)]
+
+
+_lib = None
+
+# name -> (restype, argtypes); kept in step with include/jn.h
+_P = ctypes.c_void_p
+_SIGS = {
+    "jn_create": (ctypes.c_int, [ctypes.POINTER(_P), ctypes.c_int, _P]),
+    "jn_destroy": (None, [_P]),
+    "jn_set_stream": (ctypes.c_int, [_P, _P]),
+    "jn_set_tuning": (ctypes.c_int, [_P, ctypes.POINTER(Tuning)]),
+    "jn_get_tuning": (ctypes.c_int, [_P, ctypes.POINTER(Tuning)]),
+    "jn_status_str": (ctypes.c_char_p, [ctypes.c_int]),
+    "jn_last_error": (ctypes.c_char_p, [_P]),
+    "jn_version": (ctypes.c_char_p, []),
+    "jn_count": (ctypes.c_int, [_P, ctypes.c_int32, ctypes.POINTER(Table), ctypes.POINTER(Table),
+                                ctypes.POINTER(Pred), ctypes.POINTER(ctypes.c_uint64)]),
+    "jn_aggregate": (ctypes.c_int, [_P, ctypes.c_int32, ctypes.POINTER(Table), ctypes.POINTER(Table),
+                                    ctypes.POINTER(Pred), ctypes.POINTER(ctypes.c_uint64),
+                                    ctypes.POINTER(ctypes.c_uint64)]),
+    "jn_nested_loop": (ctypes.c_int, [_P, ctypes.POINTER(Table), ctypes.POINTER(Table),
+                                      ctypes.POINTER(Pred), ctypes.POINTER(_P), ctypes.c_uint64,
+                                      ctypes.POINTER(ctypes.c_uint64)]),
+    "jn_hash": (ctypes.c_int, [_P, ctypes.POINTER(Table), ctypes.POINTER(Table), ctypes.POINTER(_P),
+                               ctypes.c_uint64, ctypes.POINTER(ctypes.c_uint64)]),
+    "jn_theta": (ctypes.c_int, [_P, ctypes.POINTER(Table), ctypes.POINTER(Table), ctypes.c_int32,
+                                ctypes.c_int64, ctypes.POINTER(_P), ctypes.c_uint64,
+                                ctypes.POINTER(ctypes.c_uint64)]),
+    "jn_free": (None, [_P, _P]),
+    "jn_set_profiling": (ctypes.c_int, [_P, ctypes.c_int32]),
+    "jn_kernel_stats": (ctypes.c_int, [_P, ctypes.POINTER(KernelStat), ctypes.c_int32,
+                                       ctypes.POINTER(ctypes.c_int32)]),
+    "jn_reset_stats": (ctypes.c_int, [_P]),
+    "jn_last_run_info": (ctypes.c_int, [_P, ctypes.POINTER(RunInfo)]),
+    "jn_launch_count": (ctypes.c_uint64, [_P]),
+}
+
+
+def exported_symbols():
+    """Names the binding expects libjn.so to export (the jn.h entry points)."""
+    return sorted(_SIGS)
+
+
+def load(path: str = LIB_PATH):
+    """Loads libjn.so; raises if it has not been built (no fallback exists)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(path):
+            raise RuntimeError("libjn.so not found at %s: build it with "
+                               "`python -m paper_1904_11201_gb300.build`" % path)
+        lib = ctypes.CDLL(path)
+        for name, (res, args) in _SIGS.items():
+            fn = getattr(lib, name)
+            fn.restype = res
+            fn.argtypes = args
+        _lib = lib
+    return _lib
+
+
+def _check(ctx, st, required=None):
+    if st != JN_OK:
+        lib = load()
+        msg = lib.jn_last_error(ctx.handle if ctx else None)
+        msg = (msg or b"").decode() or lib.jn_status_str(st).decode()
+        raise JoinError(st, msg, required)
+
+
+class Context:
+    """Owns a jn_ctx on one device and stream."""
+
+    def __init__(self, device: int = 0, stream=None):
+        lib = load()
+        if stream is None:
+            stream = torch.cuda.current_stream(device)
+        self.stream = stream
+        h = _P()
+        st = lib.jn_create(ctypes.byref(h), device, _P(stream.cuda_stream))
+        if st != JN_OK:
+            raise JoinError(st, "jn_create failed: %s" % lib.jn_status_str(st).decode())
+        self.handle = h
+        self.device = device
+        self.closed = False
+
+    def close(self):
+        if not self.closed:
+            load().jn_destroy(self.handle)
+            self.closed = True
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def set_tuning(self, **kw):
+        t = Tuning()
+        load().jn_get_tuning(self.handle, ctypes.byref(t))
+        for k, v in kw.items():
+            setattr(t, k, v)
+        _check(self, load().jn_set_tuning(self.handle, ctypes.byref(t)))
+
+    def tuning(self) -> dict:
+        t = Tuning()
+        load().jn_get_tuning(self.handle, ctypes.byref(t))
+        return {f: getattr(t, f) for f, _ in Tuning._fields_ if f != "reserved"}
+
+    def set_profiling(self, on: bool):
+        _check(self, load().jn_set_profiling(self.handle, 1 if on else 0))
+
+    def kernel_stats(self) -> dict:
+        arr = (KernelStat * 64)()
+        n = ctypes.c_int32()
+        _check(self, load().jn_kernel_stats(self.handle, arr, 64, ctypes.byref(n)))
+        return {arr[i].name.decode(): (int(arr[i].launches), float(arr[i].ms)) for i in range(n.value)}
+
+    def reset_stats(self):
+        _check(self, load().jn_reset_stats(self.handle))
+
+    def run_info(self) -> dict:
+        ri = RunInfo()
+        load().jn_last_run_info(self.handle, ctypes.byref(ri))
+        return {f: getattr(ri, f) for f, _ in RunInfo._fields_ if f != "reserved"}
+
+    def launch_count(self) -> int:
+        return int(load().jn_launch_count(self.handle))
+
+
+class TableRef:
+    """A jn_table plus references keeping its tensors alive."""
+
+    def __init__(self, key, key2=None, payload=None):
+        if key.dtype not in (torch.int32, torch.int64):
+            raise TypeError("key columns must be int32 or int64")
+        cols = [key] + [c for c in (key2,) if c is not None]
+        for c in cols:
+            if c.dtype != key.dtype or c.dim() != 1 or not c.is_contiguous():
+                raise TypeError("key columns must be contiguous 1-D tensors of one dtype")
+        if payload is not None and (payload.dtype != torch.int32 or payload.shape != key.shape
+                                    or not payload.is_contiguous()):
+            raise TypeError("payload must be a contiguous int32 tensor like the key")
+        self.refs = (key, key2, payload)
+        n = key.shape[0]
+        self.t = Table(key.data_ptr() if n else None,
+                       key2.data_ptr() if (key2 is not None and n) else None,
+                       payload.data_ptr() if (payload is not None and n) else None,
+                       n, JN_KEY_I32 if key.dtype == torch.int32 else JN_KEY_I64, 0)
+
+
+def table(key, key2=None, payload=None) -> TableRef:
+    return TableRef(key, key2, payload)
+
+
+def pred(op_a=JN_EQ, op_k=JN_ANY, band=-1) -> Pred:
+    return Pred(op_a, op_k, band)
+
+
+class _DeviceResult:
+    """Library-allocated pairs exposed through __cuda_array_interface__."""
+
+    def __init__(self, ctx, ptr, n):
+        self._ctx = ctx
+        self._ptr = ptr
+        self.__cuda_array_interface__ = {"shape": (n, 2), "typestr": "<i4", "data": (ptr, False),
+                                         "version": 3, "strides": None, "stream": None}
+
+    def __del__(self):
+        lib = load()
+        ctx = self._ctx
+        lib.jn_free(None if ctx.closed else ctx.handle, _P(self._ptr))
+
+
+def _result(ctx, out_ptr, n, user_out):
+    if user_out is not None:
+        return user_out[:n]
+    if n == 0 or not out_ptr.value:
+        return torch.empty((0, 2), dtype=torch.int32, device="cuda:%d" % ctx.device)
+    return torch.as_tensor(_DeviceResult(ctx, out_ptr.value, n), device="cuda:%d" % ctx.device)
+
+
+def _emit(ctx, fn, args, out):
+    n = ctypes.c_uint64()
+    if out is None:
+        p = _P(None)
+        cap = 0
+    else:
+        if out.dtype != torch.int32 or out.dim() != 2 or out.shape[1] != 2 or not out.is_contiguous():
+            raise TypeError("out must be a contiguous (cap, 2) int32 tensor")
+        p = _P(out.data_ptr())
+        cap = out.shape[0]
+    st = fn(ctx.handle, *args, ctypes.byref(p), cap, ctypes.byref(n))
+    _check(ctx, st, required=int(n.value) if st == JN_ERR_CAPACITY else None)
+    return _result(ctx, p, int(n.value), out)
+
+
+# ------------------------------------------------------------ entry points --
+
+def jn_count(ctx: Context, algo: int, R: TableRef, S: TableRef, pr: Pred = None) -> int:
+    c = ctypes.c_uint64()
+    st = load().jn_count(ctx.handle, algo, ctypes.byref(R.t), ctypes.byref(S.t),
+                         ctypes.byref(pr) if pr is not None else None, ctypes.byref(c))
+    _check(ctx, st)
+    return int(c.value)
+
+
+def jn_aggregate(ctx: Context, algo: int, R: TableRef, S: TableRef, pr: Pred = None):
+    c = ctypes.c_uint64()
+    h = ctypes.c_uint64()
+    st = load().jn_aggregate(ctx.handle, algo, ctypes.byref(R.t), ctypes.byref(S.t),
+                             ctypes.byref(pr) if pr is not None else None, ctypes.byref(c),
+                             ctypes.byref(h))
+    _check(ctx, st)
+    return int(c.value), int(h.value)
+
+
+def jn_nested_loop(ctx: Context, R: TableRef, S: TableRef, pr: Pred = None, out=None):
+    return _emit(ctx, load().jn_nested_loop,
+                 (ctypes.byref(R.t), ctypes.byref(S.t), ctypes.byref(pr) if pr is not None else None),
+                 out)
+
+
+def jn_hash(ctx: Context, R: TableRef, S: TableRef, out=None):
+    return _emit(ctx, load().jn_hash, (ctypes.byref(R.t), ctypes.byref(S.t)), out)
+
+
+def jn_theta(ctx: Context, R: TableRef, S: TableRef, op: int, band: int = -1, out=None):
+    return _emit(ctx, load().jn_theta, (ctypes.byref(R.t), ctypes.byref(S.t), op, band), out)

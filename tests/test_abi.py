@@ -1,0 +1,55 @@
+"""The C-ABI library builds, loads and exports every entry point of jn.h
+(no GPU needed: nothing here launches a kernel)."""
+import ctypes
+import os
+import re
+import subprocess
+
+import pytest
+
+from paper_1904_11201_gb300 import build as B
+from paper_1904_11201_gb300 import jn
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def lib_path():
+    return B.build()
+
+
+def header_functions():
+    text = open(os.path.join(ROOT, "include", "jn.h")).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    names = re.findall(r"\b(jn_[a-z_0-9]+)\s*\(", text)
+    return sorted(set(names))
+
+
+def test_header_declares_binding_names():
+    assert header_functions() == jn.exported_symbols()
+
+
+def test_library_exports_every_declared_symbol(lib_path):
+    out = subprocess.run(["nm", "-D", "--defined-only", lib_path], capture_output=True, text=True).stdout
+    exported = set(re.findall(r"\bT (jn_[a-z_0-9]+)\b", out))
+    missing = [n for n in header_functions() if n not in exported]
+    assert not missing, missing
+
+
+def test_library_loads_and_answers_without_gpu(lib_path):
+    lib = jn.load(lib_path)
+    assert lib.jn_version().startswith(b"jn ")
+    assert lib.jn_status_str(jn.JN_ERR_CAPACITY) == b"output buffer too small"
+    # NULL context arguments are rejected without touching a device
+    assert lib.jn_set_profiling(None, 1) == jn.JN_ERR_INVALID
+    assert lib.jn_count(None, 0, None, None, None, None) == jn.JN_ERR_INVALID
+    h = ctypes.c_void_p()
+    st = lib.jn_create(ctypes.byref(h), 0, None)
+    # no GPU in this container: creation must fail cleanly, not crash
+    import torch
+    if not torch.cuda.is_available():
+        assert st != jn.JN_OK and not h.value
+
+
+def test_build_targets_sm103a_only():
+    assert B.ARCH == ["-gencode", "arch=compute_103a,code=sm_103a"]

@@ -1,0 +1,244 @@
+"""GPU parity: the CUDA join path (through the C ABI) against the CPU oracle.
+
+Every comparison is exact: result multisets of (r, s) pairs are compared
+after sorting (output order is unspecified), counts and separable checksums
+must be equal.  Inputs come from the seeded generators only.
+"""
+import numpy as np
+import pytest
+import torch
+
+import oracle as O
+from paper_1904_11201_gb300 import build as B
+from paper_1904_11201_gb300 import datagen
+from paper_1904_11201_gb300 import jn
+
+pytestmark = pytest.mark.gpu
+DEV = "cuda:0"
+I32_MIN, I32_MAX = -(2 ** 31), 2 ** 31 - 1
+I64_MIN, I64_MAX = -(2 ** 63), 2 ** 63 - 1
+
+
+@pytest.fixture(scope="module")
+def ctx():
+    B.build()
+    c = jn.Context(0)
+    yield c
+    c.close()
+
+
+def canon(p):
+    if isinstance(p, torch.Tensor):
+        p = p.cpu().numpy()
+    return O.sort_pairs(p)
+
+
+def keys(n, lo, hi, seed, stream, dtype=torch.int32):
+    return datagen.uniform_keys(n, lo, hi, seed, stream, dtype=dtype)
+
+
+def with_edges(t, edges, seed):
+    t = t.clone()
+    if t.numel():
+        idx = datagen.uniform_int(len(edges), 0, t.numel(), seed, 77, dtype=torch.int64)
+        for i, v in zip(idx.tolist(), edges):
+            t[i] = v
+    return t
+
+
+# ------------------------------------------------------ config 1 (16K x 64K) --
+
+def test_uniform_16k_64k_hash_and_nested_loop(ctx):
+    r = keys(16384, 0, 65536, 0, 0)
+    s = keys(65536, 0, 65536, 0, 1)
+    rp, sp = datagen.row_ids(16384), datagen.row_ids(65536)
+    exp = canon(O.hash_join(r.numpy(), s.numpy(), rp.numpy(), sp.numpy()))
+    R = jn.table(r.to(DEV), payload=rp.to(DEV))
+    S = jn.table(s.to(DEV), payload=sp.to(DEV))
+    assert np.array_equal(canon(jn.jn_hash(ctx, R, S)), exp)
+    assert np.array_equal(canon(jn.jn_nested_loop(ctx, R, S)), exp)
+    assert jn.jn_count(ctx, jn.JN_ALGO_HASH, R, S) == exp.shape[0]
+    assert jn.jn_count(ctx, jn.JN_ALGO_NLJ, R, S) == exp.shape[0]
+    cnt, chk = O.equi_count_checksum(r.numpy(), s.numpy(), rp.numpy(), sp.numpy())
+    assert jn.jn_aggregate(ctx, jn.JN_ALGO_HASH, R, S) == (cnt, chk)
+    assert jn.jn_aggregate(ctx, jn.JN_ALGO_NLJ, R, S) == (cnt, chk)
+
+
+# --------------------------------------------------------- hash join cases --
+
+HASH_CASES = [
+    # (nr, ns, lo, hi, dtype)
+    (0, 100, 0, 10, torch.int32),
+    (100, 0, 0, 10, torch.int32),
+    (1, 1, 5, 6, torch.int32),
+    (64, 64, 7, 8, torch.int32),              # all keys equal: full Cartesian product
+    (1000, 3001, 0, 1 << 20, torch.int32),    # mostly misses
+    (4097, 12289, 0, 300, torch.int32),       # many duplicates, ragged sizes
+    (20000, 50001, I32_MIN, I32_MAX, torch.int32),
+    (5003, 7001, 0, 1000, torch.int64),
+    (30000, 20000, I64_MIN // 2, I64_MAX // 2, torch.int64),
+]
+
+
+@pytest.mark.parametrize("case", HASH_CASES)
+@pytest.mark.parametrize("pre", [0, 1])
+def test_hash_cases(ctx, case, pre):
+    nr, ns, lo, hi, dt = case
+    r = keys(nr, lo, hi, 3, 0, dt)
+    s = keys(ns, lo, hi, 3, 1, dt)
+    if dt == torch.int32:
+        r, s = with_edges(r, [I32_MIN, I32_MAX], 5), with_edges(s, [I32_MAX, I32_MIN], 6)
+    else:
+        r, s = with_edges(r, [I64_MIN, I64_MAX], 5), with_edges(s, [I64_MAX, I64_MIN], 6)
+    exp = canon(O.hash_join(r.numpy(), s.numpy()))
+    ctx.set_tuning(prefilter=pre)
+    try:
+        got = jn.jn_hash(ctx, jn.table(r.to(DEV)), jn.table(s.to(DEV)))
+    finally:
+        ctx.set_tuning(prefilter=-1)
+    assert np.array_equal(canon(got), exp)
+
+
+@pytest.mark.parametrize("bits", [(1, 1), (3, 2), (5, 0), (12, 6), (16, 8)])
+def test_hash_result_independent_of_partitioning(ctx, bits):
+    b, b1 = bits
+    r = keys(30000, 0, 9000, 8, 0)
+    s = keys(45000, 0, 9000, 8, 1)
+    exp = canon(O.hash_join(r.numpy(), s.numpy()))
+    ctx.set_tuning(radix_bits=b, radix_bits1=b1, prefilter=1)
+    try:
+        got = jn.jn_hash(ctx, jn.table(r.to(DEV)), jn.table(s.to(DEV)))
+    finally:
+        ctx.set_tuning(radix_bits=0, radix_bits1=0, prefilter=-1)
+    assert np.array_equal(canon(got), exp)
+
+
+def test_hash_unaligned_and_host_columns(ctx):
+    r = keys(10001, 0, 2000, 9, 0)
+    s = keys(20003, 0, 2000, 9, 1)
+    rp = datagen.uniform_int(10001, I32_MIN, I32_MAX, 9, 2)
+    sp = datagen.uniform_int(20003, I32_MIN, I32_MAX, 9, 3)
+    exp = canon(O.hash_join(r[1:].numpy(), s[3:].numpy(), rp[1:].numpy(), sp[3:].numpy()))
+    # device columns starting off a 16-byte boundary
+    rd, sd, rpd, spd = r.to(DEV), s.to(DEV), rp.to(DEV), sp.to(DEV)
+    got = jn.jn_hash(ctx, jn.table(rd[1:], payload=rpd[1:]), jn.table(sd[3:], payload=spd[3:]))
+    assert np.array_equal(canon(got), exp)
+    # host (pageable and pinned) columns, host output buffer
+    out = torch.empty((exp.shape[0] + 5, 2), dtype=torch.int32)
+    got = jn.jn_hash(ctx, jn.table(r[1:].clone(), payload=rp[1:].clone()),
+                     jn.table(s[3:].clone().pin_memory(), payload=sp[3:].clone()), out=out)
+    assert np.array_equal(canon(got), exp)
+
+
+def test_capacity_error_writes_nothing(ctx):
+    r = keys(3000, 0, 100, 10, 0)
+    s = keys(3000, 0, 100, 10, 1)
+    m = O.hash_join(r.numpy(), s.numpy(), count_only=True)
+    out = torch.full((m - 1, 2), -7, dtype=torch.int32, device=DEV)
+    with pytest.raises(jn.JoinError) as e:
+        jn.jn_hash(ctx, jn.table(r.to(DEV)), jn.table(s.to(DEV)), out=out)
+    assert e.value.status == jn.JN_ERR_CAPACITY and e.value.required == m
+    assert bool((out == -7).all())
+    out = torch.empty((m, 2), dtype=torch.int32, device=DEV)
+    got = jn.jn_hash(ctx, jn.table(r.to(DEV)), jn.table(s.to(DEV)), out=out)
+    assert np.array_equal(canon(got), canon(O.hash_join(r.numpy(), s.numpy())))
+
+
+def test_invalid_arguments(ctx):
+    r = keys(10, 0, 5, 1, 0)
+    s = keys(10, 0, 5, 1, 1, torch.int64)
+    with pytest.raises(jn.JoinError) as e:
+        jn.jn_hash(ctx, jn.table(r.to(DEV)), jn.table(s.to(DEV)))
+    assert e.value.status == jn.JN_ERR_INVALID
+    with pytest.raises(jn.JoinError) as e:
+        jn.jn_count(ctx, jn.JN_ALGO_HASH, jn.table(r.to(DEV)), jn.table(r.to(DEV)), jn.pred(jn.JN_LT))
+    assert e.value.status == jn.JN_ERR_UNSUPPORTED
+    with pytest.raises(jn.JoinError) as e:  # band needs key2
+        jn.jn_theta(ctx, jn.table(r.to(DEV)), jn.table(r.to(DEV)), jn.JN_LT, 3)
+    assert e.value.status == jn.JN_ERR_INVALID
+
+
+# --------------------------------------------------- nested loop predicates --
+
+@pytest.mark.parametrize("dt", [torch.int32, torch.int64])
+def test_nested_loop_all_predicates(ctx, dt):
+    nr, ns = 700, 2100
+    ra, rk = keys(nr, -20, 20, 11, 0, dt), keys(nr, -50, 50, 11, 1, dt)
+    sa, sk = keys(ns, -20, 20, 11, 2, dt), keys(ns, -50, 50, 11, 3, dt)
+    lo, hi = (I32_MIN, I32_MAX) if dt == torch.int32 else (I64_MIN, I64_MAX)
+    ra, sa = with_edges(ra, [lo, hi], 1), with_edges(sa, [hi, lo], 2)
+    rk, sk = with_edges(rk, [hi, lo], 3), with_edges(sk, [lo, hi], 4)
+    R = jn.table(ra.to(DEV), rk.to(DEV))
+    S = jn.table(sa.to(DEV), sk.to(DEV))
+    for op_a in range(7):
+        for op_k in range(7):
+            exp = O.nested_loop(ra.numpy(), sa.numpy(), rk.numpy(), sk.numpy(), op_a=op_a, op_k=op_k,
+                                count_only=True)
+            got = jn.jn_count(ctx, jn.JN_ALGO_NLJ, R, S, jn.pred(op_a, op_k))
+            assert got == exp, (op_a, op_k)
+    for op_a, op_k, band in [(jn.JN_LT, 0, 5), (jn.JN_NE, 0, 0), (jn.JN_GE, 0, 2 ** 40), (jn.JN_EQ, 5, -1),
+                             (jn.JN_ANY, jn.JN_GT, -1), (jn.JN_LE, jn.JN_NE, -1)]:
+        exp = canon(O.nested_loop(ra.numpy(), sa.numpy(), rk.numpy(), sk.numpy(), op_a=op_a,
+                                  op_k=op_k, band=band))
+        got = jn.jn_nested_loop(ctx, R, S, jn.pred(op_a, op_k, band))
+        assert np.array_equal(canon(got), exp), (op_a, op_k, band)
+        c, h = jn.jn_aggregate(ctx, jn.JN_ALGO_NLJ, R, S, jn.pred(op_a, op_k, band))
+        assert c == exp.shape[0] and h == O.checksum_pairs(exp)
+
+
+def test_nested_loop_conjunctive_band_64k_scaled(ctx):
+    # the two-column band predicate of the 64K x 1M tiled workload, at 8K x 64K
+    nr, ns, w = 8192, 65536, 24414 // 16
+    ra, rk = datagen.band_columns(nr, 24, seed=4, stream=0)
+    sa, sk = datagen.band_columns(ns, 24, seed=4, stream=1)
+    exp = canon(O.band_join_sorted(ra.numpy(), rk.numpy(), sa.numpy(), sk.numpy(), O.LT, w))
+    got = jn.jn_nested_loop(ctx, jn.table(ra.to(DEV), rk.to(DEV)), jn.table(sa.to(DEV), sk.to(DEV)),
+                            jn.pred(jn.JN_LT, jn.JN_ANY, w))
+    assert np.array_equal(canon(got), exp)
+
+
+# -------------------------------------------------------------- theta / band --
+
+@pytest.mark.parametrize("op", [jn.JN_LT, jn.JN_LE, jn.JN_GT, jn.JN_GE, jn.JN_EQ, jn.JN_NE, jn.JN_ANY])
+def test_band_join_all_ops(ctx, op):
+    nr, ns, w = 1 << 13, 1 << 16, 40
+    ra, rk = datagen.band_columns(nr, 16, seed=5, stream=0)
+    sa, sk = datagen.band_columns(ns, 16, seed=5, stream=1)
+    exp = canon(O.band_join_sorted(ra.numpy(), rk.numpy(), sa.numpy(), sk.numpy(), op, w))
+    R = jn.table(ra.to(DEV), rk.to(DEV))
+    S = jn.table(sa.to(DEV), sk.to(DEV))
+    got = jn.jn_theta(ctx, R, S, op, w)
+    assert np.array_equal(canon(got), exp)
+    c, h = jn.jn_aggregate(ctx, jn.JN_ALGO_THETA, R, S, jn.pred(op, jn.JN_ANY, w))
+    assert c == exp.shape[0] and h == O.checksum_pairs(exp)
+
+
+@pytest.mark.parametrize("band", [0, 1, 1000, 70000, 2 ** 33])
+@pytest.mark.parametrize("groups", [0, 2, 10])
+def test_band_join_widths_and_groups(ctx, band, groups):
+    nr, ns = 3000, 9000
+    ra, rk = keys(nr, 0, 100, 6, 0), keys(nr, -40000, 40000, 6, 1)
+    sa, sk = keys(ns, 0, 100, 6, 2), keys(ns, -40000, 40000, 6, 3)
+    rk, sk = with_edges(rk, [I32_MIN, I32_MAX], 8), with_edges(sk, [I32_MAX, I32_MIN], 9)
+    exp = canon(O.band_join_sorted(ra.numpy(), rk.numpy(), sa.numpy(), sk.numpy(), O.GE, band))
+    ctx.set_tuning(theta_groups=groups)
+    try:
+        got = jn.jn_theta(ctx, jn.table(ra.to(DEV), rk.to(DEV)), jn.table(sa.to(DEV), sk.to(DEV)),
+                          jn.JN_GE, band)
+    finally:
+        ctx.set_tuning(theta_groups=0)
+    assert np.array_equal(canon(got), exp)
+
+
+@pytest.mark.parametrize("op", [jn.JN_LT, jn.JN_LE, jn.JN_GT, jn.JN_GE, jn.JN_EQ, jn.JN_NE, jn.JN_ANY])
+@pytest.mark.parametrize("dt", [torch.int32, torch.int64])
+def test_one_column_theta_regions(ctx, op, dt):
+    nr, ns = 900, 1300
+    r = keys(nr, -3000, 3000, 12, 0, dt)
+    s = keys(ns, -2000, 5000, 12, 1, dt)
+    exp = canon(O.nested_loop(r.numpy(), s.numpy(), op_a=op))
+    R, S = jn.table(r.to(DEV)), jn.table(s.to(DEV))
+    got = jn.jn_theta(ctx, R, S, op, -1)
+    assert np.array_equal(canon(got), exp)
+    c, h = jn.jn_aggregate(ctx, jn.JN_ALGO_THETA, R, S, jn.pred(op, jn.JN_ANY, -1))
+    assert c == exp.shape[0] and h == O.checksum_pairs(exp)
