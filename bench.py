@@ -45,14 +45,16 @@ def peaks():
 
 # ------------------------------------------------------------- workloads --
 
-def make_workload(name, theta, device, small=False):
+def make_workload(name, theta, device, small=False, rows_log2=0):
     from paper_1904_11201_gb300 import datagen as D
     if name in ("hash", "hash_int64"):
         i64 = name == "hash_int64"
         n = (1 << 27) if i64 else (1 << 28)
+        dbits = 28
         if small:
-            n = 1 << 20
-        dbits = 28 if not small else 20
+            n, dbits = 1 << 20, 20
+        if rows_log2:
+            n, dbits = 1 << rows_log2, rows_log2
         dt = torch.int64 if i64 else torch.int32
         cdf = None
         if theta != 0:
@@ -120,7 +122,7 @@ def algorithmic_bytes(kind, info, nr, ns, m, ksize):
 
 
 class ClockSampler:
-    FIELDS = "index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active," \
+    FIELDS = "timestamp,index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active," \
              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown," \
              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap"
 
@@ -128,6 +130,7 @@ class ClockSampler:
         self.index = index
         self.proc = None
         self.lines = []
+        self.window = None
 
     def start(self):
         try:
@@ -142,7 +145,11 @@ class ClockSampler:
 
     def _read(self):
         for line in self.proc.stdout:
-            self.lines.append(line.strip())
+            self.lines.append((time.time(), line.strip()))
+
+    def mark(self, t0, t1):
+        """Keep only samples that arrived inside [t0, t1] (plus one interval)."""
+        self.window = (t0, t1 + 0.25)
 
     def stop(self):
         if not self.proc:
@@ -153,17 +160,19 @@ class ClockSampler:
         except Exception:
             self.proc.kill()
         mhz, mx, reasons = [], None, set()
-        for ln in self.lines:
+        for ts, ln in self.lines:
+            if self.window and not (self.window[0] <= ts <= self.window[1]):
+                continue
             f = [x.strip() for x in ln.split(",")]
-            if len(f) < 9:
+            if len(f) < 10:
                 continue
             try:
-                mhz.append(float(f[1]))
-                mx = float(f[2])
+                mhz.append(float(f[2]))
+                mx = float(f[3])
             except ValueError:
                 continue
             for name, v in zip(["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"],
-                               f[5:9]):
+                               f[6:10]):
                 if v.lower() == "active":
                     reasons.add(name)
         if not mhz:
@@ -275,12 +284,16 @@ def reference_arm(args, world, rank):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--steps", type=int, default=30)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="jn")
     ap.add_argument("--workload", default="hash")
     ap.add_argument("--theta", type=float, default=0.0)
     ap.add_argument("--small", action="store_true", help="small inputs (profiling runs)")
+    ap.add_argument("--rows-log2", type=int, default=0,
+                    help="hash workloads: 2^N rows per table over a 2^N key domain (profiling runs)")
+    ap.add_argument("--prefilter", type=int, default=-1, help="-1 auto, 0 off, 1 on")
+    ap.add_argument("--radix-bits", type=int, default=0)
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     args = ap.parse_args()
@@ -288,7 +301,9 @@ def main():
     if args.impl == "reference":
         reference_arm(args, world, rank)
         return
-    args.warmup = max(args.warmup, 3) if not args.small else args.warmup
+    profiling_run = args.small or args.rows_log2 > 0
+    if not profiling_run:
+        args.warmup = max(args.warmup, 3)
 
     from paper_1904_11201_gb300 import build as B
     from paper_1904_11201_gb300 import jn
@@ -299,7 +314,9 @@ def main():
     dev = "cuda:%d" % local
     stream = torch.cuda.current_stream(local)
     ctx = jn.Context(local, stream)
-    w = make_workload(args.workload, args.theta, dev, args.small)
+    if args.prefilter != -1 or args.radix_bits:
+        ctx.set_tuning(prefilter=args.prefilter, radix_bits=args.radix_bits)
+    w = make_workload(args.workload, args.theta, dev, args.small, args.rows_log2)
     (rk, rk2, rp), (sk, sk2, sp) = w["R"], w["S"]
     R = jn.table(rk, rk2, rp)
     S = jn.table(sk, sk2, sp)
@@ -307,6 +324,8 @@ def main():
     ksize = rk.element_size()
     torch.cuda.synchronize()
 
+    clk = ClockSampler(local)
+    clk.start()
     for _ in range(args.warmup):
         out = run_step(jn, ctx, w, R, S)
         m = out.shape[0]
@@ -316,10 +335,9 @@ def main():
     ctx.reset_stats()
     ctx.set_profiling(True)
     l0 = ctx.launch_count()
-    clk = ClockSampler(local)
-    clk.start()
     barrier(world)
     torch.cuda.synchronize()
+    tw0 = time.time()
     e0 = torch.cuda.Event(enable_timing=True)
     e1 = torch.cuda.Event(enable_timing=True)
     e0.record(stream)
@@ -328,6 +346,7 @@ def main():
         del out
     e1.record(stream)
     torch.cuda.synchronize()
+    clk.mark(tw0, time.time())
     barrier(world)
     clocks = clk.stop()
     launches = ctx.launch_count() - l0

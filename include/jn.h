@@ -90,7 +90,7 @@ typedef struct {
  * never depends on them. */
 typedef struct {
     int32_t prefilter;     /* -1 auto, 0 off, 1 on: Algorithm 1's common-key filter     */
-    int32_t radix_bits;    /* total partition bits of the hash join (0 = auto, <= 16)   */
+    int32_t radix_bits;    /* total partition bits of the hash join (0 = auto, <= 20)   */
     int32_t radix_bits1;   /* bits of the first partition pass (0 = auto)               */
     int32_t filter_bits;   /* log2 of the key-presence bitmap size (0 = auto, <= 30)    */
     int32_t heavy;         /* -1 auto, 0 off, 1 on: frequent keys joined as cross products */

@@ -61,6 +61,7 @@ struct jn_ctx {
     cudaMemPool_t pool = nullptr;
     jn_tuning tune{};
     uint64_t* h_small = nullptr;  // pinned host words for count read-back
+    unsigned int* d_err = nullptr;  // device error word (bounded waits that ran out)
     bool profiling = false;
     std::vector<jnx::PendingTiming> pending;
     std::vector<cudaEvent_t> spare_events;

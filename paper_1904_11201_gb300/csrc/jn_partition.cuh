@@ -10,6 +10,7 @@
 // consecutive tiles land next to each other, so partial lines merge in L2.
 #pragma once
 
+#include "jn_async.cuh"
 #include "jn_common.cuh"
 
 namespace jnx {
@@ -47,6 +48,38 @@ struct RangeDigit {
     __device__ __forceinline__ uint32_t operator()(K k) const {
         return (uint32_t)(((uint64_t)((int64_t)k - (int64_t)p->lo)) >> p->shift);
     }
+};
+
+// ---------------------------------------------------------------- rows --
+// Partitioned intermediates are stored as rows (array of structs): the key,
+// an optional second column and the payload of one tuple sit together, so a
+// tuple moves with one load and one store and a tile with one bulk copy.
+template <typename K, bool HB>
+struct Row;
+template <>
+struct __align__(8) Row<int32_t, false> {
+    int32_t key;
+    int32_t pay;
+};
+template <>
+struct __align__(16) Row<int64_t, false> {
+    int64_t key;
+    int32_t pay;
+    int32_t pad;
+};
+template <>
+struct __align__(16) Row<int32_t, true> {
+    int32_t key;
+    int32_t b;
+    int32_t pay;
+    int32_t pad;
+};
+template <>
+struct __align__(8) Row<int64_t, true> {
+    int64_t key;
+    int64_t b;
+    int32_t pay;
+    int32_t pad;
 };
 
 // ------------------------------------------------------ presence + hist --
@@ -138,7 +171,7 @@ __device__ __forceinline__ int find_segment(const uint64_t* tp, int nseg, uint64
 
 // --------------------------------------------------- per-segment hist --
 // Digit histogram of every segment: hist[seg * nd + digit].  Persistent
-// blocks claim tiles from *work.
+// blocks take tiles round-robin; the tile prefix is held in shared memory.
 template <typename K, typename Digit>
 __global__ void __launch_bounds__(SC_T)
 k_seg_hist(const K* __restrict__ keys, const uint64_t* __restrict__ seg_begin,
@@ -146,88 +179,286 @@ k_seg_hist(const K* __restrict__ keys, const uint64_t* __restrict__ seg_begin,
            int nseg, Digit dg, int nd, unsigned long long* __restrict__ hist,
            unsigned int* __restrict__ work) {
     extern __shared__ uint32_t s_h[];
-    __shared__ unsigned int s_tile;
-    const uint64_t ntiles = tile_prefix[nseg];
-    while (true) {
-        if (threadIdx.x == 0) s_tile = atomicAdd(work, 1u);
-        for (int i = threadIdx.x; i < nd; i += blockDim.x) s_h[i] = 0;
-        __syncthreads();
-        const uint64_t t = s_tile;
-        if (t >= ntiles) break;
-        const int seg = find_segment(tile_prefix, nseg, t);
-        const uint64_t off = (t - tile_prefix[seg]) * SC_TILE;
+    __shared__ uint64_t s_tp[SC_FMAX + 1];
+    for (int i = threadIdx.x; i <= nseg; i += blockDim.x) s_tp[i] = tile_prefix[i];
+    for (int i = threadIdx.x; i < nd; i += blockDim.x) s_h[i] = 0;
+    __syncthreads();
+    const uint64_t ntiles = s_tp[nseg];
+    int seg_held = -1;
+    for (uint64_t t = blockIdx.x; t < ntiles; t += gridDim.x) {
+        const int seg = find_segment(s_tp, nseg, t);
+        if (seg != seg_held) {
+            // flush the counts of the previous segment before switching
+            if (seg_held >= 0) {
+                __syncthreads();
+                for (int i = threadIdx.x; i < nd; i += blockDim.x) {
+                    if (s_h[i]) atomicAdd(&hist[(uint64_t)seg_held * nd + i], (unsigned long long)s_h[i]);
+                    s_h[i] = 0;
+                }
+                __syncthreads();
+            }
+            seg_held = seg;
+        }
+        const uint64_t off = (t - s_tp[seg]) * SC_TILE;
         const uint64_t beg = seg_begin[seg] + off;
         const int cnt = (int)min((uint64_t)SC_TILE, seg_count[seg] - off);
         for (int i = threadIdx.x; i < cnt; i += blockDim.x) atomicAdd(&s_h[dg(keys[beg + i])], 1u);
-        __syncthreads();
-        for (int i = threadIdx.x; i < nd; i += blockDim.x)
-            if (s_h[i]) atomicAdd(&hist[(uint64_t)seg * nd + i], (unsigned long long)s_h[i]);
-        __syncthreads();
     }
+    __syncthreads();
+    if (seg_held >= 0)
+        for (int i = threadIdx.x; i < nd; i += blockDim.x)
+            if (s_h[i]) atomicAdd(&hist[(uint64_t)seg_held * nd + i], (unsigned long long)s_h[i]);
+}
+
+// Input of a partition pass: column buffers (the caller's table) or rows
+// (the output of an earlier pass).
+template <typename K, bool HB>
+struct PartIn {
+    const K* key;           // columns (when rows == NULL)
+    const K* key_b;
+    const int32_t* pay;     // NULL = row index
+    const Row<K, HB>* rows; // rows (when not NULL)
+    uint64_t rows_ok;       // rows that may be read (allocation size)
+};
+
+// Digit histogram of every segment of a row array (see k_seg_hist).
+template <typename R, typename Digit>
+__global__ void __launch_bounds__(SC_T)
+k_seg_hist_rows(const R* __restrict__ rows, const uint64_t* __restrict__ seg_begin,
+                const uint64_t* __restrict__ seg_count, const uint64_t* __restrict__ tile_prefix, int nseg,
+                Digit dg, int nd, unsigned long long* __restrict__ hist) {
+    extern __shared__ uint32_t s_h[];
+    __shared__ uint64_t s_tp[SC_FMAX + 1];
+    for (int i = threadIdx.x; i <= nseg; i += blockDim.x) s_tp[i] = tile_prefix[i];
+    for (int i = threadIdx.x; i < nd; i += blockDim.x) s_h[i] = 0;
+    __syncthreads();
+    const uint64_t ntiles = s_tp[nseg];
+    int seg_held = -1;
+    for (uint64_t t = blockIdx.x; t < ntiles; t += gridDim.x) {
+        const int seg = find_segment(s_tp, nseg, t);
+        if (seg != seg_held) {
+            if (seg_held >= 0) {
+                __syncthreads();
+                for (int i = threadIdx.x; i < nd; i += blockDim.x) {
+                    if (s_h[i]) atomicAdd(&hist[(uint64_t)seg_held * nd + i], (unsigned long long)s_h[i]);
+                    s_h[i] = 0;
+                }
+                __syncthreads();
+            }
+            seg_held = seg;
+        }
+        const uint64_t off = (t - s_tp[seg]) * SC_TILE;
+        const uint64_t beg = seg_begin[seg] + off;
+        const int cnt = (int)min((uint64_t)SC_TILE, seg_count[seg] - off);
+        for (int i = threadIdx.x; i < cnt; i += blockDim.x) atomicAdd(&s_h[dg(rows[beg + i].key)], 1u);
+    }
+    __syncthreads();
+    if (seg_held >= 0)
+        for (int i = threadIdx.x; i < nd; i += blockDim.x)
+            if (s_h[i]) atomicAdd(&hist[(uint64_t)seg_held * nd + i], (unsigned long long)s_h[i]);
 }
 
 // ---------------------------------------------------------------- scatter --
 // Moves the rows of every segment into digit order.  `cursor[seg * nd + d]`
 // holds the next free output row of (segment, digit) and is advanced by one
 // atomic per tile and digit.  With FILTER, a row is dropped unless its key's
-// bit is set in `other` (the presence bitmap of the other table).  With
-// key_b, a second column is carried along.  A NULL payload means "row
-// index" (the input row number).
-template <typename K, bool FILTER, typename Digit>
-__global__ void __launch_bounds__(SC_T)
-k_scatter(const K* __restrict__ keys, const K* __restrict__ key_b, const int32_t* __restrict__ pays,
-          const uint64_t* __restrict__ seg_begin, const uint64_t* __restrict__ seg_count,
+// bit is set in `other` (the presence bitmap of the other table).
+//
+// Input tiles are staged in shared memory by 1-D TMA bulk copies: as soon as
+// a tile has been read into registers, thread 0 starts the copy of the block's
+// next tile, so its load overlaps the digit sort and write-out of this one.
+// Tiles whose widened 16-byte span would pass `rows_ok` (or whose base is not
+// 16-byte aligned) are read with plain loads instead.
+struct TileDesc {
+    unsigned long long beg;
+    int cnt;
+    int seg;
+    int valid;
+    int tma;
+    int koff;  // element offset of row `beg` in the staged key column / rows
+    int boff;
+    int poff;
+};
+
+template <typename K, bool HB>
+struct ScatterSmem {
+    using R = Row<K, HB>;
+    static constexpr int GK = SC_TILE + 32 / (int)sizeof(K);  // staged key column (and b column)
+    static constexpr int GP = SC_TILE + 8;                    // staged payload column
+    static constexpr int GR = SC_TILE + 16;                   // staged rows (widened)
+    __host__ __device__ static constexpr size_t staging_bytes() {
+        return ((((size_t)GK * sizeof(K) * (HB ? 2 : 1) + (size_t)GP * 4) > (size_t)GR * sizeof(R)
+                     ? ((size_t)GK * sizeof(K) * (HB ? 2 : 1) + (size_t)GP * 4)
+                     : (size_t)GR * sizeof(R)) +
+                127) &
+               ~(size_t)127;
+    }
+    __host__ __device__ static constexpr size_t bytes() {
+        return staging_bytes() + (size_t)SC_TILE * sizeof(R) + (size_t)SC_TILE * 2 + (size_t)SC_FMAX * 16;
+    }
+};
+
+// Rows of tile t: segment, first row and row count.  `tp` is the tile
+// prefix held in shared memory.
+__device__ __forceinline__ void tile_rows(const uint64_t* tp, int nseg, uint64_t t,
+                                          const uint64_t* __restrict__ seg_begin,
+                                          const uint64_t* __restrict__ seg_count, TileDesc* d) {
+    const int seg = find_segment(tp, nseg, t);
+    const uint64_t off = (t - tp[seg]) * SC_TILE;
+    d->seg = seg;
+    d->beg = seg_begin[seg] + off;
+    d->cnt = (int)min((uint64_t)SC_TILE, seg_count[seg] - off);
+}
+
+// Byte span [beg*E, (beg+cnt)*E) widened to 16-byte boundaries; false when
+// the base is unaligned or the widened end passes the readable bytes.
+__device__ __forceinline__ bool byte_span(const void* base, uint64_t beg, uint64_t cnt, uint64_t e,
+                                          uint64_t rows_ok, uint64_t* b0, uint32_t* bytes) {
+    const uint64_t lo = (beg * e) & ~15ull;
+    const uint64_t hi = ((beg + cnt) * e + 15) & ~15ull;
+    if ((((uintptr_t)base) & 15) != 0 || hi > rows_ok * e) return false;
+    *b0 = lo;
+    *bytes = (uint32_t)(hi - lo);
+    return true;
+}
+
+// Starts the bulk copy of a tile into the staging buffer (thread 0 only).
+template <typename K, bool HB>
+__device__ __forceinline__ void scatter_issue(TileDesc* d, const PartIn<K, HB>& in, unsigned char* stage,
+                                              uint64_t* bar) {
+    using SM = ScatterSmem<K, HB>;
+    d->tma = 0;
+    if (in.rows) {
+        uint64_t b0;
+        uint32_t nb;
+        if (!byte_span(in.rows, d->beg, d->cnt, sizeof(Row<K, HB>), in.rows_ok, &b0, &nb)) return;
+        d->tma = 1;
+        d->koff = (int)((d->beg * sizeof(Row<K, HB>) - b0));  // byte offset
+        fence_proxy_async();
+        mbar_arrive_expect_tx(bar, nb);
+        tma_load_1d(stage, reinterpret_cast<const unsigned char*>(in.rows) + b0, nb, bar);
+        return;
+    }
+    uint64_t bk = 0, bb = 0, bp = 0;
+    uint32_t nk = 0, nbb = 0, np = 0;
+    bool ok = byte_span(in.key, d->beg, d->cnt, sizeof(K), in.rows_ok, &bk, &nk);
+    if (ok && HB) ok = byte_span(in.key_b, d->beg, d->cnt, sizeof(K), in.rows_ok, &bb, &nbb);
+    if (ok && in.pay) ok = byte_span(in.pay, d->beg, d->cnt, 4, in.rows_ok, &bp, &np);
+    if (!ok) return;
+    d->tma = 1;
+    d->koff = (int)(d->beg - bk / sizeof(K));
+    d->boff = (int)(d->beg - bb / sizeof(K));
+    d->poff = (int)(d->beg - bp / 4);
+    K* gk = reinterpret_cast<K*>(stage);
+    K* gb = gk + SM::GK;
+    int32_t* gp = reinterpret_cast<int32_t*>(gb + (HB ? SM::GK : 0));
+    fence_proxy_async();
+    mbar_arrive_expect_tx(bar, nk + nbb + np);
+    tma_load_1d(gk, reinterpret_cast<const unsigned char*>(in.key) + bk, nk, bar);
+    if (HB) tma_load_1d(gb, reinterpret_cast<const unsigned char*>(in.key_b) + bb, nbb, bar);
+    if (in.pay) tma_load_1d(gp, reinterpret_cast<const unsigned char*>(in.pay) + bp, np, bar);
+}
+
+template <typename K, bool HB, bool FILTER, typename Digit>
+__global__ void __launch_bounds__(SC_T, 2)
+k_scatter(PartIn<K, HB> in, const uint64_t* __restrict__ seg_begin, const uint64_t* __restrict__ seg_count,
           const uint64_t* __restrict__ tile_prefix, int nseg, Digit dg, int nd,
-          const uint32_t* __restrict__ other, uint32_t fmask,
-          unsigned long long* __restrict__ cursor, K* __restrict__ out_keys,
-          K* __restrict__ out_key_b, int32_t* __restrict__ out_pays, unsigned int* __restrict__ work) {
-    extern __shared__ __align__(16) unsigned char smem[];
-    K* s_key = reinterpret_cast<K*>(smem);
-    K* s_kb = s_key + SC_TILE;                                   // used only with key_b
-    int32_t* s_pay = reinterpret_cast<int32_t*>(s_kb + (key_b ? SC_TILE : 0));
-    uint16_t* s_dig = reinterpret_cast<uint16_t*>(s_pay + SC_TILE);
+          const uint32_t* __restrict__ other, uint32_t fmask, unsigned long long* __restrict__ cursor,
+          Row<K, HB>* __restrict__ out, unsigned int* __restrict__ err) {
+    using SM = ScatterSmem<K, HB>;
+    using R = Row<K, HB>;
+    extern __shared__ __align__(128) unsigned char smem[];
+    unsigned char* stage = smem;
+    R* s_row = reinterpret_cast<R*>(smem + SM::staging_bytes());
+    uint16_t* s_dig = reinterpret_cast<uint16_t*>(s_row + SC_TILE);
     uint32_t* s_cnt = reinterpret_cast<uint32_t*>(s_dig + SC_TILE);
     uint32_t* s_start = s_cnt + SC_FMAX;
-    unsigned long long* s_base = reinterpret_cast<unsigned long long*>(s_start + SC_FMAX);
+    unsigned long long* s_delta = reinterpret_cast<unsigned long long*>(s_start + SC_FMAX);
     __shared__ uint32_t tmp[33];
-    __shared__ unsigned int s_tile;
+    __shared__ TileDesc desc[2];
+    __shared__ __align__(8) uint64_t bar;
+    __shared__ uint64_t s_tp[SC_FMAX + 1];
 
-    const uint64_t ntiles = tile_prefix[nseg];
+    // Tiles are dealt round-robin: block b takes tiles b, b + grid, ...
+    for (int i = threadIdx.x; i <= nseg; i += SC_T) s_tp[i] = tile_prefix[i];
+    for (int i = threadIdx.x; i < nd; i += SC_T) s_cnt[i] = 0;
+    __syncthreads();
+    const uint64_t ntiles = s_tp[nseg];
+    uint64_t t = blockIdx.x;
+    if (threadIdx.x == 0) {
+        mbar_init(&bar, 1);
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+        desc[0].valid = t < ntiles;
+        if (t < ntiles) {
+            tile_rows(s_tp, nseg, t, seg_begin, seg_count, &desc[0]);
+            scatter_issue<K, HB>(&desc[0], in, stage, &bar);
+        }
+    }
+    __syncthreads();
+    int cur = 0;
+    uint32_t phase = 0;
+    const K* gk = reinterpret_cast<const K*>(stage);
+    const K* gb = gk + SM::GK;
+    const int32_t* gp = reinterpret_cast<const int32_t*>(gb + (HB ? SM::GK : 0));
     while (true) {
-        if (threadIdx.x == 0) s_tile = atomicAdd(work, 1u);
-        for (int i = threadIdx.x; i < nd; i += SC_T) s_cnt[i] = 0;
-        __syncthreads();
-        const uint64_t t = s_tile;
-        if (t >= ntiles) break;
-        const int seg = find_segment(tile_prefix, nseg, t);
-        const uint64_t off = (t - tile_prefix[seg]) * SC_TILE;
-        const uint64_t beg = seg_begin[seg] + off;
-        const int cnt = (int)min((uint64_t)SC_TILE, seg_count[seg] - off);
+        const TileDesc d = desc[cur];
+        if (!d.valid) break;
+        // look up the next tile now; its copy starts once the staging is free
+        const uint64_t tn = t + gridDim.x;
+        TileDesc dn;
+        dn.valid = tn < ntiles;
+        if (threadIdx.x == 0 && dn.valid) tile_rows(s_tp, nseg, tn, seg_begin, seg_count, &dn);
+        bool ok = true;
+        if (d.tma) ok = mbar_wait(&bar, phase, err);
+        if (__syncthreads_or(!ok)) {
+            if (d.tma) mbar_wait(&bar, phase, nullptr);  // let the copy in flight land before exiting
+            break;
+        }
+        if (d.tma) phase ^= 1u;
+        const uint64_t beg = d.beg;
+        const int cnt = d.cnt;
 
-        K k[SC_IPT];
-        K kb[SC_IPT];
-        int32_t p[SC_IPT];
-        uint32_t d[SC_IPT];
-        uint32_t r[SC_IPT];
+        R v[SC_IPT];
+        uint32_t dd[SC_IPT];
+        uint32_t rk[SC_IPT];
 #pragma unroll
         for (int j = 0; j < SC_IPT; j++) {
             const int i = j * SC_T + threadIdx.x;
-            d[j] = SC_DROP;
+            dd[j] = SC_DROP;
             if (i < cnt) {
-                k[j] = __ldcs(keys + beg + i);
-                if (key_b) kb[j] = __ldcs(key_b + beg + i);
-                p[j] = pays ? __ldcs(pays + beg + i) : (int32_t)(beg + i);
-                bool keep = true;
-                if (FILTER) {
-                    const uint32_t b = fbits(k[j]) & fmask;
-                    keep = (__ldg(other + (b >> 5)) >> (b & 31)) & 1u;
+                if (in.rows) {
+                    v[j] = d.tma ? *reinterpret_cast<const R*>(stage + d.koff + (size_t)i * sizeof(R))
+                                 : in.rows[beg + i];
+                } else if (d.tma) {
+                    v[j].key = gk[d.koff + i];
+                    if constexpr (HB) v[j].b = gb[d.boff + i];
+                    v[j].pay = in.pay ? gp[d.poff + i] : (int32_t)(beg + i);
+                } else {
+                    v[j].key = in.key[beg + i];
+                    if constexpr (HB) v[j].b = in.key_b[beg + i];
+                    v[j].pay = in.pay ? in.pay[beg + i] : (int32_t)(beg + i);
                 }
-                if (keep) d[j] = dg(k[j]);
             }
         }
 #pragma unroll
-        for (int j = 0; j < SC_IPT; j++)
-            r[j] = (d[j] != SC_DROP) ? atomicAdd(&s_cnt[d[j]], 1u) : 0u;
+        for (int j = 0; j < SC_IPT; j++) {
+            const int i = j * SC_T + threadIdx.x;
+            if (i < cnt) {
+                bool keep = true;
+                if (FILTER) {
+                    const uint32_t b = fbits(v[j].key) & fmask;
+                    keep = (__ldg(other + (b >> 5)) >> (b & 31)) & 1u;
+                }
+                if (keep) dd[j] = dg(v[j].key);
+            }
+        }
+        __syncthreads();  // the staging buffer is free: start the next tile's copy
+        if (threadIdx.x == 0) {
+            if (dn.valid) scatter_issue<K, HB>(&dn, in, stage, &bar);
+            desc[cur ^ 1] = dn;
+        }
+#pragma unroll
+        for (int j = 0; j < SC_IPT; j++) rk[j] = (dd[j] != SC_DROP) ? atomicAdd(&s_cnt[dd[j]], 1u) : 0u;
         __syncthreads();
         // exclusive scan of the digit counts; nd <= SC_FMAX = 2 * SC_T
         uint32_t c0 = 0, c1 = 0;
@@ -235,41 +466,36 @@ k_scatter(const K* __restrict__ keys, const K* __restrict__ key_b, const int32_t
         if (i0 < nd) c0 = s_cnt[i0];
         if (i1 < nd) c1 = s_cnt[i1];
         uint32_t total;
-        uint32_t pre = block_excl_scan(c0 + c1, tmp, &total);
+        const uint32_t pre = block_excl_scan(c0 + c1, tmp, &total);
         if (i0 < nd) {
             s_start[i0] = pre;
-            if (c0) s_base[i0] = atomicAdd(&cursor[(uint64_t)seg * nd + i0], (unsigned long long)c0);
+            if (c0) s_delta[i0] = atomicAdd(&cursor[(uint64_t)d.seg * nd + i0], (unsigned long long)c0) - pre;
         }
         if (i1 < nd) {
             s_start[i1] = pre + c0;
-            if (c1) s_base[i1] = atomicAdd(&cursor[(uint64_t)seg * nd + i1], (unsigned long long)c1);
+            if (c1) s_delta[i1] = atomicAdd(&cursor[(uint64_t)d.seg * nd + i1], (unsigned long long)c1) - (pre + c0);
         }
         __syncthreads();
 #pragma unroll
         for (int j = 0; j < SC_IPT; j++) {
-            if (d[j] != SC_DROP) {
-                const uint32_t pos = s_start[d[j]] + r[j];
-                s_key[pos] = k[j];
-                if (key_b) s_kb[pos] = kb[j];
-                s_pay[pos] = p[j];
-                s_dig[pos] = (uint16_t)d[j];
+            if (dd[j] != SC_DROP) {
+                const uint32_t pos = s_start[dd[j]] + rk[j];
+                s_row[pos] = v[j];
+                s_dig[pos] = (uint16_t)dd[j];
             }
         }
         __syncthreads();
-        for (uint32_t pos = threadIdx.x; pos < total; pos += SC_T) {
-            const uint32_t dd = s_dig[pos];
-            const unsigned long long o = s_base[dd] + (pos - s_start[dd]);
-            out_keys[o] = s_key[pos];
-            if (key_b) out_key_b[o] = s_kb[pos];
-            out_pays[o] = s_pay[pos];
-        }
+        for (uint32_t pos = threadIdx.x; pos < total; pos += SC_T) out[s_delta[s_dig[pos]] + pos] = s_row[pos];
+        for (int i = threadIdx.x; i < nd; i += SC_T) s_cnt[i] = 0;
         __syncthreads();
+        cur ^= 1;
+        t = tn;
     }
 }
 
-template <typename K>
-inline size_t scatter_smem(bool with_b) {
-    return (size_t)SC_TILE * (sizeof(K) * (with_b ? 2 : 1) + 4 + 2) + SC_FMAX * 8 + SC_FMAX * 8;
+template <typename K, bool HB>
+inline size_t scatter_smem() {
+    return ScatterSmem<K, HB>::bytes();
 }
 
 // Single-block setup for one-segment passes: seg_begin = 0, count = n.

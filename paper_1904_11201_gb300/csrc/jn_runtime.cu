@@ -77,10 +77,18 @@ void ensure_smem(const void* fn, size_t smem) {
 }
 
 jn_status read_back(jn_ctx* c, const uint64_t* dsrc, uint64_t* hdst, int n) {
-    JN_CUDA(c, cudaMemcpyAsync(c->h_small, dsrc, sizeof(uint64_t) * n, cudaMemcpyDeviceToHost,
+    if (n > 0)
+        JN_CUDA(c, cudaMemcpyAsync(c->h_small, dsrc, sizeof(uint64_t) * n, cudaMemcpyDeviceToHost,
+                                   c->stream));
+    JN_CUDA(c, cudaMemcpyAsync(c->h_small + 63, c->d_err, sizeof(unsigned int), cudaMemcpyDeviceToHost,
                                c->stream));
     JN_CUDA(c, cudaStreamSynchronize(c->stream));
     for (int i = 0; i < n; i++) hdst[i] = c->h_small[i];
+    const unsigned int e = (unsigned int)(c->h_small[63] & 0xffffffffu);
+    if (e != 0) {
+        cudaMemsetAsync(c->d_err, 0, sizeof(unsigned int), c->stream);
+        return fail(c, (jn_status)e, "a bounded device-side wait ran out");
+    }
     return JN_OK;
 }
 
@@ -258,9 +266,13 @@ jn_status jn_create(jn_ctx** out, int device, void* stream) {
         e = cudaMemPoolSetAttribute(c->pool, cudaMemPoolAttrReleaseThreshold, &keep);
     }
     if (e == cudaSuccess) e = cudaMallocHost((void**)&c->h_small, 64 * sizeof(uint64_t));
+    if (e == cudaSuccess) e = cudaMalloc((void**)&c->d_err, 256);
+    if (e == cudaSuccess) e = cudaMemset(c->d_err, 0, 256);
     if (e != cudaSuccess) {
         cudaGetLastError();
         if (c->pool) cudaMemPoolDestroy(c->pool);
+        if (c->h_small) cudaFreeHost(c->h_small);
+        if (c->d_err) cudaFree(c->d_err);
         delete c;
         return JN_ERR_CUDA;
     }
@@ -274,6 +286,7 @@ void jn_destroy(jn_ctx* c) {
     resolve_pending(c);
     for (cudaEvent_t e : c->spare_events) cudaEventDestroy(e);
     if (c->h_small) cudaFreeHost(c->h_small);
+    if (c->d_err) cudaFree(c->d_err);
     if (c->pool) cudaMemPoolDestroy(c->pool);
     cudaGetLastError();
     delete c;
@@ -291,7 +304,7 @@ jn_status jn_set_tuning(jn_ctx* c, const jn_tuning* t) {
         default_tuning(&c->tune);
         return JN_OK;
     }
-    if (t->radix_bits < 0 || t->radix_bits > 16 || t->radix_bits1 < 0 || t->radix_bits1 > 10 ||
+    if (t->radix_bits < 0 || t->radix_bits > 20 || t->radix_bits1 < 0 || t->radix_bits1 > 10 ||
         t->filter_bits < 0 || t->filter_bits > 30 || t->theta_groups < 0 || t->theta_groups > 10 ||
         t->nlj_tile_r < 0 || (t->nlj_tile_r % 256) != 0 || t->nlj_tile_r > 4096)
         return fail(c, JN_ERR_INVALID, "tuning value out of range");

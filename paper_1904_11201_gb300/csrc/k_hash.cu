@@ -23,9 +23,10 @@
 namespace jnx {
 
 constexpr int HJ_T = 512;          // threads per join block
-constexpr int HJ_CAP = 8192;       // R rows per shared-memory table
-constexpr int HJ_SCH = 8192;       // S rows per work item
+constexpr int HJ_CAP = 4096;       // R rows per shared-memory table
+constexpr int HJ_SCH = 4096;       // S rows per work item
 constexpr int HJ_LGNB_MAX = 11;    // at most 2048 buckets
+constexpr int HJ_PAD = 16;         // rows of slack for 16-byte widened copies
 
 // Items of partition p: ceil(nr / CAP) R chunks x ceil(ns / SCH) S chunks.
 __global__ void k_items(const uint64_t* __restrict__ roff, const uint64_t* __restrict__ soff, int P,
@@ -47,61 +48,119 @@ __device__ __forceinline__ uint32_t bucket_of(uint32_t h, int bits, int lg) {
     return lg == 0 ? 0u : ((h << bits) >> (32 - lg));
 }
 
+// One work item: rows [rbeg, rbeg + rn) of R and [sbeg, sbeg + sn) of S.
+struct Item {
+    unsigned long long rbeg, sbeg;
+    int rn, sn;
+};
+
+// Writes the items of every partition (its R chunks x S chunks) at
+// items[item_prefix[p] ...].
+__global__ void k_item_desc(const uint64_t* __restrict__ roff, const uint64_t* __restrict__ soff,
+                            const uint64_t* __restrict__ item_prefix, int P, Item* __restrict__ items) {
+    const int p = blockIdx.x * blockDim.x + threadIdx.x;
+    if (p >= P) return;
+    const uint64_t i0 = item_prefix[p], i1 = item_prefix[p + 1];
+    if (i0 == i1) return;
+    const uint64_t nr = roff[p + 1] - roff[p], ns = soff[p + 1] - soff[p];
+    const uint64_t nrc = (nr + HJ_CAP - 1) / HJ_CAP;
+    for (uint64_t it = i0; it < i1; it++) {
+        const uint64_t local = it - i0;
+        const uint64_t rc = local % nrc, sc = local / nrc;
+        Item d;
+        d.rbeg = roff[p] + rc * HJ_CAP;
+        d.rn = (int)min((uint64_t)HJ_CAP, nr - rc * HJ_CAP);
+        d.sbeg = soff[p] + sc * HJ_SCH;
+        d.sn = (int)min((uint64_t)HJ_SCH, ns - sc * HJ_SCH);
+        items[it] = d;
+    }
+}
+
+// Starts the copy of rows [beg, beg + n) into `g` (widened to 16 bytes);
+// returns the byte offset of row `beg` inside the staged span.
+template <typename R>
+__device__ __forceinline__ uint32_t stage_span(const R* rows, uint64_t beg, int n, void* g, uint64_t* bar) {
+    const uint64_t lo = (beg * sizeof(R)) & ~15ull;
+    const uint64_t hi = ((beg + n) * sizeof(R) + 15) & ~15ull;
+    fence_proxy_async();
+    mbar_arrive_expect_tx(bar, (uint32_t)(hi - lo));
+    tma_load_1d(g, reinterpret_cast<const unsigned char*>(rows) + lo, (uint32_t)(hi - lo), bar);
+    return (uint32_t)(beg * sizeof(R) - lo);
+}
+
+template <typename R>
+__device__ __forceinline__ uint32_t span_off(uint64_t beg) {
+    return (uint32_t)(beg * sizeof(R) - ((beg * sizeof(R)) & ~15ull));
+}
+
 // MODE_COUNT: item_val[it] = matches of the item.
 // MODE_AGG:   as COUNT, and chk += sum over matches of f(r) * g(s).
 // MODE_EMIT:  writes the item's pairs at out[item_off[it] ...].
+// Items are dealt round-robin over the persistent blocks.  The R and S rows
+// of an item are staged by TMA bulk copies: the next item's R rows load
+// while this item probes, its S rows while it builds.  The partitioned rows
+// are library scratch, 16-byte aligned and padded by HJ_PAD rows, so every
+// widened copy stays inside its allocation.
 template <typename K, int MODE>
-__global__ void __launch_bounds__(HJ_T)
-k_hash_join(const K* __restrict__ rk, const int32_t* __restrict__ rp, const uint64_t* __restrict__ roff,
-            const K* __restrict__ sk, const int32_t* __restrict__ sp, const uint64_t* __restrict__ soff,
-            const uint64_t* __restrict__ item_prefix, int P, int bits,
-            unsigned long long* __restrict__ item_val, unsigned long long* __restrict__ chk,
-            const uint64_t* __restrict__ item_off, jn_pair* __restrict__ out,
-            unsigned int* __restrict__ work) {
-    extern __shared__ __align__(16) unsigned char smem[];
-    K* s_key = reinterpret_cast<K*>(smem);
+__global__ void __launch_bounds__(HJ_T, 2)
+k_hash_join(const Row<K, false>* __restrict__ rrows, const Row<K, false>* __restrict__ srows,
+            const Item* __restrict__ items, uint64_t nitems, int bits, unsigned long long* __restrict__ item_val,
+            unsigned long long* __restrict__ chk, const uint64_t* __restrict__ item_off,
+            jn_pair* __restrict__ out, unsigned int* __restrict__ err) {
+    using R = Row<K, false>;
+    constexpr int GR = HJ_CAP + 32 / (int)sizeof(R) + 2;
+    constexpr int GS = HJ_SCH + 32 / (int)sizeof(R) + 2;
+    extern __shared__ __align__(128) unsigned char smem[];
+    unsigned char* g_r = smem;                                  // GR rows
+    unsigned char* g_s = g_r + GR * sizeof(R);                  // GS rows
+    K* s_key = reinterpret_cast<K*>(g_s + GS * sizeof(R));      // HJ_CAP
     int32_t* s_pay = reinterpret_cast<int32_t*>(s_key + HJ_CAP);
-    uint32_t* s_off = reinterpret_cast<uint32_t*>(s_pay + HJ_CAP);  // (1 << HJ_LGNB_MAX) words
+    uint32_t* s_off = reinterpret_cast<uint32_t*>(s_pay + HJ_CAP);  // 1 << HJ_LGNB_MAX
     __shared__ unsigned long long tmp64[33];
     __shared__ uint32_t tmp32[33];
-    __shared__ unsigned int s_item;
     __shared__ uint32_t s_cursor;
+    __shared__ __align__(8) uint64_t bar_r, bar_s;
 
-    const uint64_t nitems = item_prefix[P];
     const int lane = threadIdx.x & 31;
+    uint64_t it = blockIdx.x;
+    if (it >= nitems) return;
+    Item d = items[it];
+    if (threadIdx.x == 0) {
+        mbar_init(&bar_r, 1);
+        mbar_init(&bar_s, 1);
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+        stage_span<R>(rrows, d.rbeg, d.rn, g_r, &bar_r);
+        stage_span<R>(srows, d.sbeg, d.sn, g_s, &bar_s);
+        s_cursor = 0;
+    }
+    __syncthreads();
+    uint32_t phase = 0;
     while (true) {
-        if (threadIdx.x == 0) {
-            s_item = atomicAdd(work, 1u);
-            s_cursor = 0;
-        }
-        __syncthreads();
-        const uint64_t it = s_item;
-        if (it >= nitems) break;
-        const int p = find_segment(item_prefix, P, it);
-        const uint64_t nr = roff[p + 1] - roff[p], ns = soff[p + 1] - soff[p];
-        const uint64_t nrc = (nr + HJ_CAP - 1) / HJ_CAP;
-        const uint64_t local = it - item_prefix[p];
-        const uint64_t rc = local % nrc, sc = local / nrc;
-        const uint64_t rbeg = roff[p] + rc * HJ_CAP;
-        const int rn = (int)min((uint64_t)HJ_CAP, nr - rc * HJ_CAP);
-        const uint64_t sbeg = soff[p] + sc * HJ_SCH;
-        const int sn = (int)min((uint64_t)HJ_SCH, ns - sc * HJ_SCH);
+        const uint64_t itn = it + gridDim.x;
+        const bool has_next = itn < nitems;
+        Item dn;
+        if (has_next) dn = items[itn];  // used once this item's staging is free
+        const int rn = d.rn, sn = d.sn;
         const int lg = bucket_bits(rn);
         const int nb = 1 << lg;
-
-        // ---- build: counting sort of the R chunk by bucket ----
         for (int i = threadIdx.x; i < nb; i += HJ_T) s_off[i] = 0;
-        __syncthreads();
+        bool ok = mbar_wait(&bar_r, phase, err);
+        if (__syncthreads_or(!ok)) {
+            mbar_wait(&bar_r, phase, nullptr);
+            mbar_wait(&bar_s, phase, nullptr);
+            break;
+        }
+        // ---- build: counting sort of the staged R chunk by bucket ----
+        const R* rrow = reinterpret_cast<const R*>(g_r + span_off<R>(d.rbeg));
         for (int i = threadIdx.x; i < rn; i += HJ_T)
-            atomicAdd(&s_off[bucket_of(khash(rk[rbeg + i]), bits, lg)], 1u);
+            atomicAdd(&s_off[bucket_of(khash(rrow[i].key), bits, lg)], 1u);
         __syncthreads();
         {
-            // exclusive scan of nb <= 2048 counters, 4 per thread
             uint32_t v[4];
             uint32_t sum = 0;
 #pragma unroll
             for (int j = 0; j < 4; j++) {
-                int i = threadIdx.x * 4 + j;
+                const int i = threadIdx.x * 4 + j;
                 v[j] = i < nb ? s_off[i] : 0u;
                 sum += v[j];
             }
@@ -109,40 +168,47 @@ k_hash_join(const K* __restrict__ rk, const int32_t* __restrict__ rp, const uint
             uint32_t pre = block_excl_scan(sum, tmp32, &tot);
 #pragma unroll
             for (int j = 0; j < 4; j++) {
-                int i = threadIdx.x * 4 + j;
+                const int i = threadIdx.x * 4 + j;
                 if (i < nb) s_off[i] = pre;
                 pre += v[j];
             }
         }
         __syncthreads();
         for (int i = threadIdx.x; i < rn; i += HJ_T) {
-            const K k = rk[rbeg + i];
-            const uint32_t pos = atomicAdd(&s_off[bucket_of(khash(k), bits, lg)], 1u);
-            s_key[pos] = k;
-            s_pay[pos] = rp[rbeg + i];
+            const R x = rrow[i];
+            const uint32_t pos = atomicAdd(&s_off[bucket_of(khash(x.key), bits, lg)], 1u);
+            s_key[pos] = x.key;
+            s_pay[pos] = x.pay;
         }
         __syncthreads();
-        // now bucket b holds rows [b ? s_off[b-1] : 0, s_off[b])
-
-        // ---- probe with the S chunk ----
+        // bucket b now holds rows [b ? s_off[b-1] : 0, s_off[b]); R staging is free
+        if (threadIdx.x == 0 && has_next) stage_span<R>(rrows, dn.rbeg, dn.rn, g_r, &bar_r);
+        ok = mbar_wait(&bar_s, phase, err);
+        if (__syncthreads_or(!ok)) {
+            mbar_wait(&bar_s, phase, nullptr);
+            if (has_next) mbar_wait(&bar_r, phase ^ 1u, nullptr);
+            break;
+        }
+        // ---- probe with the staged S chunk ----
+        const R* srow = reinterpret_cast<const R*>(g_s + span_off<R>(d.sbeg));
         unsigned long long acc = 0, csum = 0;
         const int rounds = (sn + HJ_T - 1) / HJ_T;
         for (int r = 0; r < rounds; r++) {
             const int j = r * HJ_T + threadIdx.x;
             uint32_t lo = 0, hi = 0;
-            K k = 0;
-            int32_t pay = 0;
+            R x;
+            x.key = 0;
+            x.pay = 0;
             if (j < sn) {
-                k = __ldcs(sk + sbeg + j);
-                pay = __ldcs(sp + sbeg + j);
-                const uint32_t b = bucket_of(khash(k), bits, lg);
+                x = srow[j];
+                const uint32_t b = bucket_of(khash(x.key), bits, lg);
                 lo = b ? s_off[b - 1] : 0u;
                 hi = s_off[b];
             }
             uint32_t m = 0;
             unsigned long long fs = 0;
             for (uint32_t e = lo; e < hi; e++) {
-                if (s_key[e] == k) {
+                if (s_key[e] == x.key) {
                     m++;
                     if (MODE == MODE_AGG) fs += chk_f(s_pay[e]);
                 }
@@ -156,17 +222,17 @@ k_hash_join(const K* __restrict__ rk, const int32_t* __restrict__ rp, const uint
                 if (m) {
                     uint64_t o = item_off[it] + base + (incl - m);
                     for (uint32_t e = lo; e < hi; e++) {
-                        if (s_key[e] == k) {
+                        if (s_key[e] == x.key) {
                             jn_pair q;
                             q.r = s_pay[e];
-                            q.s = pay;
+                            q.s = x.pay;
                             out[o++] = q;
                         }
                     }
                 }
             } else {
                 acc += m;
-                if (MODE == MODE_AGG && m) csum += fs * chk_g(pay);
+                if (MODE == MODE_AGG && m) csum += fs * chk_g(x.pay);
             }
         }
         if (MODE != MODE_EMIT) {
@@ -177,13 +243,24 @@ k_hash_join(const K* __restrict__ rk, const int32_t* __restrict__ rp, const uint
             }
             if (threadIdx.x == 0) item_val[it] = tot;
         }
+        __syncthreads();  // S staging and the table are free
+        if (threadIdx.x == 0) {
+            s_cursor = 0;
+            if (has_next) stage_span<R>(srows, dn.sbeg, dn.sn, g_s, &bar_s);
+        }
+        if (!has_next) break;
         __syncthreads();
+        phase ^= 1u;
+        it = itn;
+        d = dn;
     }
 }
 
 template <typename K>
 static size_t hash_smem() {
-    return (size_t)HJ_CAP * (sizeof(K) + 4) + sizeof(uint32_t) * (1u << HJ_LGNB_MAX);
+    using R = Row<K, false>;
+    const size_t gr = HJ_CAP + 32 / sizeof(R) + 2, gs = HJ_SCH + 32 / sizeof(R) + 2;
+    return (gr + gs) * sizeof(R) + (size_t)HJ_CAP * (sizeof(K) + 4) + sizeof(uint32_t) * (1u << HJ_LGNB_MAX);
 }
 
 static int persistent_grid(jn_ctx* c, const void* fn, int threads, size_t smem) {
@@ -197,12 +274,11 @@ static int persistent_grid(jn_ctx* c, const void* fn, int threads, size_t smem) 
     return per * c->num_sms;
 }
 
-// Partitions one table through both passes.  Outputs the partitioned key and
-// payload columns and offsets[P + 1].
+// Partitions one table through both passes.  Outputs the partitioned rows
+// and offsets[P + 1].
 template <typename K>
 struct Partitioned {
-    K* key = nullptr;
-    int32_t* pay = nullptr;
+    Row<K, false>* rows = nullptr;
     uint64_t* off = nullptr;  // P + 1 exact offsets
 };
 
@@ -211,32 +287,31 @@ static jn_status partition_table(jn_ctx* c, Scratch& s, const Cols<K>& T, int b1
                                  const uint32_t* other_bitmap, uint32_t fmask,
                                  const unsigned long long* hist1, Partitioned<K>* outp,
                                  uint64_t* d_survivors, unsigned int* work) {
+    using R = Row<K, false>;
     const int F1 = 1 << b1, F2 = 1 << b2, P = F1 * F2;
     const uint64_t n = (uint64_t)T.n;
     // ---- pass 1: regions sized by the unfiltered histogram ----
     uint64_t *start1, *seg_b, *seg_c, *tp;
     unsigned long long* cur1;
-    K* k1;
-    int32_t* p1;
+    R* r1;
     JN_TRY(s.get(&start1, F1 + 1));
     JN_TRY(s.get(&cur1, F1));
     JN_TRY(s.get(&seg_b, F1 + 1));
     JN_TRY(s.get(&seg_c, F1 + 1));
     JN_TRY(s.get(&tp, F1 + 2));
-    JN_TRY(s.get(&k1, n));
-    JN_TRY(s.get(&p1, n));
+    JN_TRY(s.get(&r1, n + HJ_PAD));
     JN_TRY(scan_u64(c, reinterpret_cast<const uint64_t*>(hist1), start1, F1));
     JN_TRY(launch(c, K_MISC, k_init_cursor, dim3((F1 + 255) / 256), dim3(256), 0,
                   (const uint64_t*)start1, cur1, (int64_t)F1));
     JN_TRY(launch(c, K_SEGMENTS, k_one_segment, dim3(1), dim3(32), 0, seg_b, seg_c, tp, n));
-    const size_t sm = scatter_smem<K>(false);
-    auto kern1 = other_bitmap ? k_scatter<K, true, HashDigit> : k_scatter<K, false, HashDigit>;
+    const size_t sm = scatter_smem<K, false>();
+    auto kern1 = other_bitmap ? k_scatter<K, false, true, HashDigit> : k_scatter<K, false, false, HashDigit>;
     const int g1 = persistent_grid(c, (const void*)kern1, SC_T, sm);
     HashDigit d1{32 - b1, (uint32_t)(F1 - 1)};
-    JN_TRY(zero(c, work, sizeof(unsigned int)));
-    JN_TRY(launch(c, K_SCATTER, kern1, dim3(g1), dim3(SC_T), sm, T.key, (const K*)nullptr, T.pay,
-                  (const uint64_t*)seg_b, (const uint64_t*)seg_c, (const uint64_t*)tp, 1, d1, F1,
-                  other_bitmap, fmask, cur1, k1, (K*)nullptr, p1, work));
+    PartIn<K, false> in1{T.key, nullptr, T.pay, nullptr, n};
+    JN_TRY(launch(c, K_SCATTER, kern1, dim3(g1), dim3(SC_T), sm, in1, (const uint64_t*)seg_b,
+                  (const uint64_t*)seg_c, (const uint64_t*)tp, 1, d1, F1, other_bitmap, fmask, cur1, r1,
+                  c->d_err));
     // ---- pass 1 regions become the segments of pass 2 ----
     JN_TRY(launch(c, K_SEGMENTS, k_segments, dim3(1), dim3(1024), 0, (const unsigned long long*)cur1,
                   (const uint64_t*)start1, F1, seg_c, tp, d_survivors));
@@ -248,29 +323,24 @@ static jn_status partition_table(jn_ctx* c, Scratch& s, const Cols<K>& T, int b1
     JN_TRY(s.get(&cur2, P));
     JN_TRY(zero(c, hist2, sizeof(unsigned long long) * P));
     HashDigit d2{32 - b1 - b2, (uint32_t)(F2 - 1)};
-    auto kh = k_seg_hist<K, HashDigit>;
+    auto kh = k_seg_hist_rows<R, HashDigit>;
     const size_t smh = sizeof(uint32_t) * F2;
     const int gh = persistent_grid(c, (const void*)kh, SC_T, smh);
-    JN_TRY(zero(c, work, sizeof(unsigned int)));
-    JN_TRY(launch(c, K_HIST, kh, dim3(gh), dim3(SC_T), smh, (const K*)k1, (const uint64_t*)start1,
-                  (const uint64_t*)seg_c, (const uint64_t*)tp, F1, d2, F2, hist2, work));
+    JN_TRY(launch(c, K_HIST, kh, dim3(gh), dim3(SC_T), smh, (const R*)r1, (const uint64_t*)start1,
+                  (const uint64_t*)seg_c, (const uint64_t*)tp, F1, d2, F2, hist2));
     JN_TRY(scan_u64(c, reinterpret_cast<const uint64_t*>(hist2), start2, P));
     JN_TRY(launch(c, K_MISC, k_init_cursor, dim3((P + 255) / 256), dim3(256), 0,
                   (const uint64_t*)start2, cur2, (int64_t)P));
     // ---- pass 2 ----
-    K* k2;
-    int32_t* p2;
-    JN_TRY(s.get(&k2, n));
-    JN_TRY(s.get(&p2, n));
-    auto kern2 = k_scatter<K, false, HashDigit>;
+    R* r2;
+    JN_TRY(s.get(&r2, n + HJ_PAD));
+    auto kern2 = k_scatter<K, false, false, HashDigit>;
     const int g2 = persistent_grid(c, (const void*)kern2, SC_T, sm);
-    JN_TRY(zero(c, work, sizeof(unsigned int)));
-    JN_TRY(launch(c, K_SCATTER, kern2, dim3(g2), dim3(SC_T), sm, (const K*)k1, (const K*)nullptr,
-                  (const int32_t*)p1, (const uint64_t*)start1, (const uint64_t*)seg_c,
-                  (const uint64_t*)tp, F1, d2, F2, (const uint32_t*)nullptr, 0u, cur2, k2,
-                  (K*)nullptr, p2, work));
-    outp->key = k2;
-    outp->pay = p2;
+    PartIn<K, false> in2{nullptr, nullptr, nullptr, r1, n + HJ_PAD};
+    JN_TRY(launch(c, K_SCATTER, kern2, dim3(g2), dim3(SC_T), sm, in2, (const uint64_t*)start1,
+                  (const uint64_t*)seg_c, (const uint64_t*)tp, F1, d2, F2, (const uint32_t*)nullptr, 0u, cur2,
+                  r2, c->d_err));
+    outp->rows = r2;
     outp->off = start2;
     return JN_OK;
 }
@@ -296,9 +366,9 @@ jn_status run_hash(jn_ctx* c, const Cols<K>& R, const Cols<K>& S, int mode, OutP
     if (b == 0) {
         uint64_t target = HJ_CAP / 2;  // expected R rows per partition
         b = ceil_log2((nr + target - 1) / target);
-        if (b > 16) b = 16;
+        if (b > 20) b = 20;
     }
-    int b1 = tu.radix_bits1 ? tu.radix_bits1 : (b + 1) / 2;
+    int b1 = tu.radix_bits1 ? tu.radix_bits1 : b / 2;
     if (b1 > b) b1 = b;
     if (b1 > 10) b1 = 10;
     if (b - b1 > 10) b1 = b - 10;
@@ -374,6 +444,13 @@ jn_status run_hash(jn_ctx* c, const Cols<K>& R, const Cols<K>& S, int mode, OutP
         }
         return JN_OK;
     }
+    // the join kernel stages rows with 16-byte bulk copies from these columns
+    if ((((uintptr_t)PR.rows) | ((uintptr_t)PS.rows)) & 15)
+        return fail(c, JN_ERR_CUDA, "partition scratch is not 16-byte aligned");
+    Item* idesc;
+    JN_TRY(s.get(&idesc, nitems));
+    JN_TRY(launch(c, K_ITEMS, k_item_desc, dim3((P + 255) / 256), dim3(256), 0, (const uint64_t*)PR.off,
+                  (const uint64_t*)PS.off, (const uint64_t*)iprefix, P, idesc));
     unsigned long long *ival, *chk;
     uint64_t* ioff;
     JN_TRY(s.get(&ival, nitems));
@@ -382,12 +459,10 @@ jn_status run_hash(jn_ctx* c, const Cols<K>& R, const Cols<K>& S, int mode, OutP
     JN_TRY(zero(c, chk, 8));
     const size_t smj = hash_smem<K>();
     auto kc = (mode == MODE_AGG) ? k_hash_join<K, MODE_AGG> : k_hash_join<K, MODE_COUNT>;
-    const int gj = persistent_grid(c, (const void*)kc, HJ_T, smj);
-    JN_TRY(zero(c, work, 4));
-    JN_TRY(launch(c, K_HASH_COUNT, kc, dim3(gj), dim3(HJ_T), smj, (const K*)PR.key,
-                  (const int32_t*)PR.pay, (const uint64_t*)PR.off, (const K*)PS.key,
-                  (const int32_t*)PS.pay, (const uint64_t*)PS.off, (const uint64_t*)iprefix, P, b, ival,
-                  chk, (const uint64_t*)nullptr, (jn_pair*)nullptr, work));
+    const int gj = (int)min((uint64_t)persistent_grid(c, (const void*)kc, HJ_T, smj), nitems);
+    JN_TRY(launch(c, K_HASH_COUNT, kc, dim3(gj), dim3(HJ_T), smj, (const Row<K, false>*)PR.rows,
+                  (const Row<K, false>*)PS.rows, (const Item*)idesc, nitems, b, ival, chk,
+                  (const uint64_t*)nullptr, (jn_pair*)nullptr, c->d_err));
     JN_TRY(scan_u64(c, reinterpret_cast<const uint64_t*>(ival), ioff, (int64_t)nitems));
     JN_TRY(launch(c, K_MISC, k_copy_words, dim3(1), dim3(32), 0, (const uint64_t*)(ioff + nitems),
                   d_small + 3, 1));
@@ -402,13 +477,11 @@ jn_status run_hash(jn_ctx* c, const Cols<K>& R, const Cols<K>& S, int mode, OutP
     JN_TRY(out_prepare(c, s, hc[0], *plan));
     if (hc[0] > 0) {
         auto ke = k_hash_join<K, MODE_EMIT>;
-        const int ge = persistent_grid(c, (const void*)ke, HJ_T, smj);
-        JN_TRY(zero(c, work, 4));
-        JN_TRY(launch(c, K_HASH_EMIT, ke, dim3(ge), dim3(HJ_T), smj, (const K*)PR.key,
-                      (const int32_t*)PR.pay, (const uint64_t*)PR.off, (const K*)PS.key,
-                      (const int32_t*)PS.pay, (const uint64_t*)PS.off, (const uint64_t*)iprefix, P, b,
-                      (unsigned long long*)nullptr, (unsigned long long*)nullptr,
-                      (const uint64_t*)ioff, plan->dev, work));
+        const int ge = (int)min((uint64_t)persistent_grid(c, (const void*)ke, HJ_T, smj), nitems);
+        JN_TRY(launch(c, K_HASH_EMIT, ke, dim3(ge), dim3(HJ_T), smj, (const Row<K, false>*)PR.rows,
+                      (const Row<K, false>*)PS.rows, (const Item*)idesc, nitems, b,
+                      (unsigned long long*)nullptr, (unsigned long long*)nullptr, (const uint64_t*)ioff,
+                      plan->dev, c->d_err));
     }
     JN_TRY(out_finish(c, hc[0], *plan));
     return JN_OK;

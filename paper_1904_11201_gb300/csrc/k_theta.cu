@@ -110,11 +110,17 @@ __global__ void k_theta_items(const uint64_t* __restrict__ roff, const uint64_t*
 
 // BAND: window + fine buckets; !BAND: diagonal group, every pair compared.
 // ka = compared column (a), kk = grouped column (k; equals ka when !BAND).
+// Rows: key = the grouped column (k for a band, a otherwise), b = column a
+// (band only), pay = payload.
+template <typename K, bool BAND>
+__device__ __forceinline__ K col_a(const Row<K, BAND>& x) {
+    if constexpr (BAND) return x.b; else return x.key;
+}
+
 template <typename K, int MODE, bool BAND>
 __global__ void __launch_bounds__(TH_T)
-k_theta_join(const K* __restrict__ rkk, const K* __restrict__ rka, const int32_t* __restrict__ rp,
-             const uint64_t* __restrict__ roff, const K* __restrict__ skk, const K* __restrict__ ska,
-             const int32_t* __restrict__ sp, const uint64_t* __restrict__ soff,
+k_theta_join(const Row<K, BAND>* __restrict__ rrows, const uint64_t* __restrict__ roff,
+             const Row<K, BAND>* __restrict__ srows, const uint64_t* __restrict__ soff,
              const RangeParams* __restrict__ prm, const uint64_t* __restrict__ item_prefix, int G, int op,
              long long band, unsigned long long* __restrict__ item_val, unsigned long long* __restrict__ chk,
              const uint64_t* __restrict__ item_off, jn_pair* __restrict__ out, unsigned int* __restrict__ work) {
@@ -162,7 +168,7 @@ k_theta_join(const K* __restrict__ rkk, const K* __restrict__ rka, const int32_t
             for (int i = threadIdx.x; i < nfb; i += TH_T) s_off[i] = 0;
             __syncthreads();
             for (int i = threadIdx.x; i < rn; i += TH_T) {
-                const uint64_t u = uoff(rkk[rbeg + i], P.lo);
+                const uint64_t u = uoff(rrows[rbeg + i].key, P.lo);
                 if (u >= wlo && u <= whi) atomicAdd(&s_off[(u - wlo) >> fs], 1u);
             }
             __syncthreads();
@@ -184,20 +190,21 @@ k_theta_join(const K* __restrict__ rkk, const K* __restrict__ rka, const int32_t
             }
             __syncthreads();
             for (int i = threadIdx.x; i < rn; i += TH_T) {
-                const K kk = rkk[rbeg + i];
-                const uint64_t u = uoff(kk, P.lo);
+                const Row<K, BAND> x = rrows[rbeg + i];
+                const uint64_t u = uoff(x.key, P.lo);
                 if (u >= wlo && u <= whi) {
                     const uint32_t pos = atomicAdd(&s_off[(u - wlo) >> fs], 1u);
-                    s_k[pos] = kk;
-                    s_a[pos] = rka[rbeg + i];
-                    s_p[pos] = rp[rbeg + i];
+                    s_k[pos] = x.key;
+                    s_a[pos] = col_a<K, BAND>(x);
+                    s_p[pos] = x.pay;
                 }
             }
             // bucket b now holds [b ? s_off[b-1] : 0, s_off[b])
         } else {
             for (int i = threadIdx.x; i < rn; i += TH_T) {
-                s_a[i] = rka[rbeg + i];
-                s_p[i] = rp[rbeg + i];
+                const Row<K, BAND> x = rrows[rbeg + i];
+                s_a[i] = col_a<K, BAND>(x);
+                s_p[i] = x.pay;
             }
             if (threadIdx.x == 0) s_rows = (uint32_t)rn;
         }
@@ -211,11 +218,12 @@ k_theta_join(const K* __restrict__ rkk, const K* __restrict__ rka, const int32_t
             Interval<K> ia, ib;
             int32_t pay = 0;
             if (j < sn) {
-                const K a = ska[sbeg + j];
-                pay = sp[sbeg + j];
+                const Row<K, BAND> x = srows[sbeg + j];
+                const K a = col_a<K, BAND>(x);
+                pay = x.pay;
                 ia = op_interval<K>(op, a);
                 if (BAND) {
-                    const K kk = skk[sbeg + j];
+                    const K kk = x.key;
                     ib = band_interval<K>(kk, band);
                     const uint64_t u = uoff(kk, P.lo);
                     const uint64_t b = (uint64_t)band;
@@ -305,8 +313,9 @@ __global__ void k_cross_counts(const uint64_t* __restrict__ roff, const uint64_t
 
 // Checksum of the cross regions: sum_y (sum of f over the ranges) * (sum of g over S_y),
 // using fpre = prefix sums of f over the partitioned R payloads.
+template <typename R>
 __global__ void k_cross_checksum(const uint64_t* __restrict__ roff, const uint64_t* __restrict__ soff,
-                                 const int32_t* __restrict__ sp, const uint64_t* __restrict__ fpre, int G,
+                                 const R* __restrict__ srows, const uint64_t* __restrict__ fpre, int G,
                                  int op, unsigned long long* __restrict__ chk) {
     __shared__ unsigned long long tmp[33];
     const int y = blockIdx.x;
@@ -314,7 +323,7 @@ __global__ void k_cross_checksum(const uint64_t* __restrict__ roff, const uint64
     cross_ranges(op, roff, y, G, &b0, &l0, &b1, &l1);
     if (l0 + l1 == 0) return;
     unsigned long long g = 0;
-    for (uint64_t i = soff[y] + threadIdx.x; i < soff[y + 1]; i += blockDim.x) g += chk_g(sp[i]);
+    for (uint64_t i = soff[y] + threadIdx.x; i < soff[y + 1]; i += blockDim.x) g += chk_g(srows[i].pay);
     g = block_sum(g, tmp);
     if (threadIdx.x == 0) {
         const uint64_t f = (fpre[b0 + l0] - fpre[b0]) + (fpre[b1 + l1] - fpre[b1]);
@@ -322,14 +331,16 @@ __global__ void k_cross_checksum(const uint64_t* __restrict__ roff, const uint64
     }
 }
 
-__global__ void k_fvals(const int32_t* __restrict__ p, int64_t n, uint64_t* __restrict__ f) {
+template <typename R>
+__global__ void k_fvals(const R* __restrict__ rows, int64_t n, uint64_t* __restrict__ f) {
     int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i < n) f[i] = chk_f(p[i]);
+    if (i < n) f[i] = chk_f(rows[i].pay);
 }
 
 // Writes the cross products: pair q of group y is (R[range(q % len)], S_y[q / len]).
+template <typename R>
 __global__ void __launch_bounds__(256)
-k_cross_emit(const int32_t* __restrict__ rp, const uint64_t* __restrict__ roff, const int32_t* __restrict__ sp,
+k_cross_emit(const R* __restrict__ rrows, const uint64_t* __restrict__ roff, const R* __restrict__ srows,
              const uint64_t* __restrict__ soff, const uint64_t* __restrict__ cross_off,
              const uint64_t* __restrict__ chunk_prefix, int G, int op, uint64_t base,
              jn_pair* __restrict__ out, unsigned int* __restrict__ work) {
@@ -353,17 +364,17 @@ k_cross_emit(const int32_t* __restrict__ rp, const uint64_t* __restrict__ roff, 
             const uint64_t si = q / len, ri = q - si * len;
             const uint64_t r = ri < l0 ? b0 + ri : b1 + (ri - l0);
             jn_pair v;
-            v.r = rp[r];
-            v.s = sp[soff[y] + si];
+            v.r = rrows[r].pay;
+            v.s = srows[soff[y] + si].pay;
             out[obase + q] = v;
         }
     }
 }
 
-template <typename K>
+template <typename K, bool HB>
 static jn_status range_partition(jn_ctx* c, Scratch& s, const Cols<K>& T, const K* grp, const K* carry,
-                                 const RangeParams* prm, int G, unsigned int* work, K** okk, K** oka,
-                                 int32_t** op, uint64_t** off) {
+                                 const RangeParams* prm, int G, unsigned int* work, Row<K, HB>** orows,
+                                 uint64_t** off) {
     const uint64_t n = (uint64_t)T.n;
     uint64_t *sb, *scn, *tp, *start;
     unsigned long long *hist, *cur;
@@ -380,47 +391,32 @@ static jn_status range_partition(jn_ctx* c, Scratch& s, const Cols<K>& T, const 
     const size_t smh = sizeof(uint32_t) * G;
     int per = 0;
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, kh, SC_T, smh);
-    JN_TRY(zero(c, work, 4));
     JN_TRY(launch(c, K_HIST, kh, dim3(max(per, 1) * c->num_sms), dim3(SC_T), smh, grp,
                   (const uint64_t*)sb, (const uint64_t*)scn, (const uint64_t*)tp, 1, dg, G, hist, work));
     JN_TRY(scan_u64(c, reinterpret_cast<const uint64_t*>(hist), start, G));
     JN_TRY(launch(c, K_MISC, k_init_cursor, dim3((G + 255) / 256), dim3(256), 0, (const uint64_t*)start,
                   cur, (int64_t)G));
-    K *kk, *ka = nullptr;
-    int32_t* pp;
-    JN_TRY(s.get(&kk, n));
-    if (carry) JN_TRY(s.get(&ka, n));
-    JN_TRY(s.get(&pp, n));
-    auto ks = k_scatter<K, false, RangeDigit>;
-    const size_t sm = scatter_smem<K>(carry != nullptr);
+    Row<K, HB>* rows;
+    JN_TRY(s.get(&rows, n + 16));
+    auto ks = k_scatter<K, HB, false, RangeDigit>;
+    const size_t sm = scatter_smem<K, HB>();
     per = 0;
     ensure_smem((const void*)ks, sm);
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, ks, SC_T, sm);
-    JN_TRY(zero(c, work, 4));
-    JN_TRY(launch(c, K_SCATTER, ks, dim3(max(per, 1) * c->num_sms), dim3(SC_T), sm, grp, carry, T.pay,
-                  (const uint64_t*)sb, (const uint64_t*)scn, (const uint64_t*)tp, 1, dg, G,
-                  (const uint32_t*)nullptr, 0u, cur, kk, ka, pp, work));
-    *okk = kk;
-    *oka = carry ? ka : kk;
-    *op = pp;
+    PartIn<K, HB> in{grp, carry, T.pay, nullptr, n};
+    JN_TRY(launch(c, K_SCATTER, ks, dim3(max(per, 1) * c->num_sms), dim3(SC_T), sm, in, (const uint64_t*)sb,
+                  (const uint64_t*)scn, (const uint64_t*)tp, 1, dg, G, (const uint32_t*)nullptr, 0u, cur, rows,
+                  c->d_err));
+    *orows = rows;
     *off = start;
     return JN_OK;
 }
 
-template <typename K>
-jn_status run_theta(jn_ctx* c, const Cols<K>& R, const Cols<K>& S, int op, int64_t band, int mode,
-                    OutPlan* plan, RunResult* res) {
+template <typename K, bool B>
+static jn_status run_theta_t(jn_ctx* c, const Cols<K>& R, const Cols<K>& S, int op, int64_t band, int mode,
+                             OutPlan* plan, RunResult* res) {
+    using RW = Row<K, B>;
     jn_run_info& info = c->info;
-    const bool B = band >= 0;
-    if (R.n == 0 || S.n == 0) {
-        res->count = res->checksum = 0;
-        if (mode == MODE_EMIT) {
-            Scratch s0(c);
-            JN_TRY(out_prepare(c, s0, 0, *plan));
-            JN_TRY(out_finish(c, 0, *plan));
-        }
-        return JN_OK;
-    }
     int g = c->tune.theta_groups;
     if (g == 0) {
         const uint64_t base = B ? (uint64_t)R.n : (uint64_t)max(R.n, S.n);
@@ -444,11 +440,10 @@ jn_status run_theta(jn_ctx* c, const Cols<K>& R, const Cols<K>& S, int op, int64
     JN_TRY(launch(c, K_MINMAX, k_minmax<K>, dim3(2 * c->num_sms), dim3(512), 0, rg, R.n, mm));
     JN_TRY(launch(c, K_MINMAX, k_minmax<K>, dim3(2 * c->num_sms), dim3(512), 0, sg, S.n, mm));
     JN_TRY(launch(c, K_MINMAX, k_range_setup, dim3(1), dim3(1), 0, (const long long*)mm, G, prm));
-    K *rkk, *rka, *skk, *ska;
-    int32_t *rp, *sp;
+    RW *rrows, *srows;
     uint64_t *roff, *soff;
-    JN_TRY(range_partition<K>(c, s, R, rg, B ? R.key : nullptr, prm, G, work, &rkk, &rka, &rp, &roff));
-    JN_TRY(range_partition<K>(c, s, S, sg, B ? S.key : nullptr, prm, G, work, &skk, &ska, &sp, &soff));
+    JN_TRY((range_partition<K, B>(c, s, R, rg, B ? R.key : nullptr, prm, G, work, &rrows, &roff)));
+    JN_TRY((range_partition<K, B>(c, s, S, sg, B ? S.key : nullptr, prm, G, work, &srows, &soff)));
     // ---- compared regions (band window or diagonal) ----
     uint64_t *items, *ipre;
     JN_TRY(s.get(&items, G));
@@ -480,18 +475,10 @@ jn_status run_theta(jn_ctx* c, const Cols<K>& R, const Cols<K>& S, int op, int64
     JN_TRY(zero(c, chk, 8));
     const size_t smj = (size_t)TH_RCAP * (2 * sizeof(K) + 4) + sizeof(uint32_t) * TH_NFB;
     const int cm = mode == MODE_AGG ? MODE_AGG : MODE_COUNT;
-    auto pick = [&](int m) -> void (*)(const K*, const K*, const int32_t*, const uint64_t*, const K*,
-                                       const K*, const int32_t*, const uint64_t*, const RangeParams*,
-                                       const uint64_t*, int, int, long long, unsigned long long*,
-                                       unsigned long long*, const uint64_t*, jn_pair*, unsigned int*) {
-        if (B) {
-            if (m == MODE_EMIT) return k_theta_join<K, MODE_EMIT, true>;
-            if (m == MODE_AGG) return k_theta_join<K, MODE_AGG, true>;
-            return k_theta_join<K, MODE_COUNT, true>;
-        }
-        if (m == MODE_EMIT) return k_theta_join<K, MODE_EMIT, false>;
-        if (m == MODE_AGG) return k_theta_join<K, MODE_AGG, false>;
-        return k_theta_join<K, MODE_COUNT, false>;
+    auto pick = [&](int m) {
+        if (m == MODE_EMIT) return k_theta_join<K, MODE_EMIT, B>;
+        if (m == MODE_AGG) return k_theta_join<K, MODE_AGG, B>;
+        return k_theta_join<K, MODE_COUNT, B>;
     };
     auto grid_of = [&](const void* fn) {
         int per = 0;
@@ -502,9 +489,8 @@ jn_status run_theta(jn_ctx* c, const Cols<K>& R, const Cols<K>& S, int op, int64
     if (nitems) {
         auto kc = pick(cm);
         JN_TRY(zero(c, work, 4));
-        JN_TRY(launch(c, K_THETA_COUNT, kc, dim3(grid_of((const void*)kc)), dim3(TH_T), smj,
-                      (const K*)rkk, (const K*)rka, (const int32_t*)rp, (const uint64_t*)roff, (const K*)skk,
-                      (const K*)ska, (const int32_t*)sp, (const uint64_t*)soff, (const RangeParams*)prm,
+        JN_TRY(launch(c, K_THETA_COUNT, kc, dim3(grid_of((const void*)kc)), dim3(TH_T), smj, (const RW*)rrows,
+                      (const uint64_t*)roff, (const RW*)srows, (const uint64_t*)soff, (const RangeParams*)prm,
                       (const uint64_t*)ipre, G, op, (long long)(B ? band : -1), ival, chk,
                       (const uint64_t*)nullptr, (jn_pair*)nullptr, work));
     }
@@ -513,11 +499,11 @@ jn_status run_theta(jn_ctx* c, const Cols<K>& R, const Cols<K>& S, int op, int64
         uint64_t *fv, *fpre;
         JN_TRY(s.get(&fv, R.n));
         JN_TRY(s.get(&fpre, R.n + 1));
-        JN_TRY(launch(c, K_MISC, k_fvals, dim3((unsigned)ceil_div(R.n, 256)), dim3(256), 0,
-                      (const int32_t*)rp, (int64_t)R.n, fv));
+        JN_TRY(launch(c, K_MISC, k_fvals<RW>, dim3((unsigned)ceil_div(R.n, 256)), dim3(256), 0, (const RW*)rrows,
+                      (int64_t)R.n, fv));
         JN_TRY(scan_u64(c, fv, fpre, R.n));
-        JN_TRY(launch(c, K_MISC, k_cross_checksum, dim3(G), dim3(256), 0, (const uint64_t*)roff,
-                      (const uint64_t*)soff, (const int32_t*)sp, (const uint64_t*)fpre, G, op, chk));
+        JN_TRY(launch(c, K_MISC, k_cross_checksum<RW>, dim3(G), dim3(256), 0, (const uint64_t*)roff,
+                      (const uint64_t*)soff, (const RW*)srows, (const uint64_t*)fpre, G, op, chk));
     }
     JN_CUDA(c, cudaMemcpyAsync(d_small, ioff + nitems, 8, cudaMemcpyDeviceToDevice, c->stream));
     JN_CUDA(c, cudaMemcpyAsync(d_small + 1, chk, 8, cudaMemcpyDeviceToDevice, c->stream));
@@ -539,21 +525,35 @@ jn_status run_theta(jn_ctx* c, const Cols<K>& R, const Cols<K>& S, int op, int64
     if (diag) {
         auto ke = pick(MODE_EMIT);
         JN_TRY(zero(c, work, 4));
-        JN_TRY(launch(c, K_THETA_EMIT, ke, dim3(grid_of((const void*)ke)), dim3(TH_T), smj,
-                      (const K*)rkk, (const K*)rka, (const int32_t*)rp, (const uint64_t*)roff, (const K*)skk,
-                      (const K*)ska, (const int32_t*)sp, (const uint64_t*)soff, (const RangeParams*)prm,
-                      (const uint64_t*)ipre, G, op, (long long)(B ? band : -1),
-                      (unsigned long long*)nullptr, (unsigned long long*)nullptr, (const uint64_t*)ioff,
-                      plan->dev, work));
+        JN_TRY(launch(c, K_THETA_EMIT, ke, dim3(grid_of((const void*)ke)), dim3(TH_T), smj, (const RW*)rrows,
+                      (const uint64_t*)roff, (const RW*)srows, (const uint64_t*)soff, (const RangeParams*)prm,
+                      (const uint64_t*)ipre, G, op, (long long)(B ? band : -1), (unsigned long long*)nullptr,
+                      (unsigned long long*)nullptr, (const uint64_t*)ioff, plan->dev, work));
     }
     if (crossn) {
         JN_TRY(zero(c, work, 4));
-        JN_TRY(launch(c, K_CROSS_EMIT, k_cross_emit, dim3(4 * c->num_sms), dim3(256), 0, (const int32_t*)rp,
-                      (const uint64_t*)roff, (const int32_t*)sp, (const uint64_t*)soff, (const uint64_t*)coff,
+        JN_TRY(launch(c, K_CROSS_EMIT, k_cross_emit<RW>, dim3(4 * c->num_sms), dim3(256), 0, (const RW*)rrows,
+                      (const uint64_t*)roff, (const RW*)srows, (const uint64_t*)soff, (const uint64_t*)coff,
                       (const uint64_t*)cpre, G, op, diag, plan->dev, work));
     }
     JN_TRY(out_finish(c, total, *plan));
     return JN_OK;
+}
+
+template <typename K>
+jn_status run_theta(jn_ctx* c, const Cols<K>& R, const Cols<K>& S, int op, int64_t band, int mode,
+                    OutPlan* plan, RunResult* res) {
+    if (R.n == 0 || S.n == 0) {
+        res->count = res->checksum = 0;
+        if (mode == MODE_EMIT) {
+            Scratch s0(c);
+            JN_TRY(out_prepare(c, s0, 0, *plan));
+            JN_TRY(out_finish(c, 0, *plan));
+        }
+        return JN_OK;
+    }
+    if (band >= 0) return run_theta_t<K, true>(c, R, S, op, band, mode, plan, res);
+    return run_theta_t<K, false>(c, R, S, op, band, mode, plan, res);
 }
 
 template jn_status run_theta<int32_t>(jn_ctx*, const Cols<int32_t>&, const Cols<int32_t>&, int, int64_t,

@@ -76,7 +76,7 @@ HASH_CASES = [
     (4097, 12289, 0, 300, torch.int32),       # many duplicates, ragged sizes
     (20000, 50001, I32_MIN, I32_MAX, torch.int32),
     (5003, 7001, 0, 1000, torch.int64),
-    (30000, 20000, I64_MIN // 2, I64_MAX // 2, torch.int64),
+    (30000, 20000, I64_MIN // 4, I64_MAX // 4, torch.int64),
 ]
 
 
