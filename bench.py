@@ -77,6 +77,15 @@ def make_workload(name, theta, device, small=False, rows_log2=0):
                 "config": {"workload": "band join R.a < S.a and |R.k - S.k| <= 95, 1M x 16M int32",
                            "R_rows": nr, "S_rows": ns, "key": "int32", "band": 95,
                            "algo": "jn_theta(op <, band 95)"}}
+    if name == "nlj_band":
+        nr, ns = (1 << 16, 1 << 20) if not small else (1 << 12, 1 << 16)
+        ra, rk = D.band_columns(nr, 24, seed=0, stream=0, device=device)
+        sa, sk = D.band_columns(ns, 24, seed=0, stream=1, device=device)
+        return {"kind": "nlj", "pred": (2, 6, 24414),
+                "R": (ra, rk, D.row_ids(nr, device)), "S": (sa, sk, D.row_ids(ns, device)),
+                "config": {"workload": "tiled nested loop R.a < S.a and |R.k - S.k| <= 24414, 64K x 1M int32",
+                           "R_rows": nr, "S_rows": ns, "key": "int32", "band": 24414,
+                           "algo": "jn_nested_loop (two-column predicate)"}}
     if name == "nlj":
         nr, ns = 1 << 14, 1 << 16
         r = D.uniform_keys(nr, 0, 65536, seed=0, stream=0, device=device)
@@ -87,12 +96,27 @@ def make_workload(name, theta, device, small=False, rows_log2=0):
     raise ValueError(name)
 
 
+class Counted:
+    """Result of a count-and-checksum step (pairs counted, not stored)."""
+
+    def __init__(self, n, checksum):
+        self.shape = (n, 2)
+        self.checksum = checksum
+
+
 def run_step(jn, ctx, w, R, S, out=None):
+    if w.get("aggregate"):
+        algo = {"hash": jn.JN_ALGO_HASH, "band": jn.JN_ALGO_THETA, "nlj": jn.JN_ALGO_NLJ}[w["kind"]]
+        pr = jn.pred(w["op"], jn.JN_ANY, w["band"]) if w["kind"] == "band" else None
+        if "pred" in w:
+            pr = jn.pred(*w["pred"])
+        return Counted(*jn.jn_aggregate(ctx, algo, R, S, pr))
     if w["kind"] == "hash":
         return jn.jn_hash(ctx, R, S, out=out)
     if w["kind"] == "band":
         return jn.jn_theta(ctx, R, S, w["op"], w["band"], out=out)
-    return jn.jn_nested_loop(ctx, R, S, out=out)
+    pr = jn.pred(*w["pred"]) if "pred" in w else None
+    return jn.jn_nested_loop(ctx, R, S, pr, out=out)
 
 
 # ------------------------------------------------------------ roofline --
@@ -109,6 +133,7 @@ def algorithmic_bytes(kind, info, nr, ns, m, ksize):
             "histogram": ksize * surv,
             "hash_count": row * surv,
             "hash_emit": row * surv + 8 * m,
+            "cross_emit": 8 * m,
         }
     if kind == "band":
         return {
@@ -294,6 +319,8 @@ def main():
                     help="hash workloads: 2^N rows per table over a 2^N key domain (profiling runs)")
     ap.add_argument("--prefilter", type=int, default=-1, help="-1 auto, 0 off, 1 on")
     ap.add_argument("--radix-bits", type=int, default=0)
+    ap.add_argument("--aggregate", action="store_true",
+                    help="count + checksum without storing pairs (results too large to store)")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     args = ap.parse_args()
@@ -317,6 +344,10 @@ def main():
     if args.prefilter != -1 or args.radix_bits:
         ctx.set_tuning(prefilter=args.prefilter, radix_bits=args.radix_bits)
     w = make_workload(args.workload, args.theta, dev, args.small, args.rows_log2)
+    if args.aggregate:
+        w["aggregate"] = True
+        w["config"]["mode"] = "count + separable checksum (pairs not stored)"
+        args.no_e2e = True
     (rk, rk2, rp), (sk, sk2, sp) = w["R"], w["S"]
     R = jn.table(rk, rk2, rp)
     S = jn.table(sk, sk2, sp)

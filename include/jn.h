@@ -93,7 +93,8 @@ typedef struct {
     int32_t radix_bits;    /* total partition bits of the hash join (0 = auto, <= 20)   */
     int32_t radix_bits1;   /* bits of the first partition pass (0 = auto)               */
     int32_t filter_bits;   /* log2 of the key-presence bitmap size (0 = auto, <= 30)    */
-    int32_t heavy;         /* -1 auto, 0 off, 1 on: frequent keys joined as cross products */
+    int32_t heavy;         /* -1 auto, 0 off, 1 on, >= 2 on with this many rows making a key
+                              frequent: frequent keys are joined as cross products          */
     int32_t theta_groups;  /* log2 of the theta/band group count (0 = auto, <= 10)      */
     int32_t nlj_tile_r;    /* R rows per nested-loop tile (0 = auto; multiple of 256)   */
     int32_t reserved[9];

@@ -23,8 +23,11 @@ constexpr uint32_t SC_DROP = 0xFFFFu;    // digit of a filtered row
 
 // Digit = bits of the multiplicative key hash: (khash(k) >> shift) & mask.
 struct HashDigit {
+    static constexpr int kFilterWords = 0;
     int shift;
     uint32_t mask;
+    __device__ __forceinline__ void bind(uint32_t*) {}
+    __device__ __forceinline__ bool is_special(uint32_t) const { return false; }
     template <typename K>
     __device__ __forceinline__ uint32_t operator()(K k) const {
         return (khash(k) >> shift) & mask;
@@ -43,7 +46,9 @@ struct RangeParams {
 };
 
 struct RangeDigit {
+    static constexpr int kFilterWords = 0;
     const RangeParams* p;
+    __device__ __forceinline__ void bind(uint32_t*) {}
     template <typename K>
     __device__ __forceinline__ uint32_t operator()(K k) const {
         return (uint32_t)(((uint64_t)((int64_t)k - (int64_t)p->lo)) >> p->shift);
@@ -86,11 +91,14 @@ struct __align__(8) Row<int64_t, true> {
 // One read of a key column: sets the key's bit in the presence bitmap
 // (Algorithm 1's Map1/Reduce1 key set, as a bitmap) and counts first-pass
 // digits (unfiltered, an upper bound of each region's survivors).
-template <typename K>
+template <typename K, typename Digit>
 __global__ void __launch_bounds__(512)
 k_presence_hist(const K* __restrict__ keys, int64_t n, uint32_t* __restrict__ bitmap,
-                uint32_t fmask, HashDigit dg, int nd, unsigned long long* __restrict__ hist) {
+                uint32_t fmask, Digit dg0, int nd, unsigned long long* __restrict__ hist) {
     extern __shared__ uint32_t s_h[];
+    __shared__ uint32_t s_dgf[Digit::kFilterWords > 0 ? Digit::kFilterWords : 1];
+    Digit dg = dg0;
+    dg.bind(s_dgf);
     if (hist)
         for (int i = threadIdx.x; i < nd; i += blockDim.x) s_h[i] = 0;
     __syncthreads();
@@ -100,27 +108,34 @@ k_presence_hist(const K* __restrict__ keys, int64_t n, uint32_t* __restrict__ bi
     if (vec) {
         const int64_t nv = n / 4;
         const int4* kv = reinterpret_cast<const int4*>(keys);
-        for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < nv; i += stride) {
-            int4 q = __ldcs(kv + i);
+        const int64_t nvw = (nv + 31) & ~(int64_t)31;  // warps stay converged for the merge
+        for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < nvw; i += stride) {
+            const bool in = i < nv;
+            int4 q = in ? __ldcs(kv + i) : make_int4(0, 0, 0, 0);
             int32_t v[4] = {q.x, q.y, q.z, q.w};
 #pragma unroll
             for (int j = 0; j < 4; j++) {
-                if (bitmap) {
-                    uint32_t b = fbits((K)v[j]) & fmask;
+                const uint32_t d = in ? dg((K)v[j]) : 0u;
+                if (bitmap && in && !dg.is_special(d)) {
+                    const uint32_t b = fbits((K)v[j]) & fmask;
                     atomicOr(&bitmap[b >> 5], 1u << (b & 31));
                 }
-                if (hist) atomicAdd(&s_h[dg((K)v[j])], 1u);
+                if (hist && in) atomicAdd(&s_h[d], 1u);
             }
         }
         start = nv * 4;
     }
-    for (int64_t i = start + (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) {
-        K k = keys[i];
-        if (bitmap) {
-            uint32_t b = fbits(k) & fmask;
+    const int64_t rem = n - start;
+    const int64_t remw = (rem + 31) & ~(int64_t)31;
+    for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < remw; t += stride) {
+        const bool in = t < rem;
+        const K k = in ? keys[start + t] : (K)0;
+        const uint32_t d = in ? dg(k) : 0u;
+        if (bitmap && in && !dg.is_special(d)) {
+            const uint32_t b = fbits(k) & fmask;
             atomicOr(&bitmap[b >> 5], 1u << (b & 31));
         }
-        if (hist) atomicAdd(&s_h[dg(k)], 1u);
+        if (hist && in) atomicAdd(&s_h[d], 1u);
     }
     __syncthreads();
     if (hist)
@@ -176,10 +191,13 @@ template <typename K, typename Digit>
 __global__ void __launch_bounds__(SC_T)
 k_seg_hist(const K* __restrict__ keys, const uint64_t* __restrict__ seg_begin,
            const uint64_t* __restrict__ seg_count, const uint64_t* __restrict__ tile_prefix,
-           int nseg, Digit dg, int nd, unsigned long long* __restrict__ hist,
+           int nseg, Digit dg0, int nd, unsigned long long* __restrict__ hist,
            unsigned int* __restrict__ work) {
     extern __shared__ uint32_t s_h[];
     __shared__ uint64_t s_tp[SC_FMAX + 1];
+    __shared__ uint32_t s_dgf[Digit::kFilterWords > 0 ? Digit::kFilterWords : 1];
+    Digit dg = dg0;
+    dg.bind(s_dgf);
     for (int i = threadIdx.x; i <= nseg; i += blockDim.x) s_tp[i] = tile_prefix[i];
     for (int i = threadIdx.x; i < nd; i += blockDim.x) s_h[i] = 0;
     __syncthreads();
@@ -226,9 +244,12 @@ template <typename R, typename Digit>
 __global__ void __launch_bounds__(SC_T)
 k_seg_hist_rows(const R* __restrict__ rows, const uint64_t* __restrict__ seg_begin,
                 const uint64_t* __restrict__ seg_count, const uint64_t* __restrict__ tile_prefix, int nseg,
-                Digit dg, int nd, unsigned long long* __restrict__ hist) {
+                Digit dg0, int nd, unsigned long long* __restrict__ hist) {
     extern __shared__ uint32_t s_h[];
     __shared__ uint64_t s_tp[SC_FMAX + 1];
+    __shared__ uint32_t s_dgf[Digit::kFilterWords > 0 ? Digit::kFilterWords : 1];
+    Digit dg = dg0;
+    dg.bind(s_dgf);
     for (int i = threadIdx.x; i <= nseg; i += blockDim.x) s_tp[i] = tile_prefix[i];
     for (int i = threadIdx.x; i < nd; i += blockDim.x) s_h[i] = 0;
     __syncthreads();
@@ -362,7 +383,7 @@ __device__ __forceinline__ void scatter_issue(TileDesc* d, const PartIn<K, HB>& 
 template <typename K, bool HB, bool FILTER, typename Digit>
 __global__ void __launch_bounds__(SC_T, 2)
 k_scatter(PartIn<K, HB> in, const uint64_t* __restrict__ seg_begin, const uint64_t* __restrict__ seg_count,
-          const uint64_t* __restrict__ tile_prefix, int nseg, Digit dg, int nd,
+          const uint64_t* __restrict__ tile_prefix, int nseg, Digit dg0, int nd,
           const uint32_t* __restrict__ other, uint32_t fmask, unsigned long long* __restrict__ cursor,
           Row<K, HB>* __restrict__ out, unsigned int* __restrict__ err) {
     using SM = ScatterSmem<K, HB>;
@@ -378,6 +399,9 @@ k_scatter(PartIn<K, HB> in, const uint64_t* __restrict__ seg_begin, const uint64
     __shared__ TileDesc desc[2];
     __shared__ __align__(8) uint64_t bar;
     __shared__ uint64_t s_tp[SC_FMAX + 1];
+    __shared__ uint32_t s_dgf[Digit::kFilterWords > 0 ? Digit::kFilterWords : 1];
+    Digit dg = dg0;
+    dg.bind(s_dgf);
 
     // Tiles are dealt round-robin: block b takes tiles b, b + grid, ...
     for (int i = threadIdx.x; i <= nseg; i += SC_T) s_tp[i] = tile_prefix[i];

@@ -18,23 +18,32 @@
 //   5. one exact allocation, then the emit pass repeats build and probe and
 //      writes (R.payload, S.payload) pairs at the scanned offsets.
 #include "jn_algos.h"
+#include "jn_heavy.cuh"
 #include "jn_partition.cuh"
 
 namespace jnx {
 
 constexpr int HJ_T = 512;          // threads per join block
-constexpr int HJ_CAP = 4096;       // R rows per shared-memory table
-constexpr int HJ_SCH = 4096;       // S rows per work item
+constexpr int HJ_CAP = 4096;       // R rows per shared-memory table (int32 keys)
+constexpr int HJ_SCH = 2048;       // S rows per staged chunk
 constexpr int HJ_LGNB_MAX = 11;    // at most 2048 buckets
 constexpr int HJ_PAD = 16;         // rows of slack for 16-byte widened copies
+constexpr uint64_t CE_PAIRS = 1u << 16;  // cross-product pairs per work chunk
 
-// Items of partition p: ceil(nr / CAP) R chunks x ceil(ns / SCH) S chunks.
-__global__ void k_items(const uint64_t* __restrict__ roff, const uint64_t* __restrict__ soff, int P,
+// Items of partition p: one per chunk of HJ_CAP R rows; each item probes
+// every S row of the partition, HJ_SCH rows at a time.
+__global__ void k_items(const uint64_t* __restrict__ roff, const uint64_t* __restrict__ soff, int P, int cap,
                         uint64_t* __restrict__ items) {
     int p = blockIdx.x * blockDim.x + threadIdx.x;
     if (p >= P) return;
     uint64_t nr = roff[p + 1] - roff[p], ns = soff[p + 1] - soff[p];
-    items[p] = (nr && ns) ? ((nr + HJ_CAP - 1) / HJ_CAP) * ((ns + HJ_SCH - 1) / HJ_SCH) : 0;
+    items[p] = (nr && ns) ? (nr + cap - 1) / cap : 0;
+}
+
+// R rows per shared-memory table: 4096 for int32 keys, 2048 for int64.
+template <typename K>
+__host__ __device__ constexpr int cap_of() {
+    return sizeof(K) == 4 ? HJ_CAP : HJ_CAP / 2;
 }
 
 __device__ __forceinline__ int bucket_bits(int rn) {
@@ -48,32 +57,28 @@ __device__ __forceinline__ uint32_t bucket_of(uint32_t h, int bits, int lg) {
     return lg == 0 ? 0u : ((h << bits) >> (32 - lg));
 }
 
-// One work item: rows [rbeg, rbeg + rn) of R and [sbeg, sbeg + sn) of S.
+// One work item: rows [rbeg, rbeg + rn) of R against all rows
+// [sbeg, sbeg + sn) of S of the same partition.
 struct Item {
     unsigned long long rbeg, sbeg;
     int rn, sn;
 };
 
-// Writes the items of every partition (its R chunks x S chunks) at
-// items[item_prefix[p] ...].
+// items[it] for every item: its partition is the last p with item_prefix[p] <= it.
 __global__ void k_item_desc(const uint64_t* __restrict__ roff, const uint64_t* __restrict__ soff,
-                            const uint64_t* __restrict__ item_prefix, int P, Item* __restrict__ items) {
-    const int p = blockIdx.x * blockDim.x + threadIdx.x;
-    if (p >= P) return;
-    const uint64_t i0 = item_prefix[p], i1 = item_prefix[p + 1];
-    if (i0 == i1) return;
-    const uint64_t nr = roff[p + 1] - roff[p], ns = soff[p + 1] - soff[p];
-    const uint64_t nrc = (nr + HJ_CAP - 1) / HJ_CAP;
-    for (uint64_t it = i0; it < i1; it++) {
-        const uint64_t local = it - i0;
-        const uint64_t rc = local % nrc, sc = local / nrc;
-        Item d;
-        d.rbeg = roff[p] + rc * HJ_CAP;
-        d.rn = (int)min((uint64_t)HJ_CAP, nr - rc * HJ_CAP);
-        d.sbeg = soff[p] + sc * HJ_SCH;
-        d.sn = (int)min((uint64_t)HJ_SCH, ns - sc * HJ_SCH);
-        items[it] = d;
-    }
+                            const uint64_t* __restrict__ item_prefix, int P, int cap, uint64_t nitems,
+                            Item* __restrict__ items) {
+    const uint64_t it = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (it >= nitems) return;
+    const int p = find_segment(item_prefix, P, it);
+    const uint64_t rc = it - item_prefix[p];
+    const uint64_t nr = roff[p + 1] - roff[p];
+    Item d;
+    d.rbeg = roff[p] + rc * cap;
+    d.rn = (int)min((uint64_t)cap, nr - rc * cap);
+    d.sbeg = soff[p];
+    d.sn = (int)(soff[p + 1] - soff[p]);
+    items[it] = d;
 }
 
 // Starts the copy of rows [beg, beg + n) into `g` (widened to 16 bytes);
@@ -93,69 +98,151 @@ __device__ __forceinline__ uint32_t span_off(uint64_t beg) {
     return (uint32_t)(beg * sizeof(R) - ((beg * sizeof(R)) & ~15ull));
 }
 
+// Shared-memory layout of the join kernel (bytes), shared by host and device.
+template <typename K, int MODE>
+struct JoinSmem {
+    using R = Row<K, false>;
+    static constexpr int CAP = cap_of<K>();
+    static constexpr int GR = CAP + 32 / (int)sizeof(R) + 2;     // staged R rows (widened span)
+    static constexpr int GS = HJ_SCH + 32 / (int)sizeof(R) + 2;  // staged S rows per buffer
+    static constexpr int TS = (CAP * 5) / 4;                     // open-addressing slots (count modes)
+    static constexpr size_t STAGE = (size_t)(GR + 2 * GS) * sizeof(R);
+    static constexpr size_t TABLE =
+        MODE == MODE_EMIT ? (size_t)CAP * (sizeof(K) + 4) + 4u * (1u << HJ_LGNB_MAX)
+                          : (size_t)TS * (sizeof(K) + 4) + (MODE == MODE_AGG ? (size_t)TS * 8 : 0);
+    static constexpr size_t BYTES = STAGE + TABLE;
+};
+
+// Slot of a key in the open-addressing table of a partition: the hash bits
+// below the partition bits, spread over TS slots.
+__device__ __forceinline__ uint32_t oa_slot(uint32_t h, int bits, int ts) {
+    const uint32_t x = (h << bits) * 0x9E3779B1u;
+    return (uint32_t)(((uint64_t)x * (uint64_t)ts) >> 32);
+}
+
 // MODE_COUNT: item_val[it] = matches of the item.
 // MODE_AGG:   as COUNT, and chk += sum over matches of f(r) * g(s).
 // MODE_EMIT:  writes the item's pairs at out[item_off[it] ...].
-// Items are dealt round-robin over the persistent blocks.  The R and S rows
-// of an item are staged by TMA bulk copies: the next item's R rows load
-// while this item probes, its S rows while it builds.  The partitioned rows
-// are library scratch, 16-byte aligned and padded by HJ_PAD rows, so every
-// widened copy stays inside its allocation.
-template <typename K, int MODE>
+//
+// Items (a chunk of R rows of one partition against all S rows of that
+// partition) are dealt round-robin over the persistent blocks.  R rows and S
+// chunks are staged in shared memory by TMA bulk copies: the next item's R
+// rows load while this item probes, and S chunks stream through two buffers,
+// the next chunk loading while the current one is probed.
+//   emit:         R is counting-sorted into buckets (key, payload) and every
+//                 match is written;
+//   count / agg:  equal R keys are folded into one open-addressing slot
+//                 (key, multiplicity [, sum of f]), so a probe costs one
+//                 lookup however many rows share the key.
+// The partitioned rows are library scratch, 16-byte aligned and padded by
+// HJ_PAD rows, so every widened copy stays inside its allocation.
+template <typename K, int MODE, bool MERGE = false>
 __global__ void __launch_bounds__(HJ_T, 2)
 k_hash_join(const Row<K, false>* __restrict__ rrows, const Row<K, false>* __restrict__ srows,
             const Item* __restrict__ items, uint64_t nitems, int bits, unsigned long long* __restrict__ item_val,
             unsigned long long* __restrict__ chk, const uint64_t* __restrict__ item_off,
             jn_pair* __restrict__ out, unsigned int* __restrict__ err) {
     using R = Row<K, false>;
-    constexpr int GR = HJ_CAP + 32 / (int)sizeof(R) + 2;
-    constexpr int GS = HJ_SCH + 32 / (int)sizeof(R) + 2;
+    using L = JoinSmem<K, MODE>;
+    constexpr int CAP = L::CAP;
+    constexpr int TS = L::TS;
     extern __shared__ __align__(128) unsigned char smem[];
-    unsigned char* g_r = smem;                                  // GR rows
-    unsigned char* g_s = g_r + GR * sizeof(R);                  // GS rows
-    K* s_key = reinterpret_cast<K*>(g_s + GS * sizeof(R));      // HJ_CAP
-    int32_t* s_pay = reinterpret_cast<int32_t*>(s_key + HJ_CAP);
-    uint32_t* s_off = reinterpret_cast<uint32_t*>(s_pay + HJ_CAP);  // 1 << HJ_LGNB_MAX
+    unsigned char* g_r = smem;
+    unsigned char* g_s0 = g_r + L::GR * sizeof(R);
+    unsigned char* g_s1 = g_s0 + L::GS * sizeof(R);
+    unsigned char* tab = g_s1 + L::GS * sizeof(R);
+    // emit table
+    K* s_key = reinterpret_cast<K*>(tab);
+    int32_t* s_pay = reinterpret_cast<int32_t*>(s_key + CAP);
+    uint32_t* s_off = reinterpret_cast<uint32_t*>(s_pay + CAP);
+    // count-mode table
+    K* o_key = reinterpret_cast<K*>(tab);
+    uint32_t* o_cnt = reinterpret_cast<uint32_t*>(o_key + TS);
+    unsigned long long* o_f = reinterpret_cast<unsigned long long*>(o_cnt + TS);
     __shared__ unsigned long long tmp64[33];
     __shared__ uint32_t tmp32[33];
-    __shared__ uint32_t s_cursor;
-    __shared__ __align__(8) uint64_t bar_r, bar_s;
+    __shared__ uint32_t s_cursor, s_mincnt;
+    __shared__ unsigned long long s_minf;
+    __shared__ __align__(8) uint64_t bar_r, bar_s[2];
+    const K KMIN = key_sentinel<K>();
 
     const int lane = threadIdx.x & 31;
     uint64_t it = blockIdx.x;
     if (it >= nitems) return;
     Item d = items[it];
+    // S-chunk stream: chunk q of this block sits in buffer q & 1; thread 0
+    // stages chunks ahead (producer), every thread consumes them in order.
+    uint64_t p_it = it;  // producer: item and chunk of the next chunk to stage
+    int p_sc = 0, p_nsc = (d.sn + HJ_SCH - 1) / HJ_SCH;
+    uint64_t p_sbeg = d.sbeg;
+    int p_sn = d.sn;
+    bool p_valid = true;
+    uint32_t qp = 0, qc = 0;  // chunks staged / consumed
+    auto stage_next_chunk = [&]() {  // thread 0 only
+        if (!p_valid) return;
+        const int n = min(HJ_SCH, p_sn - p_sc * HJ_SCH);
+        stage_span<R>(srows, p_sbeg + (uint64_t)p_sc * HJ_SCH, n, (qp & 1) ? g_s1 : g_s0, &bar_s[qp & 1]);
+        qp++;
+        if (++p_sc == p_nsc) {
+            p_it += gridDim.x;
+            p_valid = p_it < nitems;
+            if (p_valid) {
+                const Item x = items[p_it];
+                p_sbeg = x.sbeg;
+                p_sn = x.sn;
+                p_nsc = (x.sn + HJ_SCH - 1) / HJ_SCH;
+                p_sc = 0;
+            }
+        }
+    };
     if (threadIdx.x == 0) {
         mbar_init(&bar_r, 1);
-        mbar_init(&bar_s, 1);
+        mbar_init(&bar_s[0], 1);
+        mbar_init(&bar_s[1], 1);
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
         stage_span<R>(rrows, d.rbeg, d.rn, g_r, &bar_r);
-        stage_span<R>(srows, d.sbeg, d.sn, g_s, &bar_s);
+        stage_next_chunk();
+        stage_next_chunk();
         s_cursor = 0;
     }
     __syncthreads();
-    uint32_t phase = 0;
+    uint32_t pr = 0;  // phase of bar_r
+    bool r_pending = true;
+    bool failed = false;
     while (true) {
         const uint64_t itn = it + gridDim.x;
         const bool has_next = itn < nitems;
         Item dn;
-        if (has_next) dn = items[itn];  // used once this item's staging is free
-        const int rn = d.rn, sn = d.sn;
-        const int lg = bucket_bits(rn);
-        const int nb = 1 << lg;
-        for (int i = threadIdx.x; i < nb; i += HJ_T) s_off[i] = 0;
-        bool ok = mbar_wait(&bar_r, phase, err);
-        if (__syncthreads_or(!ok)) {
-            mbar_wait(&bar_r, phase, nullptr);
-            mbar_wait(&bar_s, phase, nullptr);
+        if (has_next) dn = items[itn];  // its R rows load once this item's R staging is free
+        const int rn = d.rn;
+        int lg = 0, nb = 1;
+        if (MODE == MODE_EMIT) {
+            lg = bucket_bits(rn);
+            nb = 1 << lg;
+            for (int i = threadIdx.x; i < nb; i += HJ_T) s_off[i] = 0;
+        } else {
+            for (int i = threadIdx.x; i < TS; i += HJ_T) {
+                o_key[i] = KMIN;
+                o_cnt[i] = 0;
+                if (MODE == MODE_AGG) o_f[i] = 0;
+            }
+            if (threadIdx.x == 0) {
+                s_mincnt = 0;
+                s_minf = 0;
+            }
+        }
+        if (__syncthreads_or(!mbar_wait(&bar_r, pr, err))) {
+            failed = true;
             break;
         }
-        // ---- build: counting sort of the staged R chunk by bucket ----
+        pr ^= 1u;
+        r_pending = false;
         const R* rrow = reinterpret_cast<const R*>(g_r + span_off<R>(d.rbeg));
-        for (int i = threadIdx.x; i < rn; i += HJ_T)
-            atomicAdd(&s_off[bucket_of(khash(rrow[i].key), bits, lg)], 1u);
-        __syncthreads();
-        {
+        if (MODE == MODE_EMIT) {
+            // ---- build: counting sort of the staged R chunk by bucket ----
+            for (int i = threadIdx.x; i < rn; i += HJ_T)
+                atomicAdd(&s_off[bucket_of(khash(rrow[i].key), bits, lg)], 1u);
+            __syncthreads();
             uint32_t v[4];
             uint32_t sum = 0;
 #pragma unroll
@@ -172,69 +259,163 @@ k_hash_join(const Row<K, false>* __restrict__ rrows, const Row<K, false>* __rest
                 if (i < nb) s_off[i] = pre;
                 pre += v[j];
             }
-        }
-        __syncthreads();
-        for (int i = threadIdx.x; i < rn; i += HJ_T) {
-            const R x = rrow[i];
-            const uint32_t pos = atomicAdd(&s_off[bucket_of(khash(x.key), bits, lg)], 1u);
-            s_key[pos] = x.key;
-            s_pay[pos] = x.pay;
-        }
-        __syncthreads();
-        // bucket b now holds rows [b ? s_off[b-1] : 0, s_off[b]); R staging is free
-        if (threadIdx.x == 0 && has_next) stage_span<R>(rrows, dn.rbeg, dn.rn, g_r, &bar_r);
-        ok = mbar_wait(&bar_s, phase, err);
-        if (__syncthreads_or(!ok)) {
-            mbar_wait(&bar_s, phase, nullptr);
-            if (has_next) mbar_wait(&bar_r, phase ^ 1u, nullptr);
-            break;
-        }
-        // ---- probe with the staged S chunk ----
-        const R* srow = reinterpret_cast<const R*>(g_s + span_off<R>(d.sbeg));
-        unsigned long long acc = 0, csum = 0;
-        const int rounds = (sn + HJ_T - 1) / HJ_T;
-        for (int r = 0; r < rounds; r++) {
-            const int j = r * HJ_T + threadIdx.x;
-            uint32_t lo = 0, hi = 0;
-            R x;
-            x.key = 0;
-            x.pay = 0;
-            if (j < sn) {
-                x = srow[j];
-                const uint32_t b = bucket_of(khash(x.key), bits, lg);
-                lo = b ? s_off[b - 1] : 0u;
-                hi = s_off[b];
+            __syncthreads();
+            for (int i = threadIdx.x; i < rn; i += HJ_T) {
+                const R x = rrow[i];
+                const uint32_t pos = atomicAdd(&s_off[bucket_of(khash(x.key), bits, lg)], 1u);
+                s_key[pos] = x.key;
+                s_pay[pos] = x.pay;
             }
-            uint32_t m = 0;
-            unsigned long long fs = 0;
-            for (uint32_t e = lo; e < hi; e++) {
-                if (s_key[e] == x.key) {
-                    m++;
-                    if (MODE == MODE_AGG) fs += chk_f(s_pay[e]);
+            // bucket b now holds rows [b ? s_off[b-1] : 0, s_off[b])
+        } else {
+            // ---- build: fold equal keys into one slot (key, count [, sum f]) ----
+            // MERGE (skewed input): lanes of a warp holding the same key insert
+            // once, with their count, to spare contended shared atomics
+            const int rnw = MERGE ? (rn + 31) & ~31 : rn;
+            for (int i = threadIdx.x; i < rnw; i += HJ_T) {
+                const bool in = i < rn;
+                R x;
+                x.key = KMIN;
+                x.pay = 0;
+                if (in) x = rrow[i];
+                uint32_t cnt = 1;
+                unsigned long long fv = 0;
+                if (MERGE) {
+                    const unsigned act = __ballot_sync(0xffffffffu, in);
+                    if (!in) continue;
+                    const unsigned peers = __match_any_sync(act, x.key);
+                    if (MODE == MODE_AGG) {
+                        // sum f over the peer group, gathered by its leader
+                        const unsigned long long mine = chk_f(x.pay);
+                        for (unsigned m = peers; m; m &= m - 1) fv += __shfl_sync(peers, mine, __ffs(m) - 1);
+                    }
+                    if ((threadIdx.x & 31) != (unsigned)(__ffs(peers) - 1)) continue;
+                    cnt = __popc(peers);
+                } else if (MODE == MODE_AGG) {
+                    fv = chk_f(x.pay);
+                }
+                if (x.key == KMIN) {  // the empty-slot marker itself: kept aside
+                    atomicAdd(&s_mincnt, cnt);
+                    if (MODE == MODE_AGG) atomicAdd(&s_minf, fv);
+                    continue;
+                }
+                uint32_t h = oa_slot(khash(x.key), bits, TS);
+                for (int probe = 0; probe < TS; probe++) {
+                    K old;
+                    if (sizeof(K) == 4)
+                        old = (K)atomicCAS(reinterpret_cast<int*>(o_key) + h, (int)KMIN, (int)x.key);
+                    else
+                        old = (K)atomicCAS(reinterpret_cast<unsigned long long*>(o_key) + h,
+                                           (unsigned long long)KMIN, (unsigned long long)x.key);
+                    if (old == KMIN || old == x.key) {
+                        atomicAdd(&o_cnt[h], cnt);
+                        if (MODE == MODE_AGG) atomicAdd(&o_f[h], fv);
+                        break;
+                    }
+                    h = (h + 1 == (uint32_t)TS) ? 0u : h + 1;
                 }
             }
-            if (MODE == MODE_EMIT) {
-                const uint32_t incl = warp_incl_scan(m);
-                const uint32_t wt = __shfl_sync(0xffffffffu, incl, 31);
-                uint32_t base = 0;
-                if (lane == 0 && wt) base = atomicAdd(&s_cursor, wt);
-                base = __shfl_sync(0xffffffffu, base, 0);
-                if (m) {
-                    uint64_t o = item_off[it] + base + (incl - m);
-                    for (uint32_t e = lo; e < hi; e++) {
-                        if (s_key[e] == x.key) {
-                            jn_pair q;
-                            q.r = s_pay[e];
-                            q.s = x.pay;
-                            out[o++] = q;
+        }
+        __syncthreads();
+        // R staging is free: stage the next item's R rows
+        if (threadIdx.x == 0 && has_next) stage_span<R>(rrows, dn.rbeg, dn.rn, g_r, &bar_r);
+        r_pending = has_next;
+        // ---- probe with every S chunk of the partition ----
+        unsigned long long acc = 0, csum = 0;
+        const int nsc = (d.sn + HJ_SCH - 1) / HJ_SCH;
+        for (int sc = 0; sc < nsc; sc++) {
+            const uint32_t b = qc & 1, ph = (qc >> 1) & 1;
+            if (__syncthreads_or(!mbar_wait(&bar_s[b], ph, err))) {
+                failed = true;
+                break;
+            }
+            const uint64_t sbeg = d.sbeg + (uint64_t)sc * HJ_SCH;
+            const int sn = min(HJ_SCH, d.sn - sc * HJ_SCH);
+            const R* srow = reinterpret_cast<const R*>((b ? g_s1 : g_s0) + span_off<R>(sbeg));
+            const int rounds = (sn + HJ_T - 1) / HJ_T;
+            for (int r = 0; r < rounds; r++) {
+                const int j = r * HJ_T + threadIdx.x;
+                R x;
+                x.key = 0;
+                x.pay = 0;
+                uint32_t m = 0;
+                unsigned long long fs = 0;
+                uint32_t lo = 0, hi = 0;
+                if (j < sn) {
+                    x = srow[j];
+                    if (MODE == MODE_EMIT) {
+                        const uint32_t bk = bucket_of(khash(x.key), bits, lg);
+                        lo = bk ? s_off[bk - 1] : 0u;
+                        hi = s_off[bk];
+                        for (uint32_t e = lo; e < hi; e++) m += (s_key[e] == x.key);
+                    } else if (x.key == KMIN) {
+                        m = s_mincnt;
+                        if (MODE == MODE_AGG) fs = s_minf;
+                    } else {
+                        uint32_t h = oa_slot(khash(x.key), bits, TS);
+                        for (int probe = 0; probe < TS; probe++) {
+                            const K kk = o_key[h];
+                            if (kk == x.key) {
+                                m = o_cnt[h];
+                                if (MODE == MODE_AGG) fs = o_f[h];
+                                break;
+                            }
+                            if (kk == KMIN) break;
+                            h = (h + 1 == (uint32_t)TS) ? 0u : h + 1;
                         }
                     }
                 }
-            } else {
-                acc += m;
-                if (MODE == MODE_AGG && m) csum += fs * chk_g(x.pay);
+                if (MODE == MODE_EMIT) {
+                    const uint32_t incl = warp_incl_scan(m);
+                    const uint32_t wt = __shfl_sync(0xffffffffu, incl, 31);
+                    uint32_t base = 0;
+                    if (lane == 0 && wt) base = atomicAdd(&s_cursor, wt);
+                    base = __shfl_sync(0xffffffffu, base, 0);
+                    const uint64_t wbase = item_off[it] + base;
+                    // long buckets are written by the whole warp, 32 entries at a
+                    // time, so their pairs go out in coalesced runs
+                    const bool longb = (hi - lo) > 32;
+                    if (m && !longb) {
+                        uint64_t o = wbase + (incl - m);
+                        for (uint32_t e = lo; e < hi; e++) {
+                            if (s_key[e] == x.key) {
+                                jn_pair q;
+                                q.r = s_pay[e];
+                                q.s = x.pay;
+                                out[o++] = q;
+                            }
+                        }
+                    }
+                    for (unsigned lanes = __ballot_sync(0xffffffffu, m && longb); lanes; lanes &= lanes - 1) {
+                        const int src = __ffs(lanes) - 1;
+                        const uint32_t blo = __shfl_sync(0xffffffffu, lo, src);
+                        const uint32_t bhi = __shfl_sync(0xffffffffu, hi, src);
+                        const K bk = __shfl_sync(0xffffffffu, x.key, src);
+                        const int32_t bp = __shfl_sync(0xffffffffu, x.pay, src);
+                        uint64_t o = wbase + __shfl_sync(0xffffffffu, incl - m, src);
+                        for (uint32_t e0 = blo; e0 < bhi; e0 += 32) {
+                            const uint32_t e = e0 + lane;
+                            const bool hit = e < bhi && s_key[e] == bk;
+                            const unsigned hm = __ballot_sync(0xffffffffu, hit);
+                            if (hit) {
+                                jn_pair q;
+                                q.r = s_pay[e];
+                                q.s = bp;
+                                out[o + __popc(hm & ((1u << lane) - 1))] = q;
+                            }
+                            o += __popc(hm);
+                        }
+                    }
+                } else {
+                    acc += m;
+                    if (MODE == MODE_AGG && m) csum += fs * chk_g(x.pay);
+                }
             }
+            __syncthreads();  // this S buffer is free: stage the chunk after next
+            qc++;
+            if (threadIdx.x == 0) stage_next_chunk();
         }
+        if (failed) break;
         if (MODE != MODE_EMIT) {
             const unsigned long long tot = block_sum(acc, tmp64);
             if (MODE == MODE_AGG) {
@@ -243,24 +424,27 @@ k_hash_join(const Row<K, false>* __restrict__ rrows, const Row<K, false>* __rest
             }
             if (threadIdx.x == 0) item_val[it] = tot;
         }
-        __syncthreads();  // S staging and the table are free
-        if (threadIdx.x == 0) {
-            s_cursor = 0;
-            if (has_next) stage_span<R>(srows, dn.sbeg, dn.sn, g_s, &bar_s);
-        }
         if (!has_next) break;
         __syncthreads();
-        phase ^= 1u;
+        if (threadIdx.x == 0) s_cursor = 0;
         it = itn;
         d = dn;
+    }
+    if (failed) {
+        // let copies in flight land before the block exits (thread 0 knows qp)
+        __shared__ uint32_t s_qp;
+        if (threadIdx.x == 0) s_qp = qp;
+        __syncthreads();
+        if (r_pending) mbar_wait(&bar_r, pr, nullptr);
+        for (uint32_t q = qc; q < s_qp; q++) mbar_wait(&bar_s[q & 1], (q >> 1) & 1, nullptr);
     }
 }
 
 template <typename K>
-static size_t hash_smem() {
-    using R = Row<K, false>;
-    const size_t gr = HJ_CAP + 32 / sizeof(R) + 2, gs = HJ_SCH + 32 / sizeof(R) + 2;
-    return (gr + gs) * sizeof(R) + (size_t)HJ_CAP * (sizeof(K) + 4) + sizeof(uint32_t) * (1u << HJ_LGNB_MAX);
+static size_t hash_smem(int mode) {
+    if (mode == MODE_EMIT) return JoinSmem<K, MODE_EMIT>::BYTES;
+    if (mode == MODE_AGG) return JoinSmem<K, MODE_AGG>::BYTES;
+    return JoinSmem<K, MODE_COUNT>::BYTES;
 }
 
 static int persistent_grid(jn_ctx* c, const void* fn, int threads, size_t smem) {
@@ -275,44 +459,46 @@ static int persistent_grid(jn_ctx* c, const void* fn, int threads, size_t smem) 
 }
 
 // Partitions one table through both passes.  Outputs the partitioned rows
-// and offsets[P + 1].
+// and offsets[P + 1]; with heavy keys, also the heavy rows grouped by key and
+// their offsets[HV_MAX + 1].
 template <typename K>
 struct Partitioned {
     Row<K, false>* rows = nullptr;
-    uint64_t* off = nullptr;  // P + 1 exact offsets
+    uint64_t* off = nullptr;        // P + 1 exact offsets
+    Row<K, false>* hrows = nullptr; // heavy rows grouped by heavy key
+    uint64_t* hoff = nullptr;       // HV_MAX + 1 offsets
 };
 
-template <typename K>
-static jn_status partition_table(jn_ctx* c, Scratch& s, const Cols<K>& T, int b1, int b2,
-                                 const uint32_t* other_bitmap, uint32_t fmask,
-                                 const unsigned long long* hist1, Partitioned<K>* outp,
-                                 uint64_t* d_survivors, unsigned int* work) {
+template <typename K, typename D1>
+static jn_status partition_table(jn_ctx* c, Scratch& s, const Cols<K>& T, int b1, int b2, D1 d1,
+                                 const HeavySet<K>* hs, const uint32_t* other_bitmap, uint32_t fmask,
+                                 const unsigned long long* hist1, Partitioned<K>* outp, uint64_t* d_survivors) {
     using R = Row<K, false>;
     const int F1 = 1 << b1, F2 = 1 << b2, P = F1 * F2;
+    const int nd1 = F1 + (hs ? 1 : 0);  // heavy rows get the extra digit F1
     const uint64_t n = (uint64_t)T.n;
     // ---- pass 1: regions sized by the unfiltered histogram ----
     uint64_t *start1, *seg_b, *seg_c, *tp;
     unsigned long long* cur1;
     R* r1;
-    JN_TRY(s.get(&start1, F1 + 1));
-    JN_TRY(s.get(&cur1, F1));
+    JN_TRY(s.get(&start1, nd1 + 1));
+    JN_TRY(s.get(&cur1, nd1));
     JN_TRY(s.get(&seg_b, F1 + 1));
     JN_TRY(s.get(&seg_c, F1 + 1));
     JN_TRY(s.get(&tp, F1 + 2));
     JN_TRY(s.get(&r1, n + HJ_PAD));
-    JN_TRY(scan_u64(c, reinterpret_cast<const uint64_t*>(hist1), start1, F1));
-    JN_TRY(launch(c, K_MISC, k_init_cursor, dim3((F1 + 255) / 256), dim3(256), 0,
-                  (const uint64_t*)start1, cur1, (int64_t)F1));
+    JN_TRY(scan_u64(c, reinterpret_cast<const uint64_t*>(hist1), start1, nd1));
+    JN_TRY(launch(c, K_MISC, k_init_cursor, dim3((nd1 + 255) / 256), dim3(256), 0,
+                  (const uint64_t*)start1, cur1, (int64_t)nd1));
     JN_TRY(launch(c, K_SEGMENTS, k_one_segment, dim3(1), dim3(32), 0, seg_b, seg_c, tp, n));
     const size_t sm = scatter_smem<K, false>();
-    auto kern1 = other_bitmap ? k_scatter<K, false, true, HashDigit> : k_scatter<K, false, false, HashDigit>;
+    auto kern1 = other_bitmap ? k_scatter<K, false, true, D1> : k_scatter<K, false, false, D1>;
     const int g1 = persistent_grid(c, (const void*)kern1, SC_T, sm);
-    HashDigit d1{32 - b1, (uint32_t)(F1 - 1)};
     PartIn<K, false> in1{T.key, nullptr, T.pay, nullptr, n};
     JN_TRY(launch(c, K_SCATTER, kern1, dim3(g1), dim3(SC_T), sm, in1, (const uint64_t*)seg_b,
-                  (const uint64_t*)seg_c, (const uint64_t*)tp, 1, d1, F1, other_bitmap, fmask, cur1, r1,
+                  (const uint64_t*)seg_c, (const uint64_t*)tp, 1, d1, nd1, other_bitmap, fmask, cur1, r1,
                   c->d_err));
-    // ---- pass 1 regions become the segments of pass 2 ----
+    // ---- pass 1 regions (without the heavy one) become the segments of pass 2 ----
     JN_TRY(launch(c, K_SEGMENTS, k_segments, dim3(1), dim3(1024), 0, (const unsigned long long*)cur1,
                   (const uint64_t*)start1, F1, seg_c, tp, d_survivors));
     unsigned long long* hist2;
@@ -342,12 +528,43 @@ static jn_status partition_table(jn_ctx* c, Scratch& s, const Cols<K>& T, int b1
                   r2, c->d_err));
     outp->rows = r2;
     outp->off = start2;
+    if (!hs) return JN_OK;
+    // ---- heavy rows (region F1) grouped by heavy key ----
+    uint64_t *hseg_c, *htp, *hstart;
+    unsigned long long *hhist, *hcur;
+    R* hr;
+    JN_TRY(s.get(&hseg_c, 2));
+    JN_TRY(s.get(&htp, 3));
+    JN_TRY(s.get(&hhist, HV_MAX));
+    JN_TRY(s.get(&hstart, HV_MAX + 1));
+    JN_TRY(s.get(&hcur, HV_MAX));
+    JN_TRY(s.get(&hr, n + HJ_PAD));
+    JN_TRY(zero(c, hhist, sizeof(unsigned long long) * HV_MAX));
+    JN_TRY(launch(c, K_SEGMENTS, k_segments, dim3(1), dim3(32), 0, (const unsigned long long*)(cur1 + F1),
+                  (const uint64_t*)(start1 + F1), 1, hseg_c, htp, (uint64_t*)nullptr));
+    HeavyIdxDigit<K> dh{*hs};
+    auto khh = k_seg_hist_rows<R, HeavyIdxDigit<K>>;
+    const int ghh = persistent_grid(c, (const void*)khh, SC_T, sizeof(uint32_t) * HV_MAX);
+    JN_TRY(launch(c, K_HIST, khh, dim3(ghh), dim3(SC_T), sizeof(uint32_t) * HV_MAX, (const R*)r1,
+                  (const uint64_t*)(start1 + F1), (const uint64_t*)hseg_c, (const uint64_t*)htp, 1, dh, HV_MAX,
+                  hhist));
+    JN_TRY(scan_u64(c, reinterpret_cast<const uint64_t*>(hhist), hstart, HV_MAX));
+    JN_TRY(launch(c, K_MISC, k_init_cursor, dim3((HV_MAX + 255) / 256), dim3(256), 0, (const uint64_t*)hstart,
+                  hcur, (int64_t)HV_MAX));
+    auto kern3 = k_scatter<K, false, false, HeavyIdxDigit<K>>;
+    const int g3 = persistent_grid(c, (const void*)kern3, SC_T, sm);
+    JN_TRY(launch(c, K_SCATTER, kern3, dim3(g3), dim3(SC_T), sm, in2, (const uint64_t*)(start1 + F1),
+                  (const uint64_t*)hseg_c, (const uint64_t*)htp, 1, dh, HV_MAX, (const uint32_t*)nullptr, 0u,
+                  hcur, hr, c->d_err));
+    outp->hrows = hr;
+    outp->hoff = hstart;
     return JN_OK;
 }
 
 template <typename K>
 jn_status run_hash(jn_ctx* c, const Cols<K>& R, const Cols<K>& S, int mode, OutPlan* plan,
                    RunResult* res) {
+    using RW = Row<K, false>;
     const uint64_t nr = (uint64_t)R.n, ns = (uint64_t)S.n;
     jn_run_info& info = c->info;
     if (nr == 0 || ns == 0) {
@@ -362,19 +579,26 @@ jn_status run_hash(jn_ctx* c, const Cols<K>& R, const Cols<K>& S, int mode, OutP
     }
     const jn_tuning& tu = c->tune;
     // ---- parameters ----
+    const bool heavy = tu.heavy >= 1 || (tu.heavy == -1 && nr + ns >= (1u << 20));
+    const int64_t heavy_rows = tu.heavy >= 2 ? tu.heavy : cap_of<K>() / 4;  // rows that make a key heavy
+    bool pre = tu.prefilter == 1 || (tu.prefilter == -1 && nr + ns >= (1u << 22));
     int b = tu.radix_bits;
     if (b == 0) {
-        uint64_t target = HJ_CAP / 2;  // expected R rows per partition
+        // expected R rows per partition: the table capacity when the filter
+        // will thin the rows out, half of it otherwise
+        uint64_t target = pre ? cap_of<K>() : cap_of<K>() / 2;
         b = ceil_log2((nr + target - 1) / target);
         if (b > 20) b = 20;
     }
     int b1 = tu.radix_bits1 ? tu.radix_bits1 : b / 2;
     if (b1 > b) b1 = b;
-    if (b1 > 10) b1 = 10;
+    const int b1max = heavy ? 9 : 10;  // pass 1 needs F1 (+1 heavy) <= 1024 digits
+    if (b1 > b1max) b1 = b1max;
     if (b - b1 > 10) b1 = b - 10;
+    if (b1 > b1max) return fail(c, JN_ERR_UNSUPPORTED, "radix bits too large for two passes");
     const int b2 = b - b1;
     const int F1 = 1 << b1, P = 1 << b;
-    bool pre = tu.prefilter == 1 || (tu.prefilter == -1 && nr + ns >= (1u << 22));
+    const int nd1 = F1 + (heavy ? 1 : 0);
     int fb = tu.filter_bits ? tu.filter_bits : ceil_log2(nr + ns) + 1;
     if (fb < 10) fb = 10;
     if (fb > 28 && tu.filter_bits == 0) fb = 28;
@@ -382,49 +606,92 @@ jn_status run_hash(jn_ctx* c, const Cols<K>& R, const Cols<K>& S, int mode, OutP
     const uint32_t fmask = (uint32_t)((uint64_t(1) << fb) - 1);
 
     Scratch s(c);
-    unsigned int* work;
-    uint64_t* d_small;  // [0] R survivors, [1] S survivors
-    JN_TRY(s.get(&work, 4));
+    uint64_t* d_small;  // [0] R survivors, [1] S survivors, [2] items, [3] count, [4] checksum, [5] heavy
     JN_TRY(s.get(&d_small, 8));
+    JN_TRY(zero(c, d_small, 64));
     uint32_t *bmR = nullptr, *bmS = nullptr;
     unsigned long long *h1R, *h1S;
-    JN_TRY(s.get(&h1R, F1));
-    JN_TRY(s.get(&h1S, F1));
-    JN_TRY(zero(c, h1R, sizeof(unsigned long long) * F1));
-    JN_TRY(zero(c, h1S, sizeof(unsigned long long) * F1));
+    JN_TRY(s.get(&h1R, nd1));
+    JN_TRY(s.get(&h1S, nd1));
+    JN_TRY(zero(c, h1R, sizeof(unsigned long long) * nd1));
+    JN_TRY(zero(c, h1S, sizeof(unsigned long long) * nd1));
     if (pre) {
         JN_TRY(s.get(&bmR, fwords));
         JN_TRY(s.get(&bmS, fwords));
         JN_TRY(zero(c, bmR, fwords * 4));
         JN_TRY(zero(c, bmS, fwords * 4));
     }
+    // ---- 0. heavy keys from a strided sample of both key columns ----
+    HeavySet<K> hs{};
+    int* d_hcount = nullptr;
+    if (heavy) {
+        K *tk, *hkeys, *htk;
+        unsigned int* tc;
+        int* htidx;
+        const int slots = 1 << HV_SAMPLE_LOG;
+        JN_TRY(s.get(&tk, slots));
+        JN_TRY(s.get(&tc, 2 * slots));
+        JN_TRY(s.get(&hkeys, HV_MAX));
+        JN_TRY(s.get(&htk, HV_SLOTS));
+        JN_TRY(s.get(&htidx, HV_SLOTS));
+        JN_TRY(s.get(&d_hcount, 1));
+        const int64_t target = 1 << 19;  // samples per table
+        const int64_t sr = max((int64_t)1, (int64_t)nr / target), ss = max((int64_t)1, (int64_t)ns / target);
+        // a key is heavy when about heavy_rows rows of one table carry it
+        const unsigned thr_r = (unsigned)max((int64_t)(sr > 1 ? 3 : 1), heavy_rows / sr);
+        const unsigned thr_s = (unsigned)max((int64_t)(ss > 1 ? 3 : 1), heavy_rows / ss);
+        const unsigned thr = thr_r < thr_s ? thr_r : thr_s;
+        JN_TRY(launch(c, K_HEAVY_SAMPLE, k_sample_init<K>, dim3(256), dim3(256), 0, tk, tc, slots));
+        JN_TRY(launch(c, K_HEAVY_SAMPLE, k_sample<K>, dim3(256), dim3(256), 0, R.key, R.n, sr, 0, tk, tc));
+        JN_TRY(launch(c, K_HEAVY_SAMPLE, k_sample<K>, dim3(256), dim3(256), 0, S.key, S.n, ss, 1, tk, tc));
+        JN_TRY(zero(c, d_hcount, sizeof(int)));
+        JN_TRY(launch(c, K_HEAVY_SELECT, k_heavy_collect<K>, dim3(2 * c->num_sms), dim3(256), 0, (const K*)tk,
+                      (const unsigned int*)tc, thr, hkeys, d_hcount));
+        JN_TRY(launch(c, K_HEAVY_SELECT, k_heavy_table<K>, dim3(1), dim3(1024), 0, (const K*)hkeys, htk, htidx,
+                      d_hcount));
+        hs = HeavySet<K>{htk, htidx, hkeys, d_hcount};
+        if (pre) JN_TRY(launch(c, K_HEAVY_SELECT, k_heavy_bits<K>, dim3(1), dim3(1024), 0, hs, bmR, bmS, fmask));
+    }
     // ---- 1. presence bitmaps + first-pass histograms ----
-    HashDigit d1{32 - b1, (uint32_t)(F1 - 1)};
-    {
-        auto kp = k_presence_hist<K>;
-        const size_t smp = sizeof(uint32_t) * F1;
+    Partitioned<K> PR, PS;
+    auto pass_all = [&](auto d1) -> jn_status {
+        using D1 = decltype(d1);
+        auto kp = k_presence_hist<K, D1>;
+        const size_t smp = sizeof(uint32_t) * nd1;
         int per = 0;
         cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, kp, 512, smp);
         if (per < 1) per = 1;
         const int g = per * c->num_sms;
-        JN_TRY(launch(c, K_PRESENCE, kp, dim3(g), dim3(512), smp, R.key, R.n, bmR, fmask, d1, F1, h1R));
-        JN_TRY(launch(c, K_PRESENCE, kp, dim3(g), dim3(512), smp, S.key, S.n, bmS, fmask, d1, F1, h1S));
+        JN_TRY(launch(c, K_PRESENCE, kp, dim3(g), dim3(512), smp, R.key, R.n, bmR, fmask, d1, nd1, h1R));
+        JN_TRY(launch(c, K_PRESENCE, kp, dim3(g), dim3(512), smp, S.key, S.n, bmS, fmask, d1, nd1, h1S));
+        // ---- 2-3. two partition passes per table (filtered by the other's bitmap) ----
+        JN_TRY((partition_table<K, D1>(c, s, R, b1, b2, d1, heavy ? &hs : nullptr, bmS, fmask, h1R, &PR,
+                                       d_small + 0)));
+        JN_TRY((partition_table<K, D1>(c, s, S, b1, b2, d1, heavy ? &hs : nullptr, bmR, fmask, h1S, &PS,
+                                       d_small + 1)));
+        return JN_OK;
+    };
+    if (heavy) {
+        HeavyHashDigit<K> d1{32 - b1, (uint32_t)(F1 - 1), (uint32_t)F1, hs, nullptr};
+        JN_TRY(pass_all(d1));
+    } else {
+        HashDigit d1{32 - b1, (uint32_t)(F1 - 1)};
+        JN_TRY(pass_all(d1));
     }
-    // ---- 2-3. two partition passes per table (filtered by the other's bitmap) ----
-    Partitioned<K> PR, PS;
-    JN_TRY(partition_table<K>(c, s, R, b1, b2, bmS, fmask, h1R, &PR, d_small + 0, work));
-    JN_TRY(partition_table<K>(c, s, S, b1, b2, bmR, fmask, h1S, &PS, d_small + 1, work));
     // ---- 4. work items and the count pass ----
     uint64_t *items, *iprefix;
     JN_TRY(s.get(&items, P));
     JN_TRY(s.get(&iprefix, P + 1));
     JN_TRY(launch(c, K_ITEMS, k_items, dim3((P + 255) / 256), dim3(256), 0, (const uint64_t*)PR.off,
-                  (const uint64_t*)PS.off, P, items));
+                  (const uint64_t*)PS.off, P, cap_of<K>(), items));
     JN_TRY(scan_u64(c, items, iprefix, P));
-    uint64_t h[3];
+    uint64_t h[8];
     JN_TRY(launch(c, K_MISC, k_copy_words, dim3(1), dim3(32), 0, (const uint64_t*)(iprefix + P),
                   d_small + 2, 1));
-    JN_TRY(read_back(c, d_small, h, 3));
+    if (heavy) JN_CUDA(c, cudaMemcpyAsync(d_small + 7, d_hcount, 4, cudaMemcpyDeviceToDevice, c->stream));
+    JN_TRY(read_back(c, d_small, h, 8));
+    // many frequent keys in the sample: expect duplicate-heavy partitions too
+    const bool skewed = heavy && (h[7] & 0xffffffffu) >= 64;
     const uint64_t nitems = h[2];
     info.r_survivors = h[0];
     info.s_survivors = h[1];
@@ -435,55 +702,84 @@ jn_status run_hash(jn_ctx* c, const Cols<K>& R, const Cols<K>& S, int mode, OutP
     info.radix_bits1 = b1;
     info.filter_bits = pre ? fb : 0;
     info.heavy_keys = 0;
-    if (nitems == 0) {
-        res->count = 0;
-        res->checksum = 0;
-        if (mode == MODE_EMIT) {
-            JN_TRY(out_prepare(c, s, 0, *plan));
-            JN_TRY(out_finish(c, 0, *plan));
-        }
-        return JN_OK;
-    }
-    // the join kernel stages rows with 16-byte bulk copies from these columns
+    // the join kernel stages rows with 16-byte bulk copies from these arrays
     if ((((uintptr_t)PR.rows) | ((uintptr_t)PS.rows)) & 15)
         return fail(c, JN_ERR_CUDA, "partition scratch is not 16-byte aligned");
     Item* idesc;
-    JN_TRY(s.get(&idesc, nitems));
-    JN_TRY(launch(c, K_ITEMS, k_item_desc, dim3((P + 255) / 256), dim3(256), 0, (const uint64_t*)PR.off,
-                  (const uint64_t*)PS.off, (const uint64_t*)iprefix, P, idesc));
     unsigned long long *ival, *chk;
     uint64_t* ioff;
-    JN_TRY(s.get(&ival, nitems));
+    JN_TRY(s.get(&idesc, nitems + 1));
+    JN_TRY(s.get(&ival, nitems + 1));
     JN_TRY(s.get(&ioff, nitems + 1));
     JN_TRY(s.get(&chk, 1));
     JN_TRY(zero(c, chk, 8));
-    const size_t smj = hash_smem<K>();
-    auto kc = (mode == MODE_AGG) ? k_hash_join<K, MODE_AGG> : k_hash_join<K, MODE_COUNT>;
-    const int gj = (int)min((uint64_t)persistent_grid(c, (const void*)kc, HJ_T, smj), nitems);
-    JN_TRY(launch(c, K_HASH_COUNT, kc, dim3(gj), dim3(HJ_T), smj, (const Row<K, false>*)PR.rows,
-                  (const Row<K, false>*)PS.rows, (const Item*)idesc, nitems, b, ival, chk,
-                  (const uint64_t*)nullptr, (jn_pair*)nullptr, c->d_err));
+    if (nitems) {
+        JN_TRY(launch(c, K_ITEMS, k_item_desc, dim3((unsigned)ceil_div(nitems, 256)), dim3(256), 0,
+                      (const uint64_t*)PR.off, (const uint64_t*)PS.off, (const uint64_t*)iprefix, P, cap_of<K>(),
+                      nitems, idesc));
+        const int cm = mode == MODE_AGG ? MODE_AGG : MODE_COUNT;
+        const size_t smc = hash_smem<K>(cm);
+        auto kc = (cm == MODE_AGG) ? (skewed ? k_hash_join<K, MODE_AGG, true> : k_hash_join<K, MODE_AGG, false>)
+                                   : (skewed ? k_hash_join<K, MODE_COUNT, true> : k_hash_join<K, MODE_COUNT, false>);
+        const int gj = (int)min((uint64_t)persistent_grid(c, (const void*)kc, HJ_T, smc), nitems);
+        JN_TRY(launch(c, K_HASH_COUNT, kc, dim3(gj), dim3(HJ_T), smc, (const RW*)PR.rows, (const RW*)PS.rows,
+                      (const Item*)idesc, nitems, b, ival, chk, (const uint64_t*)nullptr, (jn_pair*)nullptr,
+                      c->d_err));
+    }
     JN_TRY(scan_u64(c, reinterpret_cast<const uint64_t*>(ival), ioff, (int64_t)nitems));
+    // ---- heavy keys: c_R(h) * c_S(h) pairs each ----
+    uint64_t *hp = nullptr, *hpoff = nullptr, *hch = nullptr, *hchp = nullptr;
+    if (heavy) {
+        JN_TRY(s.get(&hp, HV_MAX));
+        JN_TRY(s.get(&hpoff, HV_MAX + 1));
+        JN_TRY(s.get(&hch, HV_MAX));
+        JN_TRY(s.get(&hchp, HV_MAX + 1));
+        unsigned long long *fsum, *gsum;
+        JN_TRY(s.get(&fsum, HV_MAX));
+        JN_TRY(s.get(&gsum, HV_MAX));
+        JN_TRY(zero(c, fsum, 8 * HV_MAX));
+        JN_TRY(zero(c, gsum, 8 * HV_MAX));
+        JN_TRY(launch(c, K_HEAVY_SELECT, k_heavy_pairs<RW>, dim3(mode == MODE_AGG ? 64 : 1, HV_MAX), dim3(256), 0,
+                      (const RW*)PR.hrows, (const uint64_t*)PR.hoff, (const RW*)PS.hrows, (const uint64_t*)PS.hoff,
+                      (const int*)d_hcount, hp, hch, fsum, gsum, mode == MODE_AGG ? 1 : 0, (uint64_t)CE_PAIRS));
+        if (mode == MODE_AGG)
+            JN_TRY(launch(c, K_HEAVY_SELECT, k_heavy_chk, dim3(1), dim3(1024), 0, (const unsigned long long*)fsum,
+                          (const unsigned long long*)gsum, chk));
+        JN_TRY(scan_u64(c, hp, hpoff, HV_MAX));
+        JN_TRY(scan_u64(c, hch, hchp, HV_MAX));
+        JN_TRY(launch(c, K_MISC, k_copy_words, dim3(1), dim3(32), 0, (const uint64_t*)(hpoff + HV_MAX),
+                      d_small + 5, 1));
+        JN_CUDA(c, cudaMemcpyAsync(d_small + 6, d_hcount, 4, cudaMemcpyDeviceToDevice, c->stream));
+    }
     JN_TRY(launch(c, K_MISC, k_copy_words, dim3(1), dim3(32), 0, (const uint64_t*)(ioff + nitems),
                   d_small + 3, 1));
     JN_TRY(launch(c, K_MISC, k_copy_words, dim3(1), dim3(32), 0, (const uint64_t*)chk, d_small + 4, 1));
-    uint64_t hc[2];
-    JN_TRY(read_back(c, d_small + 3, hc, 2));
-    res->count = hc[0];
+    uint64_t hc[4];
+    JN_TRY(read_back(c, d_small + 3, hc, 4));
+    const uint64_t normal = hc[0], heavy_pairs = heavy ? hc[2] : 0;
+    const uint64_t total = normal + heavy_pairs;
+    res->count = total;
     res->checksum = hc[1];
-    info.result = hc[0];
+    info.result = total;
+    info.heavy_keys = heavy ? (hc[3] & 0xffffffffu) : 0;
     if (mode != MODE_EMIT) return JN_OK;
     // ---- 5. exact allocation and the emit pass ----
-    JN_TRY(out_prepare(c, s, hc[0], *plan));
-    if (hc[0] > 0) {
+    JN_TRY(out_prepare(c, s, total, *plan));
+    if (normal > 0) {
         auto ke = k_hash_join<K, MODE_EMIT>;
-        const int ge = (int)min((uint64_t)persistent_grid(c, (const void*)ke, HJ_T, smj), nitems);
-        JN_TRY(launch(c, K_HASH_EMIT, ke, dim3(ge), dim3(HJ_T), smj, (const Row<K, false>*)PR.rows,
-                      (const Row<K, false>*)PS.rows, (const Item*)idesc, nitems, b,
-                      (unsigned long long*)nullptr, (unsigned long long*)nullptr, (const uint64_t*)ioff,
-                      plan->dev, c->d_err));
+        const size_t sme = hash_smem<K>(MODE_EMIT);
+        const int ge = (int)min((uint64_t)persistent_grid(c, (const void*)ke, HJ_T, sme), nitems);
+        JN_TRY(launch(c, K_HASH_EMIT, ke, dim3(ge), dim3(HJ_T), sme, (const RW*)PR.rows, (const RW*)PS.rows,
+                      (const Item*)idesc, nitems, b, (unsigned long long*)nullptr, (unsigned long long*)nullptr,
+                      (const uint64_t*)ioff, plan->dev, c->d_err));
     }
-    JN_TRY(out_finish(c, hc[0], *plan));
+    if (heavy_pairs > 0) {
+        JN_TRY(launch(c, K_CROSS_EMIT, k_cartesian<RW>, dim3(8 * c->num_sms), dim3(256), 0, (const RW*)PR.hrows,
+                      (const uint64_t*)PR.hoff, (const RW*)PS.hrows, (const uint64_t*)PS.hoff,
+                      (const uint64_t*)hpoff, (const uint64_t*)hchp, HV_MAX, (uint64_t)CE_PAIRS, normal,
+                      plan->dev));
+    }
+    JN_TRY(out_finish(c, total, *plan));
     return JN_OK;
 }
 

@@ -242,3 +242,62 @@ def test_one_column_theta_regions(ctx, op, dt):
     assert np.array_equal(canon(got), exp)
     c, h = jn.jn_aggregate(ctx, jn.JN_ALGO_THETA, R, S, jn.pred(op, jn.JN_ANY, -1))
     assert c == exp.shape[0] and h == O.checksum_pairs(exp)
+
+
+# ------------------------------------------------------------- skewed keys --
+
+def skewed(n, d, theta, seed, stream, dtype=torch.int32):
+    ranks = datagen.zipf_ranks(n, theta, d, seed, stream)
+    if dtype == torch.int32:
+        return datagen.rank_to_key32(ranks, 20, seed)
+    return datagen.rank_to_key64(ranks, seed)
+
+
+@pytest.mark.parametrize("theta", [0.5, 1.0])
+@pytest.mark.parametrize("dt", [torch.int32, torch.int64])
+def test_hash_heavy_keys(ctx, theta, dt):
+    nr, ns, d = 60000, 90000, 1 << 14
+    r = skewed(nr, d, theta, 21, 0, dt)
+    s = skewed(ns, d, theta, 21, 1, dt)
+    rp = datagen.uniform_int(nr, I32_MIN, I32_MAX, 21, 5)
+    sp = datagen.uniform_int(ns, I32_MIN, I32_MAX, 21, 6)
+    cnt, chk = O.equi_count_checksum(r.numpy(), s.numpy(), rp.numpy(), sp.numpy())
+    R = jn.table(r.to(DEV), payload=rp.to(DEV))
+    S = jn.table(s.to(DEV), payload=sp.to(DEV))
+    for heavy in (64, 0):
+        ctx.set_tuning(heavy=heavy, prefilter=1)
+        try:
+            assert jn.jn_aggregate(ctx, jn.JN_ALGO_HASH, R, S) == (cnt, chk)
+            info = ctx.run_info()
+            if heavy:
+                assert info["heavy_keys"] > 0
+            if cnt <= 30_000_000:
+                got = jn.jn_hash(ctx, R, S)
+                assert got.shape[0] == cnt
+                assert O.checksum_pairs(got.cpu().numpy()) == chk
+        finally:
+            ctx.set_tuning(heavy=-1, prefilter=-1)
+    if cnt <= 3_000_000:
+        ctx.set_tuning(heavy=64)
+        try:
+            got = jn.jn_hash(ctx, R, S)
+        finally:
+            ctx.set_tuning(heavy=-1)
+        exp = canon(O.hash_join(r.numpy(), s.numpy(), rp.numpy(), sp.numpy()))
+        assert np.array_equal(canon(got), exp)
+
+
+def test_hash_one_key_everywhere(ctx):
+    # every row carries the same key: a single heavy key, output = |R| * |S|
+    r = torch.full((3000,), 42, dtype=torch.int32)
+    s = torch.full((5000,), 42, dtype=torch.int32)
+    for heavy in (2, 0):
+        ctx.set_tuning(heavy=heavy)
+        try:
+            got = jn.jn_hash(ctx, jn.table(r.to(DEV)), jn.table(s.to(DEV)))
+        finally:
+            ctx.set_tuning(heavy=-1)
+        assert got.shape[0] == 3000 * 5000
+        g = got.cpu().numpy()
+        assert np.array_equal(np.bincount(g[:, 0], minlength=3000), np.full(3000, 5000))
+        assert np.array_equal(np.bincount(g[:, 1], minlength=5000), np.full(5000, 3000))
