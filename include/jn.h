@@ -97,7 +97,8 @@ typedef struct {
                               frequent: frequent keys are joined as cross products          */
     int32_t theta_groups;  /* log2 of the theta/band group count (0 = auto, <= 10)      */
     int32_t nlj_tile_r;    /* R rows per nested-loop tile (0 = auto; multiple of 256)   */
-    int32_t reserved[9];
+    int32_t graphs;        /* 1: jn_batch captures and replays its phases as CUDA graphs */
+    int32_t reserved[8];
 } jn_tuning;
 
 /* Per-kernel launch statistics (profiling mode). */
@@ -128,8 +129,10 @@ typedef struct jn_ctx jn_ctx;
 /* ------------------------------------------------------------ context --- */
 
 /* Create a context on CUDA device `device` issuing work on `stream` (a
- * cudaStream_t; NULL = the legacy default stream).  The context owns its
- * scratch memory and a device memory pool for outputs. */
+ * cudaStream_t; NULL = the legacy default stream).  Scratch and outputs are
+ * stream-ordered allocations from the device's default memory pool (whose
+ * release threshold the library raises so freed blocks are reused); outputs
+ * may outlive the context. */
 jn_status jn_create(jn_ctx** ctx, int device, void* stream);
 void jn_destroy(jn_ctx* ctx);
 jn_status jn_set_stream(jn_ctx* ctx, void* stream);
@@ -198,10 +201,90 @@ jn_status jn_hash(jn_ctx* ctx, const jn_table* R, const jn_table* S,
 jn_status jn_theta(jn_ctx* ctx, const jn_table* R, const jn_table* S, int32_t op, int64_t band,
                    jn_pair** out, uint64_t capacity, uint64_t* n_out);
 
+/* One join of a batch. */
+typedef struct {
+    jn_table R;
+    jn_table S;
+    int32_t op;        /* band < 0: must be JN_EQ (equi-join on key); band >= 0: op on key */
+    int32_t reserved;  /* must be 0 */
+    int64_t band;      /* < 0: equi-join; >= 0: band join |R.key2 - S.key2| <= band        */
+} jn_join;
+
+/* Runs `count` independent joins as one batch and writes all their pairs to
+ * one device output (jn.h's output convention; the output must be device
+ * memory, and *n_out receives the total).  first[i] and pairs[i] (host,
+ * count words each) receive where join i's pairs start and how many there
+ * are: they are out[first[i] .. first[i] + pairs[i]).  Equi-joins of a batch
+ * share every phase (one radix pass over all their tables, one count pass
+ * and one emit pass over a single work queue of (join, partition) items);
+ * band joins are counted and written one after another.  The whole batch
+ * makes one exact output allocation.  This is the batched form of the
+ * Reducer = grid hierarchy of Sec. 3.3.4: many small joins fill the GPU
+ * together instead of one launch sequence each. */
+jn_status jn_batch(jn_ctx* ctx, int32_t count, const jn_join* joins, jn_pair** out, uint64_t capacity,
+                   uint64_t* n_out, uint64_t* first, uint64_t* pairs);
+
 /* Release an output allocated by a join (stream ordered on the context's
  * stream; with ctx == NULL, on the legacy default stream, so results may
  * outlive their context). */
 void jn_free(jn_ctx* ctx, jn_pair* p);
+
+/* ------------------------------------------------------------- serving --- */
+
+/* A request server over this library: requests are queued from any host
+ * thread and run by `slots` worker threads, each with its own context and
+ * CUDA stream, so the work of several requests overlaps on the device.
+ * Small requests (|R| + |S| < coalesce_rows) waiting at the same time are
+ * run together as one jn_batch (at most max_batch of them); larger requests
+ * run alone after an exact count pass and wait until their scratch estimate
+ * plus exact output fits memory_budget next to the outputs still held.
+ * Tables registered with the server stay resident on the device.  The paper
+ * has no serving layer; this is the request loop around its join method. */
+typedef struct jn_server jn_server;
+
+typedef struct {
+    int32_t slots;           /* worker threads / streams, 1..16                     */
+    int32_t coalesce_rows;   /* requests below this many rows are coalesced         */
+    int32_t max_batch;       /* requests per coalesced batch, >= 1                  */
+    int32_t graphs;          /* 1: batches replay their phases as CUDA graphs       */
+    uint64_t memory_budget;  /* device bytes for scratch and held outputs           */
+} jn_server_config;
+
+typedef struct {
+    int32_t r_handle;        /* > 0: registered table used as R; otherwise R below  */
+    int32_t s_handle;        /* > 0: registered table used as S; otherwise S below  */
+    jn_table R;              /* device tables, complete when submitted (the server reads
+                                them on its own streams) and valid until completion  */
+    jn_table S;
+    int32_t op;              /* band < 0: JN_EQ; band >= 0: op on key               */
+    int32_t reserved;        /* must be 0                                           */
+    int64_t band;            /* < 0: equi-join; >= 0: band join on key2             */
+} jn_request;
+
+typedef struct {
+    int32_t status;          /* jn_status of the request                            */
+    int32_t reserved;
+    uint64_t pairs;          /* result size                                         */
+    jn_pair* out;            /* device pairs, owned by the server until released    */
+    double queue_ms;         /* submit -> start on the device                       */
+    double run_ms;           /* start -> pairs complete                              */
+    double total_ms;         /* submit -> pairs complete                             */
+} jn_result;
+
+typedef struct {
+    uint64_t submitted, completed, failed, batches, queued;
+    uint64_t held_bytes, peak_bytes, resident_bytes;
+} jn_server_stats;
+
+jn_status jn_server_create(jn_server** s, int device, const jn_server_config* cfg);
+void jn_server_destroy(jn_server* s);          /* finishes queued requests, frees all */
+/* Copies a table (host or device columns) into server-owned device memory. */
+jn_status jn_server_register(jn_server* s, const jn_table* t, int32_t* handle);
+jn_status jn_server_unregister(jn_server* s, int32_t handle);
+jn_status jn_server_submit(jn_server* s, const jn_request* req, uint64_t* ticket);
+jn_status jn_server_wait(jn_server* s, uint64_t ticket, jn_result* res);  /* blocks */
+jn_status jn_server_release(jn_server* s, uint64_t ticket);  /* frees the pairs of a done request */
+jn_status jn_server_stats_get(jn_server* s, jn_server_stats* out);
 
 /* ------------------------------------------------------- introspection --- */
 
@@ -212,6 +295,7 @@ jn_status jn_kernel_stats(jn_ctx* ctx, jn_kernel_stat* out, int32_t max, int32_t
 jn_status jn_reset_stats(jn_ctx* ctx);
 jn_status jn_last_run_info(const jn_ctx* ctx, jn_run_info* info);
 uint64_t jn_launch_count(const jn_ctx* ctx);           /* kernels launched since creation */
+int32_t jn_pointer_is_device(const void* p);            /* 1 if p is device (or managed) memory */
 
 #ifdef __cplusplus
 }

@@ -41,6 +41,10 @@ jn_status run_hash(jn_ctx* c, const Cols<K>& R, const Cols<K>& S, int mode, OutP
                    RunResult* res);
 
 template <typename K>
+jn_status run_batch_hash(jn_ctx* c, int n, const Cols<K>* Rs, const Cols<K>* Ss, OutPlan* plan,
+                         uint64_t* offsets, uint64_t extra);
+
+template <typename K>
 jn_status run_nlj(jn_ctx* c, const Cols<K>& R, const Cols<K>& S, const jn_pred& pred, int mode,
                   OutPlan* plan, RunResult* res);
 

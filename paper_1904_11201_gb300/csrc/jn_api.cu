@@ -2,6 +2,8 @@
 // dispatch on key type, and the output convention of jn.h.
 #include <string.h>
 
+#include <vector>
+
 #include "jn_algos.h"
 
 namespace jnx {
@@ -128,6 +130,69 @@ static jn_status run(jn_ctx* c, int algo, const jn_table* R, const jn_table* S, 
     return JN_OK;
 }
 
+template <typename K>
+static jn_status batch_typed(jn_ctx* c, int count, const jn_join* joins, jn_pair** out, uint64_t capacity,
+                             uint64_t* n_out, uint64_t* first, uint64_t* pairs) {
+    Scratch s(c);
+    std::vector<int> eq, bd;
+    for (int i = 0; i < count; i++) (joins[i].band < 0 ? eq : bd).push_back(i);
+    std::vector<Cols<K>> Rs(eq.size()), Ss(eq.size());
+    for (size_t j = 0; j < eq.size(); j++) {
+        JN_TRY(stage<K>(c, s, &joins[eq[j]].R, false, &Rs[j]));
+        JN_TRY(stage<K>(c, s, &joins[eq[j]].S, false, &Ss[j]));
+    }
+    // band joins: exact counts first, so the batch allocates once
+    std::vector<Cols<K>> BR(bd.size()), BS(bd.size());
+    std::vector<uint64_t> bcnt(bd.size());
+    uint64_t extra = 0;
+    for (size_t j = 0; j < bd.size(); j++) {
+        JN_TRY(stage<K>(c, s, &joins[bd[j]].R, true, &BR[j]));
+        JN_TRY(stage<K>(c, s, &joins[bd[j]].S, true, &BS[j]));
+        RunResult rr;
+        JN_TRY(run_theta<K>(c, BR[j], BS[j], joins[bd[j]].op, joins[bd[j]].band, MODE_COUNT, nullptr, &rr));
+        bcnt[j] = rr.count;
+        extra += rr.count;
+    }
+    OutPlan plan;
+    plan.user_out = out;
+    plan.capacity = capacity;
+    plan.n_out = n_out;
+    uint64_t eq_total = 0;
+    if (!eq.empty()) {
+        std::vector<uint64_t> off(eq.size() + 1);
+        JN_TRY(run_batch_hash<K>(c, (int)eq.size(), Rs.data(), Ss.data(), &plan, off.data(), extra));
+        for (size_t j = 0; j < eq.size(); j++) {
+            first[eq[j]] = off[j];
+            pairs[eq[j]] = off[j + 1] - off[j];
+        }
+        eq_total = off[eq.size()];
+    } else {
+        JN_TRY(out_prepare(c, s, extra, plan));
+        if (plan.host_copy) return fail(c, JN_ERR_INVALID, "batch outputs must be device memory");
+        JN_TRY(out_finish(c, extra, plan));
+    }
+    jn_pair* base = *out;
+    uint64_t at = eq_total;
+    for (size_t j = 0; j < bd.size(); j++) {
+        first[bd[j]] = at;
+        pairs[bd[j]] = bcnt[j];
+        if (bcnt[j]) {
+            jn_pair* dst = base + at;
+            uint64_t got = 0;
+            OutPlan bp;
+            bp.user_out = &dst;
+            bp.capacity = bcnt[j];
+            bp.n_out = &got;
+            RunResult rr;
+            JN_TRY(run_theta<K>(c, BR[j], BS[j], joins[bd[j]].op, joins[bd[j]].band, MODE_EMIT, &bp, &rr));
+        }
+        at += bcnt[j];
+    }
+    *n_out = at;
+    c->info.result = at;
+    return JN_OK;
+}
+
 }  // namespace jnx
 
 using namespace jnx;
@@ -152,6 +217,37 @@ jn_status jn_nested_loop(jn_ctx* ctx, const jn_table* R, const jn_table* S, cons
 jn_status jn_hash(jn_ctx* ctx, const jn_table* R, const jn_table* S, jn_pair** out, uint64_t capacity,
                   uint64_t* n_out) {
     return run(ctx, JN_ALGO_HASH, R, S, nullptr, MODE_EMIT, out, capacity, n_out, nullptr, nullptr);
+}
+
+jn_status jn_batch(jn_ctx* ctx, int32_t count, const jn_join* joins, jn_pair** out, uint64_t capacity,
+                   uint64_t* n_out, uint64_t* first, uint64_t* pairs) {
+    if (!ctx) return JN_ERR_INVALID;
+    ctx->err.clear();
+    if (count < 0 || (count > 0 && (!joins || !first || !pairs)) || !out || !n_out)
+        return fail(ctx, JN_ERR_INVALID, "jn_batch: bad arguments");
+    if (count == 0) {
+        *n_out = 0;
+        return JN_OK;
+    }
+    const int32_t kt = joins[0].R.key_type;
+    for (int i = 0; i < count; i++) {
+        const jn_join& j = joins[i];
+        const bool band = j.band >= 0;
+        JN_TRY(check_table(ctx, &j.R, "R", band));
+        JN_TRY(check_table(ctx, &j.S, "S", band));
+        if (j.R.key_type != kt || j.S.key_type != kt)
+            return fail(ctx, JN_ERR_INVALID, "jn_batch: all tables of a batch share one key type");
+        if (j.reserved != 0 || !valid_op(j.op)) return fail(ctx, JN_ERR_INVALID, "jn_batch: bad join");
+        if (!band && j.op != JN_EQ)
+            return fail(ctx, JN_ERR_UNSUPPORTED, "jn_batch: a join without a band must be an equi-join");
+    }
+    JN_CUDA(ctx, cudaSetDevice(ctx->device));
+    ctx->info = jn_run_info();
+    const uint64_t l0 = ctx->launches_total;
+    jn_status st = kt == JN_KEY_I32 ? batch_typed<int32_t>(ctx, count, joins, out, capacity, n_out, first, pairs)
+                                    : batch_typed<int64_t>(ctx, count, joins, out, capacity, n_out, first, pairs);
+    ctx->info.kernel_launches = ctx->launches_total - l0;
+    return st;
 }
 
 jn_status jn_theta(jn_ctx* ctx, const jn_table* R, const jn_table* S, int32_t op, int64_t band,

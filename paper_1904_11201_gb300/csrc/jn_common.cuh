@@ -58,10 +58,11 @@ struct jn_ctx {
     int num_sms = 0;
     size_t smem_optin = 0;
     cudaStream_t stream = nullptr;
-    cudaMemPool_t pool = nullptr;
+    cudaMemPool_t pool = nullptr;  // the device's default pool (never destroyed)
     jn_tuning tune{};
     uint64_t* h_small = nullptr;  // pinned host words for count read-back
     unsigned int* d_err = nullptr;  // device error word (bounded waits that ran out)
+    cudaStream_t capture_stream = nullptr;  // private stream for CUDA-graph capture
     bool profiling = false;
     std::vector<jnx::PendingTiming> pending;
     std::vector<cudaEvent_t> spare_events;

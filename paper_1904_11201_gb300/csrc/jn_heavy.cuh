@@ -157,6 +157,7 @@ struct HeavyIdxDigit {
     static constexpr int kFilterWords = 0;
     HeavySet<K> hs;
     __device__ __forceinline__ void bind(uint32_t*) {}
+    __device__ __forceinline__ void set_seg(int) {}
     __device__ __forceinline__ uint32_t operator()(K k) const {
         const int i = hv_lookup(hs, k);
         return i < 0 ? 0u : (uint32_t)i;  // every row of the heavy region has a heavy key
@@ -174,6 +175,7 @@ struct HeavyHashDigit {
     HeavySet<K> hs;
     const uint32_t* f;
     __device__ __forceinline__ bool is_special(uint32_t d) const { return d == heavy_digit; }
+    __device__ __forceinline__ void set_seg(int) {}
     // Fills the block's filter; all threads call it (it synchronises).
     __device__ __forceinline__ void bind(uint32_t* smem_filter) {
         hv_filter_fill(smem_filter, hs);

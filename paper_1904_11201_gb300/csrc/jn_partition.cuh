@@ -27,10 +27,26 @@ struct HashDigit {
     int shift;
     uint32_t mask;
     __device__ __forceinline__ void bind(uint32_t*) {}
+    __device__ __forceinline__ void set_seg(int) {}
     __device__ __forceinline__ bool is_special(uint32_t) const { return false; }
     template <typename K>
     __device__ __forceinline__ uint32_t operator()(K k) const {
         return (khash(k) >> shift) & mask;
+    }
+};
+
+// Per-segment hash digit for batches of joins: segment s takes the top
+// bits[s] bits of the key hash (0 bits: a single partition).
+struct SegHashDigit {
+    static constexpr int kFilterWords = 0;
+    const int* bits;
+    int b;
+    __device__ __forceinline__ void bind(uint32_t*) {}
+    __device__ __forceinline__ void set_seg(int s) { b = bits[s]; }
+    __device__ __forceinline__ bool is_special(uint32_t) const { return false; }
+    template <typename K>
+    __device__ __forceinline__ uint32_t operator()(K k) const {
+        return b ? (khash(k) >> (32 - b)) : 0u;
     }
 };
 
@@ -49,6 +65,7 @@ struct RangeDigit {
     static constexpr int kFilterWords = 0;
     const RangeParams* p;
     __device__ __forceinline__ void bind(uint32_t*) {}
+    __device__ __forceinline__ void set_seg(int) {}
     template <typename K>
     __device__ __forceinline__ uint32_t operator()(K k) const {
         return (uint32_t)(((uint64_t)((int64_t)k - (int64_t)p->lo)) >> p->shift);
@@ -230,6 +247,22 @@ k_seg_hist(const K* __restrict__ keys, const uint64_t* __restrict__ seg_begin,
 
 // Input of a partition pass: column buffers (the caller's table) or rows
 // (the output of an earlier pass).
+// Columns of one segment of a batch (a table of one join of the batch).
+template <typename K>
+struct SegCols {
+    const K* key;
+    const int32_t* pay;  // NULL = row index
+    uint64_t n;
+    uint64_t pad;
+};
+
+// A tile of a batch: rows [beg, beg + cnt) of segment seg.
+struct TileRef {
+    unsigned long long beg;
+    int seg;
+    int cnt;
+};
+
 template <typename K, bool HB>
 struct PartIn {
     const K* key;           // columns (when rows == NULL)
@@ -237,6 +270,8 @@ struct PartIn {
     const int32_t* pay;     // NULL = row index
     const Row<K, HB>* rows; // rows (when not NULL)
     uint64_t rows_ok;       // rows that may be read (allocation size)
+    const SegCols<K>* segs; // batches: per-segment columns (key, pay), else NULL
+    const TileRef* tiles;   // batches: tile list, else NULL (tiles from the segment prefix)
 };
 
 // Digit histogram of every segment of a row array (see k_seg_hist).
@@ -323,7 +358,15 @@ struct ScatterSmem {
 // prefix held in shared memory.
 __device__ __forceinline__ void tile_rows(const uint64_t* tp, int nseg, uint64_t t,
                                           const uint64_t* __restrict__ seg_begin,
-                                          const uint64_t* __restrict__ seg_count, TileDesc* d) {
+                                          const uint64_t* __restrict__ seg_count, TileDesc* d,
+                                          const TileRef* tiles = nullptr) {
+    if (tiles) {
+        const TileRef x = tiles[t];
+        d->seg = x.seg;
+        d->beg = x.beg;
+        d->cnt = x.cnt;
+        return;
+    }
     const int seg = find_segment(tp, nseg, t);
     const uint64_t off = (t - tp[seg]) * SC_TILE;
     d->seg = seg;
@@ -360,11 +403,14 @@ __device__ __forceinline__ void scatter_issue(TileDesc* d, const PartIn<K, HB>& 
         tma_load_1d(stage, reinterpret_cast<const unsigned char*>(in.rows) + b0, nb, bar);
         return;
     }
+    const K* ikey = in.segs ? in.segs[d->seg].key : in.key;
+    const int32_t* ipay = in.segs ? in.segs[d->seg].pay : in.pay;
+    const uint64_t iok = in.segs ? in.segs[d->seg].n : in.rows_ok;
     uint64_t bk = 0, bb = 0, bp = 0;
     uint32_t nk = 0, nbb = 0, np = 0;
-    bool ok = byte_span(in.key, d->beg, d->cnt, sizeof(K), in.rows_ok, &bk, &nk);
-    if (ok && HB) ok = byte_span(in.key_b, d->beg, d->cnt, sizeof(K), in.rows_ok, &bb, &nbb);
-    if (ok && in.pay) ok = byte_span(in.pay, d->beg, d->cnt, 4, in.rows_ok, &bp, &np);
+    bool ok = byte_span(ikey, d->beg, d->cnt, sizeof(K), iok, &bk, &nk);
+    if (ok && HB) ok = byte_span(in.key_b, d->beg, d->cnt, sizeof(K), iok, &bb, &nbb);
+    if (ok && ipay) ok = byte_span(ipay, d->beg, d->cnt, 4, iok, &bp, &np);
     if (!ok) return;
     d->tma = 1;
     d->koff = (int)(d->beg - bk / sizeof(K));
@@ -375,9 +421,9 @@ __device__ __forceinline__ void scatter_issue(TileDesc* d, const PartIn<K, HB>& 
     int32_t* gp = reinterpret_cast<int32_t*>(gb + (HB ? SM::GK : 0));
     fence_proxy_async();
     mbar_arrive_expect_tx(bar, nk + nbb + np);
-    tma_load_1d(gk, reinterpret_cast<const unsigned char*>(in.key) + bk, nk, bar);
+    tma_load_1d(gk, reinterpret_cast<const unsigned char*>(ikey) + bk, nk, bar);
     if (HB) tma_load_1d(gb, reinterpret_cast<const unsigned char*>(in.key_b) + bb, nbb, bar);
-    if (in.pay) tma_load_1d(gp, reinterpret_cast<const unsigned char*>(in.pay) + bp, np, bar);
+    if (ipay) tma_load_1d(gp, reinterpret_cast<const unsigned char*>(ipay) + bp, np, bar);
 }
 
 template <typename K, bool HB, bool FILTER, typename Digit>
@@ -404,17 +450,19 @@ k_scatter(PartIn<K, HB> in, const uint64_t* __restrict__ seg_begin, const uint64
     dg.bind(s_dgf);
 
     // Tiles are dealt round-robin: block b takes tiles b, b + grid, ...
-    for (int i = threadIdx.x; i <= nseg; i += SC_T) s_tp[i] = tile_prefix[i];
+    // batches pass a tile list (tile_prefix[0] = tile count) instead of segments
+    if (!in.tiles)
+        for (int i = threadIdx.x; i <= nseg; i += SC_T) s_tp[i] = tile_prefix[i];
     for (int i = threadIdx.x; i < nd; i += SC_T) s_cnt[i] = 0;
     __syncthreads();
-    const uint64_t ntiles = s_tp[nseg];
+    const uint64_t ntiles = in.tiles ? tile_prefix[0] : s_tp[nseg];
     uint64_t t = blockIdx.x;
     if (threadIdx.x == 0) {
         mbar_init(&bar, 1);
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
         desc[0].valid = t < ntiles;
         if (t < ntiles) {
-            tile_rows(s_tp, nseg, t, seg_begin, seg_count, &desc[0]);
+            tile_rows(s_tp, nseg, t, seg_begin, seg_count, &desc[0], in.tiles);
             scatter_issue<K, HB>(&desc[0], in, stage, &bar);
         }
     }
@@ -431,7 +479,7 @@ k_scatter(PartIn<K, HB> in, const uint64_t* __restrict__ seg_begin, const uint64
         const uint64_t tn = t + gridDim.x;
         TileDesc dn;
         dn.valid = tn < ntiles;
-        if (threadIdx.x == 0 && dn.valid) tile_rows(s_tp, nseg, tn, seg_begin, seg_count, &dn);
+        if (threadIdx.x == 0 && dn.valid) tile_rows(s_tp, nseg, tn, seg_begin, seg_count, &dn, in.tiles);
         bool ok = true;
         if (d.tma) ok = mbar_wait(&bar, phase, err);
         if (__syncthreads_or(!ok)) {
@@ -441,6 +489,9 @@ k_scatter(PartIn<K, HB> in, const uint64_t* __restrict__ seg_begin, const uint64
         if (d.tma) phase ^= 1u;
         const uint64_t beg = d.beg;
         const int cnt = d.cnt;
+        dg.set_seg(d.seg);
+        const K* ikey = in.segs ? in.segs[d.seg].key : in.key;
+        const int32_t* ipay = in.segs ? in.segs[d.seg].pay : in.pay;
 
         R v[SC_IPT];
         uint32_t dd[SC_IPT];
@@ -456,11 +507,11 @@ k_scatter(PartIn<K, HB> in, const uint64_t* __restrict__ seg_begin, const uint64
                 } else if (d.tma) {
                     v[j].key = gk[d.koff + i];
                     if constexpr (HB) v[j].b = gb[d.boff + i];
-                    v[j].pay = in.pay ? gp[d.poff + i] : (int32_t)(beg + i);
+                    v[j].pay = ipay ? gp[d.poff + i] : (int32_t)(beg + i);
                 } else {
-                    v[j].key = in.key[beg + i];
+                    v[j].key = ikey[beg + i];
                     if constexpr (HB) v[j].b = in.key_b[beg + i];
-                    v[j].pay = in.pay ? in.pay[beg + i] : (int32_t)(beg + i);
+                    v[j].pay = ipay ? ipay[beg + i] : (int32_t)(beg + i);
                 }
             }
         }

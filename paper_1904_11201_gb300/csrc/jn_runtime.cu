@@ -253,16 +253,13 @@ jn_status jn_create(jn_ctx** out, int device, void* stream) {
         c->smem_optin = prop.sharedMemPerBlockOptin;
     }
     if (e == cudaSuccess) {
-        cudaMemPoolProps props;
-        memset(&props, 0, sizeof(props));
-        props.allocType = cudaMemAllocationTypePinned;
-        props.handleTypes = cudaMemHandleTypeNone;
-        props.location.type = cudaMemLocationTypeDevice;
-        props.location.id = device;
-        e = cudaMemPoolCreate(&c->pool, &props);
+        // Outputs may outlive the context (jn_free accepts a NULL context), so
+        // allocations come from the device's default pool, which lives as long
+        // as the process; freed blocks are kept for reuse by later calls.
+        e = cudaDeviceGetDefaultMemPool(&c->pool, device);
     }
     if (e == cudaSuccess) {
-        uint64_t keep = UINT64_MAX;  // keep freed blocks for reuse by later calls
+        uint64_t keep = UINT64_MAX;
         e = cudaMemPoolSetAttribute(c->pool, cudaMemPoolAttrReleaseThreshold, &keep);
     }
     if (e == cudaSuccess) e = cudaMallocHost((void**)&c->h_small, 64 * sizeof(uint64_t));
@@ -270,7 +267,6 @@ jn_status jn_create(jn_ctx** out, int device, void* stream) {
     if (e == cudaSuccess) e = cudaMemset(c->d_err, 0, 256);
     if (e != cudaSuccess) {
         cudaGetLastError();
-        if (c->pool) cudaMemPoolDestroy(c->pool);
         if (c->h_small) cudaFreeHost(c->h_small);
         if (c->d_err) cudaFree(c->d_err);
         delete c;
@@ -287,7 +283,7 @@ void jn_destroy(jn_ctx* c) {
     for (cudaEvent_t e : c->spare_events) cudaEventDestroy(e);
     if (c->h_small) cudaFreeHost(c->h_small);
     if (c->d_err) cudaFree(c->d_err);
-    if (c->pool) cudaMemPoolDestroy(c->pool);
+    if (c->capture_stream) cudaStreamDestroy(c->capture_stream);
     cudaGetLastError();
     delete c;
 }
@@ -360,5 +356,7 @@ jn_status jn_last_run_info(const jn_ctx* c, jn_run_info* info) {
 }
 
 uint64_t jn_launch_count(const jn_ctx* c) { return c ? c->launches_total : 0; }
+
+int32_t jn_pointer_is_device(const void* p) { return p && is_device_pointer(p) ? 1 : 0; }
 
 }  // extern "C"

@@ -1,0 +1,461 @@
+// Serving engine: a request loop over the join library.
+//
+// Requests arrive on any host thread (jn_server_submit) and wait in one
+// queue.  `slots` worker threads, each with its own context and CUDA stream,
+// take requests as soon as they free up, so the work of several requests
+// overlaps on the device (continuous batching: a request that arrives while
+// others run is admitted as soon as a slot and memory allow, not after the
+// current group ends).  A worker that finds small requests at the head of the
+// queue takes up to max_batch of them and runs them as one jn_batch (one
+// launch sequence for the group); a large request runs alone.  Admission is
+// by device memory: a large request is first counted exactly (the count pass
+// that sizes every output) and waits until its scratch estimate plus its
+// exact output fits in the budget next to the outputs still held; a request
+// that can never fit is refused with JN_ERR_OOM.  Tables registered with the
+// server stay resident on the device across requests.
+//
+// The engine only calls the public entry points of jn.h; it adds no join
+// arithmetic of its own.
+#include <string.h>
+
+#include <chrono>
+#include <condition_variable>
+#include <deque>
+#include <map>
+#include <memory>
+#include <mutex>
+#include <thread>
+#include <vector>
+
+#include "jn_common.cuh"
+
+namespace {
+
+using Clock = std::chrono::steady_clock;
+
+struct OutBuf {  // one output allocation, shared by the requests of a batch
+    jn_pair* ptr = nullptr;
+    uint64_t bytes = 0;
+    int refs = 0;
+};
+
+struct Job {
+    uint64_t ticket = 0;
+    jn_request req{};
+    Clock::time_point submitted, started, finished;
+    bool done = false;
+    jn_status status = JN_OK;
+    uint64_t pairs = 0;
+    jn_pair* out = nullptr;
+    std::shared_ptr<OutBuf> buf;
+    std::string err;
+};
+
+struct Resident {
+    jn_table t{};
+    std::vector<void*> owned;
+    uint64_t bytes = 0;
+};
+
+}  // namespace
+
+struct jn_server {
+    int device = 0;
+    jn_server_config cfg{};
+    std::mutex mu;
+    std::condition_variable cv_work, cv_done, cv_mem;
+    std::deque<std::shared_ptr<Job>> queue;
+    std::map<uint64_t, std::shared_ptr<Job>> jobs;
+    std::map<int32_t, Resident> tables;
+    int32_t next_handle = 1;
+    uint64_t next_ticket = 1;
+    uint64_t mem_held = 0;  // bytes of outputs not yet released + scratch reserved by running requests
+    bool stop = false;
+    std::vector<std::thread> workers;
+    jn_server_stats stats{};
+};
+
+namespace {
+
+uint64_t rows_of(const jn_request& r) { return (uint64_t)r.R.n + (uint64_t)r.S.n; }
+
+// Device bytes a request needs besides its output: the partitioned copies
+// and bookkeeping of the radix passes (two passes, rows of 8 or 16 bytes).
+uint64_t scratch_estimate(const jn_request& r) {
+    const uint64_t row = r.R.key_type == JN_KEY_I64 ? 16 : 8;
+    return 3 * row * rows_of(r) + (16ull << 20);
+}
+
+jn_status resolve(jn_server* s, const jn_request& in, jn_request* out) {
+    *out = in;
+    std::lock_guard<std::mutex> g(s->mu);
+    if (in.r_handle > 0) {
+        auto it = s->tables.find(in.r_handle);
+        if (it == s->tables.end()) return JN_ERR_INVALID;
+        out->R = it->second.t;
+    }
+    if (in.s_handle > 0) {
+        auto it = s->tables.find(in.s_handle);
+        if (it == s->tables.end()) return JN_ERR_INVALID;
+        out->S = it->second.t;
+    }
+    return JN_OK;
+}
+
+void finish(jn_server* s, const std::shared_ptr<Job>& j, jn_status st, uint64_t pairs, jn_pair* out,
+            const std::shared_ptr<OutBuf>& buf, const char* err) {
+    if (st == JN_OK && pairs > 0 && !jnx::is_device_pointer(out)) {
+        st = JN_ERR_CUDA;  // never hand out a pointer the device does not own
+        err = "result pointer is not device memory";
+    }
+    std::lock_guard<std::mutex> g(s->mu);
+    j->finished = Clock::now();
+    j->status = st;
+    j->pairs = pairs;
+    j->out = out;
+    j->buf = buf;
+    if (err) j->err = err;
+    j->done = true;
+    s->stats.completed++;
+    if (st != JN_OK) s->stats.failed++;
+    s->cv_done.notify_all();
+}
+
+// Waits until `bytes` more fit the budget (false: they never can).
+bool reserve(jn_server* s, uint64_t bytes) {
+    std::unique_lock<std::mutex> lk(s->mu);
+    if (bytes > s->cfg.memory_budget) return false;
+    s->cv_mem.wait(lk, [&] { return s->stop || s->mem_held + bytes <= s->cfg.memory_budget; });
+    if (s->stop) return false;
+    s->mem_held += bytes;
+    if (s->mem_held > s->stats.peak_bytes) s->stats.peak_bytes = s->mem_held;
+    return true;
+}
+
+void unreserve(jn_server* s, uint64_t bytes) {
+    std::lock_guard<std::mutex> g(s->mu);
+    s->mem_held -= bytes;
+    s->cv_mem.notify_all();
+}
+
+void run_single(jn_server* s, jn_ctx* ctx, cudaStream_t stream, const std::shared_ptr<Job>& j) {
+    jn_request r;
+    if (resolve(s, j->req, &r) != JN_OK) {
+        finish(s, j, JN_ERR_INVALID, 0, nullptr, nullptr, "unknown table handle");
+        return;
+    }
+    jn_pred pr{r.op, JN_ANY, r.band};
+    const int algo = r.band >= 0 ? JN_ALGO_THETA : JN_ALGO_HASH;
+    uint64_t m = 0;
+    jn_status st = jn_count(ctx, algo, &r.R, &r.S, r.band >= 0 ? &pr : nullptr, &m);
+    if (st != JN_OK) {
+        finish(s, j, st, 0, nullptr, nullptr, jn_last_error(ctx));
+        return;
+    }
+    const uint64_t out_bytes = m * sizeof(jn_pair), scratch = scratch_estimate(r);
+    if (!reserve(s, out_bytes + scratch)) {
+        finish(s, j, JN_ERR_OOM, m, nullptr, nullptr, "request does not fit the memory budget");
+        return;
+    }
+    {
+        std::lock_guard<std::mutex> g(s->mu);
+        j->started = Clock::now();
+    }
+    jn_pair* out = nullptr;
+    uint64_t n = 0;
+    st = r.band >= 0 ? jn_theta(ctx, &r.R, &r.S, r.op, r.band, &out, 0, &n)
+                     : jn_hash(ctx, &r.R, &r.S, &out, 0, &n);
+    if (st == JN_OK && cudaStreamSynchronize(stream) != cudaSuccess) {
+        cudaGetLastError();
+        st = JN_ERR_CUDA;
+    }
+    unreserve(s, scratch);
+    if (st != JN_OK) {
+        unreserve(s, out_bytes);
+        finish(s, j, st, 0, nullptr, nullptr, jn_last_error(ctx));
+        return;
+    }
+    auto buf = std::make_shared<OutBuf>();
+    buf->ptr = out;
+    buf->bytes = out_bytes;
+    buf->refs = 1;
+    finish(s, j, JN_OK, n, out, buf, nullptr);
+}
+
+void run_group(jn_server* s, jn_ctx* ctx, cudaStream_t stream, std::vector<std::shared_ptr<Job>>& g) {
+    std::vector<jn_join> joins;
+    std::vector<std::shared_ptr<Job>> live;
+    uint64_t scratch = 0;
+    for (auto& j : g) {
+        jn_request r;
+        if (resolve(s, j->req, &r) != JN_OK) {
+            finish(s, j, JN_ERR_INVALID, 0, nullptr, nullptr, "unknown table handle");
+            continue;
+        }
+        jn_join x;
+        memset(&x, 0, sizeof(x));
+        x.R = r.R;
+        x.S = r.S;
+        x.op = r.op;
+        x.band = r.band;
+        joins.push_back(x);
+        live.push_back(j);
+        scratch += scratch_estimate(r);
+    }
+    if (live.empty()) return;
+    if (!reserve(s, scratch)) {
+        for (auto& j : live) finish(s, j, JN_ERR_OOM, 0, nullptr, nullptr, "batch does not fit the memory budget");
+        return;
+    }
+    {
+        std::lock_guard<std::mutex> lk(s->mu);
+        const auto now = Clock::now();
+        for (auto& j : live) j->started = now;
+        s->stats.batches++;
+    }
+    std::vector<uint64_t> first(live.size()), cnt(live.size());
+    jn_pair* out = nullptr;
+    uint64_t total = 0;
+    jn_status st = jn_batch(ctx, (int32_t)joins.size(), joins.data(), &out, 0, &total, first.data(), cnt.data());
+    if (st == JN_OK && cudaStreamSynchronize(stream) != cudaSuccess) {
+        cudaGetLastError();
+        st = JN_ERR_CUDA;
+    }
+    unreserve(s, scratch);
+    if (st != JN_OK) {
+        for (auto& j : live) finish(s, j, st, 0, nullptr, nullptr, jn_last_error(ctx));
+        return;
+    }
+    // outputs of a group are one allocation: account for it until all are released
+    auto buf = std::make_shared<OutBuf>();
+    buf->ptr = out;
+    buf->bytes = total * sizeof(jn_pair);
+    buf->refs = (int)live.size();
+    {
+        std::lock_guard<std::mutex> lk(s->mu);
+        s->mem_held += buf->bytes;
+        if (s->mem_held > s->stats.peak_bytes) s->stats.peak_bytes = s->mem_held;
+    }
+    for (size_t i = 0; i < live.size(); i++) finish(s, live[i], JN_OK, cnt[i], out ? out + first[i] : nullptr, buf, nullptr);
+}
+
+void worker_main(jn_server* s, int slot) {
+    cudaSetDevice(s->device);
+    cudaStream_t stream = nullptr;
+    cudaStreamCreateWithFlags(&stream, cudaStreamNonBlocking);
+    jn_ctx* ctx = nullptr;
+    if (jn_create(&ctx, s->device, stream) != JN_OK) {
+        cudaStreamDestroy(stream);
+        return;
+    }
+    jn_tuning t;
+    jn_get_tuning(ctx, &t);
+    t.graphs = s->cfg.graphs ? 1 : 0;
+    jn_set_tuning(ctx, &t);
+    (void)slot;
+    while (true) {
+        std::vector<std::shared_ptr<Job>> take;
+        {
+            std::unique_lock<std::mutex> lk(s->mu);
+            s->cv_work.wait(lk, [&] { return s->stop || !s->queue.empty(); });
+            if (s->stop && s->queue.empty()) break;
+            auto head = s->queue.front();
+            s->queue.pop_front();
+            take.push_back(head);
+            if (rows_of(head->req) < (uint64_t)s->cfg.coalesce_rows) {
+                // coalesce the small requests waiting now
+                for (auto it = s->queue.begin(); it != s->queue.end() && (int)take.size() < s->cfg.max_batch;) {
+                    if (rows_of((*it)->req) < (uint64_t)s->cfg.coalesce_rows &&
+                        (*it)->req.R.key_type == head->req.R.key_type) {
+                        take.push_back(*it);
+                        it = s->queue.erase(it);
+                    } else {
+                        ++it;
+                    }
+                }
+            }
+        }
+        if (take.size() == 1 && rows_of(take[0]->req) >= (uint64_t)s->cfg.coalesce_rows)
+            run_single(s, ctx, stream, take[0]);
+        else
+            run_group(s, ctx, stream, take);
+    }
+    jn_destroy(ctx);
+    cudaStreamDestroy(stream);
+}
+
+}  // namespace
+
+extern "C" {
+
+jn_status jn_server_create(jn_server** out, int device, const jn_server_config* cfg) {
+    if (!out || !cfg || cfg->slots < 1 || cfg->slots > 16 || cfg->max_batch < 1)
+        return JN_ERR_INVALID;
+    int ndev = 0;
+    if (cudaGetDeviceCount(&ndev) != cudaSuccess || device < 0 || device >= ndev) {
+        cudaGetLastError();
+        return JN_ERR_INVALID;
+    }
+    jn_server* s = new jn_server();
+    s->device = device;
+    s->cfg = *cfg;
+    for (int i = 0; i < cfg->slots; i++) s->workers.emplace_back(worker_main, s, i);
+    *out = s;
+    return JN_OK;
+}
+
+void jn_server_destroy(jn_server* s) {
+    if (!s) return;
+    {
+        std::lock_guard<std::mutex> g(s->mu);
+        s->stop = true;
+    }
+    s->cv_work.notify_all();
+    s->cv_mem.notify_all();
+    for (auto& t : s->workers) t.join();
+    cudaSetDevice(s->device);
+    for (auto& kv : s->jobs)
+        if (kv.second->buf && kv.second->buf->ptr && --kv.second->buf->refs == 0) cudaFree(kv.second->buf->ptr);
+    for (auto& kv : s->tables)
+        for (void* p : kv.second.owned) cudaFree(p);
+    delete s;
+}
+
+jn_status jn_server_register(jn_server* s, const jn_table* t, int32_t* handle) {
+    if (!s || !t || !handle || (t->key_type != JN_KEY_I32 && t->key_type != JN_KEY_I64) || t->n < 0 ||
+        t->n > INT32_MAX || (t->n > 0 && !t->key))
+        return JN_ERR_INVALID;
+    cudaSetDevice(s->device);
+    Resident r;
+    r.t = *t;
+    const size_t kb = (size_t)t->n * (size_t)t->key_type;
+    auto copy = [&](const void* src, size_t bytes, const void** dst) -> jn_status {
+        if (!src || bytes == 0) {
+            *dst = src && bytes == 0 ? nullptr : *dst;
+            return JN_OK;
+        }
+        void* d = nullptr;
+        if (cudaMalloc(&d, bytes) != cudaSuccess) {
+            cudaGetLastError();
+            return JN_ERR_OOM;
+        }
+        if (cudaMemcpy(d, src, bytes, cudaMemcpyDefault) != cudaSuccess) {
+            cudaGetLastError();
+            cudaFree(d);
+            return JN_ERR_CUDA;
+        }
+        r.owned.push_back(d);
+        r.bytes += bytes;
+        *dst = d;
+        return JN_OK;
+    };
+    jn_status st = copy(t->key, kb, &r.t.key);
+    if (st == JN_OK && t->key2) st = copy(t->key2, kb, &r.t.key2);
+    if (st == JN_OK && t->payload) {
+        const void* p = nullptr;
+        st = copy(t->payload, (size_t)t->n * 4, &p);
+        r.t.payload = static_cast<const int32_t*>(p);
+    }
+    if (st != JN_OK) {
+        for (void* p : r.owned) cudaFree(p);
+        return st;
+    }
+    std::lock_guard<std::mutex> g(s->mu);
+    *handle = s->next_handle++;
+    s->stats.resident_bytes += r.bytes;
+    s->tables[*handle] = std::move(r);
+    return JN_OK;
+}
+
+jn_status jn_server_unregister(jn_server* s, int32_t handle) {
+    if (!s) return JN_ERR_INVALID;
+    std::lock_guard<std::mutex> g(s->mu);
+    auto it = s->tables.find(handle);
+    if (it == s->tables.end()) return JN_ERR_INVALID;
+    cudaSetDevice(s->device);
+    cudaDeviceSynchronize();  // requests already running may still read it
+    for (void* p : it->second.owned) cudaFree(p);
+    s->stats.resident_bytes -= it->second.bytes;
+    s->tables.erase(it);
+    return JN_OK;
+}
+
+jn_status jn_server_submit(jn_server* s, const jn_request* req, uint64_t* ticket) {
+    if (!s || !req || !ticket || req->reserved != 0 || req->op < JN_EQ || req->op > JN_ANY ||
+        (req->band < 0 && req->op != JN_EQ))
+        return JN_ERR_INVALID;
+    auto j = std::make_shared<Job>();
+    j->req = *req;
+    {
+        std::lock_guard<std::mutex> g(s->mu);
+        // resolve sizes of resident tables now, for coalescing decisions
+        if (req->r_handle > 0) {
+            auto it = s->tables.find(req->r_handle);
+            if (it == s->tables.end()) return JN_ERR_INVALID;
+            j->req.R.n = it->second.t.n;
+            j->req.R.key_type = it->second.t.key_type;
+        }
+        if (req->s_handle > 0) {
+            auto it = s->tables.find(req->s_handle);
+            if (it == s->tables.end()) return JN_ERR_INVALID;
+            j->req.S.n = it->second.t.n;
+            j->req.S.key_type = it->second.t.key_type;
+        }
+        j->ticket = s->next_ticket++;
+        j->submitted = Clock::now();
+        s->jobs[j->ticket] = j;
+        s->queue.push_back(j);
+        s->stats.submitted++;
+        *ticket = j->ticket;
+    }
+    s->cv_work.notify_one();
+    return JN_OK;
+}
+
+jn_status jn_server_wait(jn_server* s, uint64_t ticket, jn_result* res) {
+    if (!s || !res) return JN_ERR_INVALID;
+    std::unique_lock<std::mutex> lk(s->mu);
+    auto it = s->jobs.find(ticket);
+    if (it == s->jobs.end()) return JN_ERR_INVALID;
+    auto j = it->second;
+    s->cv_done.wait(lk, [&] { return j->done; });
+    memset(res, 0, sizeof(*res));
+    res->status = j->status;
+    res->pairs = j->pairs;
+    res->out = j->out;
+    using ms = std::chrono::duration<double, std::milli>;
+    res->queue_ms = ms(j->started - j->submitted).count();
+    res->run_ms = ms(j->finished - j->started).count();
+    res->total_ms = ms(j->finished - j->submitted).count();
+    if (j->started.time_since_epoch().count() == 0) res->queue_ms = res->run_ms = 0;
+    return JN_OK;
+}
+
+jn_status jn_server_release(jn_server* s, uint64_t ticket) {
+    if (!s) return JN_ERR_INVALID;
+    std::lock_guard<std::mutex> g(s->mu);
+    auto it = s->jobs.find(ticket);
+    if (it == s->jobs.end() || !it->second->done) return JN_ERR_INVALID;
+    auto buf = it->second->buf;
+    s->jobs.erase(it);
+    if (buf && --buf->refs == 0) {
+        if (buf->ptr) {
+            cudaSetDevice(s->device);
+            jn_free(nullptr, buf->ptr);
+        }
+        s->mem_held -= buf->bytes;
+        s->cv_mem.notify_all();
+    }
+    return JN_OK;
+}
+
+jn_status jn_server_stats_get(jn_server* s, jn_server_stats* out) {
+    if (!s || !out) return JN_ERR_INVALID;
+    std::lock_guard<std::mutex> g(s->mu);
+    *out = s->stats;
+    out->held_bytes = s->mem_held;
+    out->queued = s->queue.size();
+    return JN_OK;
+}
+
+}  // extern "C"

@@ -17,6 +17,8 @@
 //      the total (one 8-byte read-back).
 //   5. one exact allocation, then the emit pass repeats build and probe and
 //      writes (R.payload, S.payload) pairs at the scanned offsets.
+#include <vector>
+
 #include "jn_algos.h"
 #include "jn_heavy.cuh"
 #include "jn_partition.cuh"
@@ -66,10 +68,9 @@ struct Item {
 
 // items[it] for every item: its partition is the last p with item_prefix[p] <= it.
 __global__ void k_item_desc(const uint64_t* __restrict__ roff, const uint64_t* __restrict__ soff,
-                            const uint64_t* __restrict__ item_prefix, int P, int cap, uint64_t nitems,
-                            Item* __restrict__ items) {
+                            const uint64_t* __restrict__ item_prefix, int P, int cap, Item* __restrict__ items) {
     const uint64_t it = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (it >= nitems) return;
+    if (it >= item_prefix[P]) return;
     const int p = find_segment(item_prefix, P, it);
     const uint64_t rc = it - item_prefix[p];
     const uint64_t nr = roff[p + 1] - roff[p];
@@ -139,7 +140,8 @@ __device__ __forceinline__ uint32_t oa_slot(uint32_t h, int bits, int ts) {
 template <typename K, int MODE, bool MERGE = false>
 __global__ void __launch_bounds__(HJ_T, 2)
 k_hash_join(const Row<K, false>* __restrict__ rrows, const Row<K, false>* __restrict__ srows,
-            const Item* __restrict__ items, uint64_t nitems, int bits, unsigned long long* __restrict__ item_val,
+            const Item* __restrict__ items, const uint64_t* __restrict__ nitems_p, int bits,
+            unsigned long long* __restrict__ item_val,
             unsigned long long* __restrict__ chk, const uint64_t* __restrict__ item_off,
             jn_pair* __restrict__ out, unsigned int* __restrict__ err) {
     using R = Row<K, false>;
@@ -167,6 +169,7 @@ k_hash_join(const Row<K, false>* __restrict__ rrows, const Row<K, false>* __rest
     const K KMIN = key_sentinel<K>();
 
     const int lane = threadIdx.x & 31;
+    const uint64_t nitems = *nitems_p;
     uint64_t it = blockIdx.x;
     if (it >= nitems) return;
     Item d = items[it];
@@ -494,7 +497,7 @@ static jn_status partition_table(jn_ctx* c, Scratch& s, const Cols<K>& T, int b1
     const size_t sm = scatter_smem<K, false>();
     auto kern1 = other_bitmap ? k_scatter<K, false, true, D1> : k_scatter<K, false, false, D1>;
     const int g1 = persistent_grid(c, (const void*)kern1, SC_T, sm);
-    PartIn<K, false> in1{T.key, nullptr, T.pay, nullptr, n};
+    PartIn<K, false> in1{T.key, nullptr, T.pay, nullptr, n, nullptr, nullptr};
     JN_TRY(launch(c, K_SCATTER, kern1, dim3(g1), dim3(SC_T), sm, in1, (const uint64_t*)seg_b,
                   (const uint64_t*)seg_c, (const uint64_t*)tp, 1, d1, nd1, other_bitmap, fmask, cur1, r1,
                   c->d_err));
@@ -522,7 +525,7 @@ static jn_status partition_table(jn_ctx* c, Scratch& s, const Cols<K>& T, int b1
     JN_TRY(s.get(&r2, n + HJ_PAD));
     auto kern2 = k_scatter<K, false, false, HashDigit>;
     const int g2 = persistent_grid(c, (const void*)kern2, SC_T, sm);
-    PartIn<K, false> in2{nullptr, nullptr, nullptr, r1, n + HJ_PAD};
+    PartIn<K, false> in2{nullptr, nullptr, nullptr, r1, n + HJ_PAD, nullptr, nullptr};
     JN_TRY(launch(c, K_SCATTER, kern2, dim3(g2), dim3(SC_T), sm, in2, (const uint64_t*)start1,
                   (const uint64_t*)seg_c, (const uint64_t*)tp, F1, d2, F2, (const uint32_t*)nullptr, 0u, cur2,
                   r2, c->d_err));
@@ -716,15 +719,15 @@ jn_status run_hash(jn_ctx* c, const Cols<K>& R, const Cols<K>& S, int mode, OutP
     if (nitems) {
         JN_TRY(launch(c, K_ITEMS, k_item_desc, dim3((unsigned)ceil_div(nitems, 256)), dim3(256), 0,
                       (const uint64_t*)PR.off, (const uint64_t*)PS.off, (const uint64_t*)iprefix, P, cap_of<K>(),
-                      nitems, idesc));
+                      idesc));
         const int cm = mode == MODE_AGG ? MODE_AGG : MODE_COUNT;
         const size_t smc = hash_smem<K>(cm);
         auto kc = (cm == MODE_AGG) ? (skewed ? k_hash_join<K, MODE_AGG, true> : k_hash_join<K, MODE_AGG, false>)
                                    : (skewed ? k_hash_join<K, MODE_COUNT, true> : k_hash_join<K, MODE_COUNT, false>);
         const int gj = (int)min((uint64_t)persistent_grid(c, (const void*)kc, HJ_T, smc), nitems);
         JN_TRY(launch(c, K_HASH_COUNT, kc, dim3(gj), dim3(HJ_T), smc, (const RW*)PR.rows, (const RW*)PS.rows,
-                      (const Item*)idesc, nitems, b, ival, chk, (const uint64_t*)nullptr, (jn_pair*)nullptr,
-                      c->d_err));
+                      (const Item*)idesc, (const uint64_t*)(iprefix + P), b, ival, chk, (const uint64_t*)nullptr,
+                      (jn_pair*)nullptr, c->d_err));
     }
     JN_TRY(scan_u64(c, reinterpret_cast<const uint64_t*>(ival), ioff, (int64_t)nitems));
     // ---- heavy keys: c_R(h) * c_S(h) pairs each ----
@@ -770,8 +773,8 @@ jn_status run_hash(jn_ctx* c, const Cols<K>& R, const Cols<K>& S, int mode, OutP
         const size_t sme = hash_smem<K>(MODE_EMIT);
         const int ge = (int)min((uint64_t)persistent_grid(c, (const void*)ke, HJ_T, sme), nitems);
         JN_TRY(launch(c, K_HASH_EMIT, ke, dim3(ge), dim3(HJ_T), sme, (const RW*)PR.rows, (const RW*)PS.rows,
-                      (const Item*)idesc, nitems, b, (unsigned long long*)nullptr, (unsigned long long*)nullptr,
-                      (const uint64_t*)ioff, plan->dev, c->d_err));
+                      (const Item*)idesc, (const uint64_t*)(iprefix + P), b, (unsigned long long*)nullptr,
+                      (unsigned long long*)nullptr, (const uint64_t*)ioff, plan->dev, c->d_err));
     }
     if (heavy_pairs > 0) {
         JN_TRY(launch(c, K_CROSS_EMIT, k_cartesian<RW>, dim3(8 * c->num_sms), dim3(256), 0, (const RW*)PR.hrows,
@@ -782,6 +785,238 @@ jn_status run_hash(jn_ctx* c, const Cols<K>& R, const Cols<K>& S, int mode, OutP
     JN_TRY(out_finish(c, total, *plan));
     return JN_OK;
 }
+
+// ------------------------------------------------------------------ batch --
+// Histogram of per-segment digits over a tile list: hist[seg * 1024 + d].
+template <typename K>
+__global__ void __launch_bounds__(SC_T)
+k_batch_hist(const SegCols<K>* __restrict__ segs, const TileRef* __restrict__ tiles,
+             const uint64_t* __restrict__ ntiles_p, SegHashDigit dg, unsigned long long* __restrict__ hist) {
+    __shared__ uint32_t s_h[SC_FMAX];
+    const uint64_t ntiles = *ntiles_p;
+    for (uint64_t t = blockIdx.x; t < ntiles; t += gridDim.x) {
+        const TileRef x = tiles[t];
+        dg.set_seg(x.seg);
+        const int nd = 1 << dg.b;
+        for (int i = threadIdx.x; i < nd; i += blockDim.x) s_h[i] = 0;
+        __syncthreads();
+        const K* k = segs[x.seg].key;
+        for (int i = threadIdx.x; i < x.cnt; i += blockDim.x) atomicAdd(&s_h[dg(k[x.beg + i])], 1u);
+        __syncthreads();
+        for (int i = threadIdx.x; i < nd; i += blockDim.x)
+            if (s_h[i]) atomicAdd(&hist[(uint64_t)x.seg * SC_FMAX + i], (unsigned long long)s_h[i]);
+        __syncthreads();
+    }
+}
+
+// out_off[i] = output offset of join i: the offset of its first item.
+__global__ void k_batch_offsets(const uint64_t* __restrict__ item_prefix, const uint64_t* __restrict__ ioff,
+                                int count, uint64_t* __restrict__ out_off) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i > count) return;
+    out_off[i] = ioff[item_prefix[(uint64_t)i * SC_FMAX]];
+}
+
+// A batch of equi-joins run as one: every table of every join is a segment
+// of one radix pass (segment i = R of join i, segment n + i = S of join i),
+// partition (i, d) has the global id i * 1024 + d, and the count and emit
+// passes run over the work queue of (partition, R chunk) items of all joins.
+// Each phase is one launch for the whole batch; with graphs on, the phases
+// up to the count read-back and the emit phase are each captured and
+// replayed as a CUDA graph.  offsets (host, n + 1) receives where each join's
+// pairs start in the output.
+template <typename K>
+jn_status run_batch_hash(jn_ctx* c, int n, const Cols<K>* Rs, const Cols<K>* Ss, OutPlan* plan,
+                         uint64_t* offsets, uint64_t extra) {
+    using RW = Row<K, false>;
+    const int cap = cap_of<K>();
+    // ---- host plan: per-join fan-out, segment table and tile list ----
+    std::vector<SegCols<K>> segs(2 * (size_t)n);
+    std::vector<int> bits(2 * (size_t)n);
+    std::vector<TileRef> tiles;
+    uint64_t rows = 0, rrows = 0;
+    for (int i = 0; i < n; i++) {
+        const uint64_t nr = (uint64_t)Rs[i].n;
+        int b = ceil_log2(ceil_div(nr, (uint64_t)cap / 2));
+        if (b > 10) b = 10;
+        bits[i] = bits[n + i] = b;
+        segs[i] = SegCols<K>{Rs[i].key, Rs[i].pay, (uint64_t)Rs[i].n, 0};
+        segs[n + i] = SegCols<K>{Ss[i].key, Ss[i].pay, (uint64_t)Ss[i].n, 0};
+        rows += (uint64_t)Rs[i].n + (uint64_t)Ss[i].n;
+        rrows += (uint64_t)Rs[i].n;
+    }
+    for (int sgi = 0; sgi < 2 * n; sgi++)
+        for (uint64_t b = 0; b < segs[sgi].n; b += SC_TILE)
+            tiles.push_back(TileRef{b, sgi, (int)min((uint64_t)SC_TILE, segs[sgi].n - b)});
+    const uint64_t ntiles = tiles.size();
+    const uint64_t P = (uint64_t)n * SC_FMAX;                 // partitions of all joins
+    const uint64_t item_bound = P + rrows / (uint64_t)cap + 1;  // items <= P + sum nr / cap
+    Scratch s(c);
+    SegCols<K>* d_segs;
+    int* d_bits;
+    TileRef* d_tiles;
+    uint64_t* d_ntiles;
+    unsigned long long *hist, *cur;
+    uint64_t *start, *items, *iprefix, *ioff, *d_small, *d_off;
+    RW* prow;
+    Item* idesc;
+    unsigned long long *ival, *chk;
+    JN_TRY(s.get(&d_segs, 2 * (size_t)n));
+    JN_TRY(s.get(&d_bits, 2 * (size_t)n));
+    JN_TRY(s.get(&d_tiles, ntiles + 1));
+    JN_TRY(s.get(&d_ntiles, 1));
+    JN_TRY(s.get(&hist, 2 * P));
+    JN_TRY(s.get(&start, 2 * P + 1));
+    JN_TRY(s.get(&cur, 2 * P));
+    JN_TRY(s.get(&prow, rows + HJ_PAD));
+    JN_TRY(s.get(&items, P));
+    JN_TRY(s.get(&iprefix, P + 1));
+    JN_TRY(s.get(&idesc, item_bound));
+    JN_TRY(s.get(&ival, item_bound));
+    JN_TRY(s.get(&ioff, item_bound + 1));
+    JN_TRY(s.get(&chk, 1));
+    JN_TRY(s.get(&d_small, 2));
+    JN_TRY(s.get(&d_off, (size_t)n + 1));
+    JN_CUDA(c, cudaMemcpyAsync(d_segs, segs.data(), sizeof(SegCols<K>) * segs.size(), cudaMemcpyHostToDevice,
+                               c->stream));
+    JN_CUDA(c, cudaMemcpyAsync(d_bits, bits.data(), sizeof(int) * bits.size(), cudaMemcpyHostToDevice, c->stream));
+    if (ntiles)
+        JN_CUDA(c, cudaMemcpyAsync(d_tiles, tiles.data(), sizeof(TileRef) * ntiles, cudaMemcpyHostToDevice,
+                                   c->stream));
+    JN_CUDA(c, cudaMemcpyAsync(d_ntiles, &ntiles, sizeof(uint64_t), cudaMemcpyHostToDevice, c->stream));
+    JN_CUDA(c, cudaStreamSynchronize(c->stream));  // host vectors go out of scope below
+
+    const bool graphs = c->tune.graphs != 0 && !c->profiling;
+    cudaGraph_t g1 = nullptr, g2 = nullptr;
+    cudaGraphExec_t x1 = nullptr, x2 = nullptr;
+    // Phases are captured on a private stream (the caller's stream may be the
+    // legacy default stream, which cannot be captured) and replayed on the
+    // caller's stream, after everything it already holds.
+    cudaStream_t user = c->stream;
+    if (graphs && !c->capture_stream)
+        JN_CUDA(c, cudaStreamCreateWithFlags(&c->capture_stream, cudaStreamNonBlocking));
+    auto begin_capture = [&]() -> jn_status {
+        if (!graphs) return JN_OK;
+        c->stream = c->capture_stream;
+        cudaError_t e = cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeThreadLocal);
+        if (e != cudaSuccess) c->stream = user;
+        JN_CUDA(c, e);
+        return JN_OK;
+    };
+    auto end_replay = [&](cudaGraph_t* g, cudaGraphExec_t* x) -> jn_status {
+        if (!graphs) return JN_OK;
+        cudaError_t e = cudaStreamEndCapture(c->stream, g);
+        c->stream = user;
+        JN_CUDA(c, e);
+        JN_CUDA(c, cudaGraphInstantiate(x, *g, 0));
+        JN_CUDA(c, cudaGraphLaunch(*x, c->stream));
+        return JN_OK;
+    };
+    auto abort_capture = [&]() {
+        if (!graphs || c->stream == user) return;
+        cudaGraph_t junk = nullptr;
+        cudaStreamEndCapture(c->stream, &junk);
+        if (junk) cudaGraphDestroy(junk);
+        c->stream = user;
+        cudaGetLastError();
+    };
+    struct GraphGuard {
+        cudaGraph_t* g[2];
+        cudaGraphExec_t* x[2];
+        ~GraphGuard() {
+            for (int i = 0; i < 2; i++) {
+                if (*x[i]) cudaGraphExecDestroy(*x[i]);
+                if (*g[i]) cudaGraphDestroy(*g[i]);
+            }
+        }
+    } guard{{&g1, &g2}, {&x1, &x2}};
+
+    // ---- phase 1: histogram, scan, scatter, items, count, scan ----
+    JN_TRY(begin_capture());
+    jn_status st = JN_OK;
+    do {
+        SegHashDigit dg{d_bits, 0};
+        if ((st = zero(c, hist, sizeof(unsigned long long) * 2 * P)) != JN_OK) break;
+        if ((st = zero(c, chk, 8)) != JN_OK) break;
+        if ((st = zero(c, ival, sizeof(unsigned long long) * item_bound)) != JN_OK) break;
+        if ((st = launch(c, K_HIST, k_batch_hist<K>, dim3(4 * c->num_sms), dim3(SC_T), 0,
+                         (const SegCols<K>*)d_segs, (const TileRef*)d_tiles, (const uint64_t*)d_ntiles, dg,
+                         hist)) != JN_OK)
+            break;
+        if ((st = scan_u64(c, reinterpret_cast<const uint64_t*>(hist), start, (int64_t)(2 * P))) != JN_OK) break;
+        if ((st = launch(c, K_MISC, k_init_cursor, dim3((unsigned)ceil_div(2 * P, 256)), dim3(256), 0,
+                         (const uint64_t*)start, cur, (int64_t)(2 * P))) != JN_OK)
+            break;
+        auto ks = k_scatter<K, false, false, SegHashDigit>;
+        const size_t sm = scatter_smem<K, false>();
+        PartIn<K, false> in{nullptr, nullptr, nullptr, nullptr, 0, d_segs, d_tiles};
+        if ((st = launch(c, K_SCATTER, ks, dim3(persistent_grid(c, (const void*)ks, SC_T, sm)), dim3(SC_T), sm, in,
+                         (const uint64_t*)nullptr, (const uint64_t*)nullptr, (const uint64_t*)d_ntiles, 0, dg,
+                         SC_FMAX, (const uint32_t*)nullptr, 0u, cur, prow, c->d_err)) != JN_OK)
+            break;
+        const uint64_t* roff = start;
+        const uint64_t* soff = start + P;
+        if ((st = launch(c, K_ITEMS, k_items, dim3((unsigned)ceil_div(P, 256)), dim3(256), 0, roff, soff, (int)P,
+                         cap, items)) != JN_OK)
+            break;
+        if ((st = scan_u64(c, items, iprefix, (int64_t)P)) != JN_OK) break;
+        if ((st = launch(c, K_ITEMS, k_item_desc, dim3((unsigned)ceil_div(item_bound, 256)), dim3(256), 0, roff,
+                         soff, (const uint64_t*)iprefix, (int)P, cap, idesc)) != JN_OK)
+            break;
+        auto kc = k_hash_join<K, MODE_COUNT, false>;
+        const size_t smc = hash_smem<K>(MODE_COUNT);
+        if ((st = launch(c, K_HASH_COUNT, kc, dim3(persistent_grid(c, (const void*)kc, HJ_T, smc)), dim3(HJ_T), smc,
+                         (const RW*)prow, (const RW*)prow, (const Item*)idesc, (const uint64_t*)(iprefix + P),
+                         SC_FMAX == 1024 ? 10 : 10, ival, chk, (const uint64_t*)nullptr, (jn_pair*)nullptr,
+                         c->d_err)) != JN_OK)
+            break;
+        // items past the real count keep zero counts: scan the whole bound
+        if ((st = scan_u64(c, reinterpret_cast<const uint64_t*>(ival), ioff, (int64_t)item_bound)) != JN_OK) break;
+        if ((st = launch(c, K_MISC, k_batch_offsets, dim3((unsigned)ceil_div((uint64_t)n + 1, 256)), dim3(256), 0,
+                         (const uint64_t*)iprefix, (const uint64_t*)ioff, n, d_off)) != JN_OK)
+            break;
+    } while (0);
+    if (st != JN_OK) {
+        abort_capture();
+        return st;
+    }
+    JN_TRY(end_replay(&g1, &x1));
+    std::vector<uint64_t> hoff((size_t)n + 1);
+    JN_CUDA(c, cudaMemcpyAsync(hoff.data(), d_off, sizeof(uint64_t) * (n + 1), cudaMemcpyDeviceToHost, c->stream));
+    uint64_t dummy;
+    JN_TRY(read_back(c, d_small, &dummy, 0));
+    const uint64_t total = hoff[n];
+    for (int i = 0; i <= n; i++) offsets[i] = hoff[i];
+    // ---- phase 2: one exact allocation (with room for `extra` more pairs), then the emit pass ----
+    JN_TRY(out_prepare(c, s, total + extra, *plan));
+    if (total > 0) {
+        JN_TRY(begin_capture());
+        auto ke = k_hash_join<K, MODE_EMIT>;
+        const size_t sme = hash_smem<K>(MODE_EMIT);
+        st = launch(c, K_HASH_EMIT, ke, dim3(persistent_grid(c, (const void*)ke, HJ_T, sme)), dim3(HJ_T), sme,
+                    (const RW*)prow, (const RW*)prow, (const Item*)idesc, (const uint64_t*)(iprefix + P), 10,
+                    (unsigned long long*)nullptr, (unsigned long long*)nullptr, (const uint64_t*)ioff, plan->dev,
+                    c->d_err);
+        if (st != JN_OK) {
+            abort_capture();
+            return st;
+        }
+        JN_TRY(end_replay(&g2, &x2));
+    }
+    if (plan->host_copy)
+        return fail(c, JN_ERR_INVALID, "batch outputs must be device memory");
+    JN_TRY(out_finish(c, total + extra, *plan));
+    JN_TRY(read_back(c, d_small, &dummy, 0));
+    c->info.result = total;
+    c->info.partitions = P;
+    c->info.work_items = item_bound;
+    return JN_OK;
+}
+
+template jn_status run_batch_hash<int32_t>(jn_ctx*, int, const Cols<int32_t>*, const Cols<int32_t>*, OutPlan*,
+                                           uint64_t*, uint64_t);
+template jn_status run_batch_hash<int64_t>(jn_ctx*, int, const Cols<int64_t>*, const Cols<int64_t>*, OutPlan*,
+                                           uint64_t*, uint64_t);
 
 template jn_status run_hash<int32_t>(jn_ctx*, const Cols<int32_t>&, const Cols<int32_t>&, int,
                                      OutPlan*, RunResult*);

@@ -403,7 +403,7 @@ static jn_status range_partition(jn_ctx* c, Scratch& s, const Cols<K>& T, const 
     per = 0;
     ensure_smem((const void*)ks, sm);
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, ks, SC_T, sm);
-    PartIn<K, HB> in{grp, carry, T.pay, nullptr, n};
+    PartIn<K, HB> in{grp, carry, T.pay, nullptr, n, nullptr, nullptr};
     JN_TRY(launch(c, K_SCATTER, ks, dim3(max(per, 1) * c->num_sms), dim3(SC_T), sm, in, (const uint64_t*)sb,
                   (const uint64_t*)scn, (const uint64_t*)tp, 1, dg, G, (const uint32_t*)nullptr, 0u, cur, rows,
                   c->d_err));

@@ -47,7 +47,34 @@ class Tuning(ctypes.Structure):
     _fields_ = [("prefilter", ctypes.c_int32), ("radix_bits", ctypes.c_int32),
                 ("radix_bits1", ctypes.c_int32), ("filter_bits", ctypes.c_int32),
                 ("heavy", ctypes.c_int32), ("theta_groups", ctypes.c_int32),
-                ("nlj_tile_r", ctypes.c_int32), ("reserved", ctypes.c_int32 * 9)]
+                ("nlj_tile_r", ctypes.c_int32), ("graphs", ctypes.c_int32),
+                ("reserved", ctypes.c_int32 * 8)]
+
+
+class Join(ctypes.Structure):
+    _fields_ = [("R", Table), ("S", Table), ("op", ctypes.c_int32), ("reserved", ctypes.c_int32),
+                ("band", ctypes.c_int64)]
+
+
+class ServerConfig(ctypes.Structure):
+    _fields_ = [("slots", ctypes.c_int32), ("coalesce_rows", ctypes.c_int32), ("max_batch", ctypes.c_int32),
+                ("graphs", ctypes.c_int32), ("memory_budget", ctypes.c_uint64)]
+
+
+class Request(ctypes.Structure):
+    _fields_ = [("r_handle", ctypes.c_int32), ("s_handle", ctypes.c_int32), ("R", Table), ("S", Table),
+                ("op", ctypes.c_int32), ("reserved", ctypes.c_int32), ("band", ctypes.c_int64)]
+
+
+class Result(ctypes.Structure):
+    _fields_ = [("status", ctypes.c_int32), ("reserved", ctypes.c_int32), ("pairs", ctypes.c_uint64),
+                ("out", ctypes.c_void_p), ("queue_ms", ctypes.c_double), ("run_ms", ctypes.c_double),
+                ("total_ms", ctypes.c_double)]
+
+
+class ServerStats(ctypes.Structure):
+    _fields_ = [(n, ctypes.c_uint64) for n in ("submitted", "completed", "failed", "batches", "queued",
+                                               "held_bytes", "peak_bytes", "resident_bytes")]
 
 
 class KernelStat(ctypes.Structure):
@@ -93,13 +120,25 @@ _SIGS = {
     "jn_theta": (ctypes.c_int, [_P, ctypes.POINTER(Table), ctypes.POINTER(Table), ctypes.c_int32,
                                 ctypes.c_int64, ctypes.POINTER(_P), ctypes.c_uint64,
                                 ctypes.POINTER(ctypes.c_uint64)]),
+    "jn_batch": (ctypes.c_int, [_P, ctypes.c_int32, ctypes.POINTER(Join), ctypes.POINTER(_P), ctypes.c_uint64,
+                                ctypes.POINTER(ctypes.c_uint64), ctypes.POINTER(ctypes.c_uint64),
+                                ctypes.POINTER(ctypes.c_uint64)]),
     "jn_free": (None, [_P, _P]),
+    "jn_server_create": (ctypes.c_int, [ctypes.POINTER(_P), ctypes.c_int, ctypes.POINTER(ServerConfig)]),
+    "jn_server_destroy": (None, [_P]),
+    "jn_server_register": (ctypes.c_int, [_P, ctypes.POINTER(Table), ctypes.POINTER(ctypes.c_int32)]),
+    "jn_server_unregister": (ctypes.c_int, [_P, ctypes.c_int32]),
+    "jn_server_submit": (ctypes.c_int, [_P, ctypes.POINTER(Request), ctypes.POINTER(ctypes.c_uint64)]),
+    "jn_server_wait": (ctypes.c_int, [_P, ctypes.c_uint64, ctypes.POINTER(Result)]),
+    "jn_server_release": (ctypes.c_int, [_P, ctypes.c_uint64]),
+    "jn_server_stats_get": (ctypes.c_int, [_P, ctypes.POINTER(ServerStats)]),
     "jn_set_profiling": (ctypes.c_int, [_P, ctypes.c_int32]),
     "jn_kernel_stats": (ctypes.c_int, [_P, ctypes.POINTER(KernelStat), ctypes.c_int32,
                                        ctypes.POINTER(ctypes.c_int32)]),
     "jn_reset_stats": (ctypes.c_int, [_P]),
     "jn_last_run_info": (ctypes.c_int, [_P, ctypes.POINTER(RunInfo)]),
     "jn_launch_count": (ctypes.c_uint64, [_P]),
+    "jn_pointer_is_device": (ctypes.c_int32, [_P]),
 }
 
 
@@ -291,3 +330,119 @@ def jn_hash(ctx: Context, R: TableRef, S: TableRef, out=None):
 
 def jn_theta(ctx: Context, R: TableRef, S: TableRef, op: int, band: int = -1, out=None):
     return _emit(ctx, load().jn_theta, (ctypes.byref(R.t), ctypes.byref(S.t), op, band), out)
+
+
+def jn_batch(ctx: Context, joins, out=None):
+    """Runs a batch of joins [(R, S, op, band), ...] (band < 0: equi-join).
+
+    Returns (pairs, first, count): the pairs of join i are
+    pairs[first[i] : first[i] + count[i]].
+    """
+    n = len(joins)
+    arr = (Join * max(n, 1))()
+    for i, (R, S, op, band) in enumerate(joins):
+        arr[i] = Join(R.t, S.t, op, 0, band)
+    first = (ctypes.c_uint64 * max(n, 1))()
+    cnt = (ctypes.c_uint64 * max(n, 1))()
+    total = ctypes.c_uint64()
+    if out is None:
+        p = _P(None)
+        cap = 0
+    else:
+        p = _P(out.data_ptr())
+        cap = out.shape[0]
+    st = load().jn_batch(ctx.handle, n, arr, ctypes.byref(p), cap, ctypes.byref(total), first, cnt)
+    _check(ctx, st, required=int(total.value) if st == JN_ERR_CAPACITY else None)
+    res = _result(ctx, p, int(total.value), out)
+    return res, [int(first[i]) for i in range(n)], [int(cnt[i]) for i in range(n)]
+
+
+class _View:
+    """A non-owning view of device pairs (valid until the owner releases them)."""
+
+    def __init__(self, ptr, n):
+        self.__cuda_array_interface__ = {"shape": (n, 2), "typestr": "<i4", "data": (ptr, False),
+                                         "version": 3, "strides": None, "stream": None}
+
+
+class Server:
+    """jn_server: a request loop over the library (see jn.h, serving)."""
+
+    def __init__(self, device=0, slots=4, coalesce_rows=1 << 18, max_batch=64, memory_budget=64 << 30,
+                 graphs=False):
+        lib = load()
+        cfg = ServerConfig(slots, coalesce_rows, max_batch, 1 if graphs else 0, memory_budget)
+        h = _P()
+        st = lib.jn_server_create(ctypes.byref(h), device, ctypes.byref(cfg))
+        if st != JN_OK:
+            raise JoinError(st, "jn_server_create failed")
+        self.handle = h
+        self.device = device
+        self._keep = {}
+
+    def close(self):
+        if self.handle:
+            load().jn_server_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def register(self, t: TableRef) -> int:
+        hnd = ctypes.c_int32()
+        st = load().jn_server_register(self.handle, ctypes.byref(t.t), ctypes.byref(hnd))
+        if st != JN_OK:
+            raise JoinError(st, "jn_server_register failed")
+        return int(hnd.value)
+
+    def unregister(self, handle: int):
+        st = load().jn_server_unregister(self.handle, handle)
+        if st != JN_OK:
+            raise JoinError(st, "jn_server_unregister failed")
+
+    def submit(self, R=None, S=None, op=JN_EQ, band=-1, r_handle=0, s_handle=0) -> int:
+        """R, S: TableRef (device columns) or None with a registered handle."""
+        empty = Table(None, None, None, 0, JN_KEY_I32, 0)
+        req = Request(r_handle, s_handle, R.t if R is not None else empty, S.t if S is not None else empty,
+                      op, 0, band)
+        if r_handle and R is None and S is not None:
+            req.R.key_type = S.t.key_type
+        if s_handle and S is None and R is not None:
+            req.S.key_type = R.t.key_type
+        tk = ctypes.c_uint64()
+        st = load().jn_server_submit(self.handle, ctypes.byref(req), ctypes.byref(tk))
+        if st != JN_OK:
+            raise JoinError(st, "jn_server_submit failed")
+        self._keep[int(tk.value)] = (R, S)  # columns stay alive until the request is released
+        return int(tk.value)
+
+    def wait(self, ticket: int) -> dict:
+        r = Result()
+        st = load().jn_server_wait(self.handle, ticket, ctypes.byref(r))
+        if st != JN_OK:
+            raise JoinError(st, "jn_server_wait failed")
+        return {"status": r.status, "pairs": int(r.pairs), "out": r.out, "queue_ms": r.queue_ms,
+                "run_ms": r.run_ms, "total_ms": r.total_ms}
+
+    def pairs(self, res: dict):
+        """Copies a finished request's pairs into a new CUDA tensor."""
+        if res["status"] != JN_OK:
+            raise JoinError(res["status"], "request failed")
+        if res["pairs"] == 0:
+            return torch.empty((0, 2), dtype=torch.int32, device="cuda:%d" % self.device)
+        if not res["out"] or not load().jn_pointer_is_device(_P(res["out"])):
+            raise JoinError(JN_ERR_CUDA, "request output is not device memory: %r" % (res["out"],))
+        v = torch.as_tensor(_View(res["out"], res["pairs"]), device="cuda:%d" % self.device)
+        return v.clone()
+
+    def release(self, ticket: int):
+        load().jn_server_release(self.handle, ticket)
+        self._keep.pop(ticket, None)
+
+    def stats(self) -> dict:
+        x = ServerStats()
+        load().jn_server_stats_get(self.handle, ctypes.byref(x))
+        return {f: int(getattr(x, f)) for f, _ in ServerStats._fields_}

@@ -301,3 +301,57 @@ def test_hash_one_key_everywhere(ctx):
         g = got.cpu().numpy()
         assert np.array_equal(np.bincount(g[:, 0], minlength=3000), np.full(3000, 5000))
         assert np.array_equal(np.bincount(g[:, 1], minlength=5000), np.full(5000, 3000))
+
+
+# ------------------------------------------------------------------ batch --
+
+@pytest.mark.parametrize("graphs", [0, 1])
+def test_batch_matches_oracle_per_join(ctx, graphs):
+    sizes = datagen.log_uniform_int(40, 1, 30000, seed=31, stream=0).tolist()
+    sizes2 = datagen.log_uniform_int(40, 1, 50000, seed=31, stream=1).tolist()
+    joins, exp, keep = [], [], []
+    for i, (nr, ns) in enumerate(zip(sizes, sizes2)):
+        if i % 3 == 2:  # band join
+            ra, rk = datagen.band_columns(nr, 14, seed=40 + i, stream=0)
+            sa, sk = datagen.band_columns(ns, 14, seed=40 + i, stream=1)
+            w = i % 7
+            keep.append((ra, rk, sa, sk))
+            joins.append((jn.table(ra.to(DEV), rk.to(DEV)), jn.table(sa.to(DEV), sk.to(DEV)), jn.JN_LT, w))
+            exp.append(canon(O.band_join_sorted(ra.numpy(), rk.numpy(), sa.numpy(), sk.numpy(), O.LT, w)))
+        else:
+            d = max(16, (nr + ns) // (1 + i % 4))
+            r = keys(nr, 0, d, 50 + i, 0)
+            s = keys(ns, 0, d, 50 + i, 1)
+            rp = datagen.uniform_int(nr, I32_MIN, I32_MAX, 60 + i, 2)
+            keep.append((r, s, rp))
+            joins.append((jn.table(r.to(DEV), payload=rp.to(DEV)), jn.table(s.to(DEV)), jn.JN_EQ, -1))
+            exp.append(canon(O.hash_join(r.numpy(), s.numpy(), rp.numpy(), None)))
+    ctx.set_tuning(graphs=graphs)
+    try:
+        pairs, first, cnt = jn.jn_batch(ctx, joins)
+    finally:
+        ctx.set_tuning(graphs=0)
+    got = pairs.cpu().numpy()
+    assert got.shape[0] == sum(cnt)
+    for i in range(len(joins)):
+        assert cnt[i] == exp[i].shape[0], i
+        assert np.array_equal(canon(got[first[i]:first[i] + cnt[i]]), exp[i]), i
+    # alone and in the batch: the same pairs
+    for i in (0, 1, 2):
+        R, S, op, band = joins[i]
+        alone = jn.jn_hash(ctx, R, S) if band < 0 else jn.jn_theta(ctx, R, S, op, band)
+        assert np.array_equal(canon(alone), exp[i])
+
+
+def test_batch_capacity_and_empty(ctx):
+    r = keys(1000, 0, 50, 70, 0)
+    s = keys(1000, 0, 50, 70, 1)
+    joins = [(jn.table(r.to(DEV)), jn.table(s.to(DEV)), jn.JN_EQ, -1),
+             (jn.table(r[:0].to(DEV)), jn.table(s.to(DEV)), jn.JN_EQ, -1)]
+    m = O.hash_join(r.numpy(), s.numpy(), count_only=True)
+    small = torch.empty((m - 1, 2), dtype=torch.int32, device=DEV)
+    with pytest.raises(jn.JoinError) as e:
+        jn.jn_batch(ctx, joins, out=small)
+    assert e.value.status == jn.JN_ERR_CAPACITY and e.value.required == m
+    pairs, first, cnt = jn.jn_batch(ctx, joins)
+    assert cnt == [m, 0]
