@@ -224,6 +224,32 @@ typedef struct {
 jn_status jn_batch(jn_ctx* ctx, int32_t count, const jn_join* joins, jn_pair** out, uint64_t capacity,
                    uint64_t* n_out, uint64_t* first, uint64_t* pairs);
 
+/* Nested-loop join that allocates nothing, for callers that may not
+ * allocate device memory: an application that owns every byte of the device
+ * under a fixed memory plan, or a latency-critical loop that must not call
+ * cudaMalloc / cudaFree (or any allocator, this library's pool included) and
+ * the synchronisation they bring.  The paper has no counterpart; it is the
+ * jn_nested_loop join without its allocations.
+ *   - Scratch is one fixed device array inside the library (about 1 MiB per
+ *     device, held until the process exits); a call handles at most 65536
+ *     tiles, i.e. ceil(|S| / 1024) * ceil(|R| / 1024) <= 65536 and
+ *     ceil(|R| / 1024) <= 65535.  Larger inputs return JN_ERR_INVALID.
+ *   - Every call shares that array and it keeps the previous call's contents
+ *     (the call rewrites what it reads): calls that overlap on the GPU, from
+ *     any thread or stream, race and must be serialised by the caller.
+ *   - The first call on a device looks up the array's device address; make
+ *     that first call before any stream capture.
+ *   - Columns must be device memory; the output is a caller buffer of
+ *     `capacity` pairs in device memory.  When the result has more pairs,
+ *     JN_ERR_CAPACITY is returned with *n_out = the required count and
+ *     nothing is written.
+ *   - Work is issued on `stream` (a cudaStream_t, NULL = legacy default); the
+ *     call waits for the count, then queues the writes, which are complete
+ *     when the stream reaches that point.
+ * No context is used, so no error text is recorded: the status says it all. */
+jn_status jn_nested_loop_noalloc(const jn_table* R, const jn_table* S, const jn_pred* pred, jn_pair* out,
+                                 uint64_t capacity, uint64_t* n_out, void* stream);
+
 /* Release an output allocated by a join (stream ordered on the context's
  * stream; with ctx == NULL, on the legacy default stream, so results may
  * outlive their context). */

@@ -11,6 +11,8 @@
 // writes one count per tile; an exclusive scan gives each tile its exact
 // output offset (replacing the NB_S * NB_T per-thread buffers); the emit pass
 // repeats the comparisons and writes pairs.
+#include <mutex>
+
 #include "jn_algos.h"
 
 namespace jnx {
@@ -181,9 +183,136 @@ jn_status run_nlj(jn_ctx* c, const Cols<K>& R, const Cols<K>& S, const jn_pred& 
     return JN_OK;
 }
 
+// ------------------------------------------------------ allocation-free --
+// A nested-loop join for callers that may not allocate device memory at all:
+// code running inside a region where the application owns every byte of the
+// device (a fixed memory plan, a real-time or serving loop that forbids
+// cudaMalloc / cudaFree and the synchronisation they bring), or code that
+// must not touch any allocator, the library's pool included.  Its scratch
+// (per-tile counts, their scan and the checksum word) lives in the fixed
+// device array below, so a call allocates nothing; the caller supplies the
+// output buffer.
+constexpr int NA_MAX_TILES = 65536;  // R tiles x S tiles per call
+static __device__ __align__(256) unsigned long long g_na_scratch[2 * NA_MAX_TILES + 8];
+
+// Device address of g_na_scratch, looked up once per device (host code
+// cannot use the symbol itself as an address).
+static std::mutex g_na_mu;
+static void* g_na_addr[64];
+
+static jn_status na_scratch(void** p) {
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) {
+        cudaGetLastError();
+        return JN_ERR_CUDA;
+    }
+    std::lock_guard<std::mutex> g(g_na_mu);
+    if (!g_na_addr[dev]) {
+        void* a = nullptr;
+        if (cudaGetSymbolAddress(&a, g_na_scratch) != cudaSuccess || !a) {
+            cudaGetLastError();
+            return JN_ERR_CUDA;
+        }
+        g_na_addr[dev] = a;
+    }
+    *p = g_na_addr[dev];
+    return JN_OK;
+}
+
+// Single-block exclusive scan of n <= NA_MAX_TILES counts; out[n] = total.
+static __global__ void k_na_scan(const unsigned long long* __restrict__ in, int n, unsigned long long* __restrict__ out) {
+    __shared__ unsigned long long tmp[33];
+    unsigned long long carry = 0;
+    for (int base = 0; base < n; base += blockDim.x) {
+        const int i = base + threadIdx.x;
+        const unsigned long long v = i < n ? in[i] : 0ull;
+        unsigned long long tot;
+        const unsigned long long pre = block_excl_scan(v, tmp, &tot);
+        if (i < n) out[i] = carry + pre;
+        carry += tot;
+    }
+    if (threadIdx.x == 0) out[n] = carry;
+}
+
+template <typename K, bool HAS2>
+static jn_status na_run(const jn_table* R, const jn_table* S, const jn_pred& pr, jn_pair* out, uint64_t capacity,
+                        uint64_t* n_out, cudaStream_t st) {
+    const int tr = 1024;
+    const uint64_t gx = ceil_div((uint64_t)S->n, NLJ_STILE), gy = ceil_div((uint64_t)R->n, tr);
+    const uint64_t tiles = gx * gy;
+    if (tiles > NA_MAX_TILES || gy > 65535) return JN_ERR_INVALID;  // beyond the fixed scratch
+    void* base = nullptr;
+    JN_TRY(na_scratch(&base));
+    unsigned long long* val = static_cast<unsigned long long*>(base);
+    unsigned long long* off = val + NA_MAX_TILES;
+    unsigned long long* chk = off + NA_MAX_TILES + 1;
+    const dim3 grid((unsigned)gx, (unsigned)gy);
+    const size_t smem = (size_t)tr * (sizeof(K) * (HAS2 ? 2 : 1) + 4);
+    const K* rk = static_cast<const K*>(R->key);
+    const K* rk2 = static_cast<const K*>(R->key2);
+    const K* sk = static_cast<const K*>(S->key);
+    const K* sk2 = static_cast<const K*>(S->key2);
+    // the array keeps the previous call's contents: counts are rewritten for
+    // every tile of this call, the checksum word is cleared
+    if (cudaMemsetAsync(chk, 0, sizeof(unsigned long long), st) != cudaSuccess) return JN_ERR_CUDA;
+    k_nlj<K, HAS2, MODE_COUNT><<<grid, NLJ_T, smem, st>>>(rk, rk2, R->payload, R->n, sk, sk2, S->payload, S->n,
+                                                          pr.op_a, pr.op_k, (long long)pr.band, tr, val, chk,
+                                                          nullptr, nullptr);
+    k_na_scan<<<1, 1024, 0, st>>>(val, (int)tiles, off);
+    if (cudaGetLastError() != cudaSuccess) return JN_ERR_CUDA;
+    uint64_t total = 0;
+    if (cudaMemcpyAsync(&total, off + tiles, sizeof(uint64_t), cudaMemcpyDeviceToHost, st) != cudaSuccess ||
+        cudaStreamSynchronize(st) != cudaSuccess) {
+        cudaGetLastError();
+        return JN_ERR_CUDA;
+    }
+    *n_out = total;
+    if (total > capacity) return JN_ERR_CAPACITY;
+    if (total > 0) {
+        k_nlj<K, HAS2, MODE_EMIT><<<grid, NLJ_T, smem, st>>>(rk, rk2, R->payload, R->n, sk, sk2, S->payload, S->n,
+                                                             pr.op_a, pr.op_k, (long long)pr.band, tr, nullptr,
+                                                             nullptr, reinterpret_cast<const uint64_t*>(off), out);
+        if (cudaGetLastError() != cudaSuccess) return JN_ERR_CUDA;
+    }
+    return JN_OK;
+}
+
 template jn_status run_nlj<int32_t>(jn_ctx*, const Cols<int32_t>&, const Cols<int32_t>&,
                                     const jn_pred&, int, OutPlan*, RunResult*);
 template jn_status run_nlj<int64_t>(jn_ctx*, const Cols<int64_t>&, const Cols<int64_t>&,
                                     const jn_pred&, int, OutPlan*, RunResult*);
 
 }  // namespace jnx
+
+using namespace jnx;
+
+extern "C" jn_status jn_nested_loop_noalloc(const jn_table* R, const jn_table* S, const jn_pred* pred,
+                                            jn_pair* out, uint64_t capacity, uint64_t* n_out, void* stream) {
+    if (!R || !S || !n_out || (capacity > 0 && !out)) return JN_ERR_INVALID;
+    if (R->key_type != S->key_type || (R->key_type != JN_KEY_I32 && R->key_type != JN_KEY_I64)) return JN_ERR_INVALID;
+    if (R->n < 0 || S->n < 0 || R->n > INT32_MAX || S->n > INT32_MAX || R->reserved || S->reserved)
+        return JN_ERR_INVALID;
+    jn_pred pr;
+    pr.op_a = JN_EQ;
+    pr.op_k = JN_ANY;
+    pr.band = -1;
+    if (pred) pr = *pred;
+    if (pr.op_a < JN_EQ || pr.op_a > JN_ANY || pr.op_k < JN_EQ || pr.op_k > JN_ANY) return JN_ERR_INVALID;
+    // columns and output must be device memory: nothing may be staged
+    const void* cols[6] = {R->key, R->key2, R->payload, S->key, S->key2, S->payload};
+    for (const void* c : cols)
+        if (c && !is_device_pointer(c)) return JN_ERR_INVALID;
+    if (capacity > 0 && !is_device_pointer(out)) return JN_ERR_INVALID;
+    if (R->n == 0 || S->n == 0) {
+        *n_out = 0;
+        return JN_OK;
+    }
+    if ((R->n > 0 && !R->key) || (S->n > 0 && !S->key)) return JN_ERR_INVALID;
+    const bool has2 = R->key2 && S->key2;
+    cudaStream_t st = (cudaStream_t)stream;
+    if (R->key_type == JN_KEY_I32)
+        return has2 ? na_run<int32_t, true>(R, S, pr, out, capacity, n_out, st)
+                    : na_run<int32_t, false>(R, S, pr, out, capacity, n_out, st);
+    return has2 ? na_run<int64_t, true>(R, S, pr, out, capacity, n_out, st)
+                : na_run<int64_t, false>(R, S, pr, out, capacity, n_out, st);
+}

@@ -124,6 +124,8 @@ _SIGS = {
                                 ctypes.POINTER(ctypes.c_uint64), ctypes.POINTER(ctypes.c_uint64),
                                 ctypes.POINTER(ctypes.c_uint64)]),
     "jn_free": (None, [_P, _P]),
+    "jn_nested_loop_noalloc": (ctypes.c_int, [ctypes.POINTER(Table), ctypes.POINTER(Table), ctypes.POINTER(Pred),
+                                              _P, ctypes.c_uint64, ctypes.POINTER(ctypes.c_uint64), _P]),
     "jn_server_create": (ctypes.c_int, [ctypes.POINTER(_P), ctypes.c_int, ctypes.POINTER(ServerConfig)]),
     "jn_server_destroy": (None, [_P]),
     "jn_server_register": (ctypes.c_int, [_P, ctypes.POINTER(Table), ctypes.POINTER(ctypes.c_int32)]),
@@ -446,3 +448,18 @@ class Server:
         x = ServerStats()
         load().jn_server_stats_get(self.handle, ctypes.byref(x))
         return {f: int(getattr(x, f)) for f, _ in ServerStats._fields_}
+
+
+def jn_nested_loop_noalloc(R: TableRef, S: TableRef, pr: Pred = None, out=None, stream=None):
+    """The allocation-free nested-loop join: pairs go to the caller's `out`
+    (a (cap, 2) int32 CUDA tensor); returns the filled view."""
+    if out is None:
+        raise ValueError("jn_nested_loop_noalloc writes to a caller buffer: pass out=")
+    n = ctypes.c_uint64()
+    st = stream if stream is not None else torch.cuda.current_stream()
+    rc = load().jn_nested_loop_noalloc(ctypes.byref(R.t), ctypes.byref(S.t),
+                                       ctypes.byref(pr) if pr is not None else None, _P(out.data_ptr()),
+                                       out.shape[0], ctypes.byref(n), _P(st.cuda_stream))
+    if rc != JN_OK:
+        raise JoinError(rc, load().jn_status_str(rc).decode(), int(n.value) if rc == JN_ERR_CAPACITY else None)
+    return out[:int(n.value)]
