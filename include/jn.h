@@ -214,11 +214,13 @@ typedef struct {
  * one device output (jn.h's output convention; the output must be device
  * memory, and *n_out receives the total).  first[i] and pairs[i] (host,
  * count words each) receive where join i's pairs start and how many there
- * are: they are out[first[i] .. first[i] + pairs[i]).  Equi-joins of a batch
- * share every phase (one radix pass over all their tables, one count pass
- * and one emit pass over a single work queue of (join, partition) items);
- * band joins are counted and written one after another.  The whole batch
- * makes one exact output allocation.  This is the batched form of the
+ * are: they are out[first[i] .. first[i] + pairs[i]).  The equi-joins of a
+ * batch share every phase (one radix pass over all their tables, one count
+ * pass and one emit pass over a single work queue of (join, partition)
+ * items), and so do its band joins (one range pass, one count pass and one
+ * emit pass over (join, group) items).  Every join is counted before the
+ * single exact output allocation; with tuning.graphs on, each phase is
+ * replayed as a CUDA graph.  This is the batched form of the
  * Reducer = grid hierarchy of Sec. 3.3.4: many small joins fill the GPU
  * together instead of one launch sequence each. */
 jn_status jn_batch(jn_ctx* ctx, int32_t count, const jn_join* joins, jn_pair** out, uint64_t capacity,

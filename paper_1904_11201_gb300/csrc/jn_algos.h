@@ -1,6 +1,9 @@
 // Internal entry points of the join algorithms (device-resident columns).
 #pragma once
 
+#include <memory>
+#include <vector>
+
 #include "jn_common.cuh"
 
 namespace jnx {
@@ -40,9 +43,39 @@ template <typename K>
 jn_status run_hash(jn_ctx* c, const Cols<K>& R, const Cols<K>& S, int mode, OutPlan* plan,
                    RunResult* res);
 
+// A batch of joins run as one: prepare() (all passes up to the exact
+// counts) fills total and the per-join offsets; emit() writes the pairs to
+// out[0 .. total).  The object owns the batch's scratch between the two.
+struct BatchRun {
+    uint64_t total = 0;
+    std::vector<uint64_t> offsets;  // joins + 1 offsets inside this run's pairs
+    virtual ~BatchRun() {}
+    virtual jn_status emit(jn_ctx* c, jn_pair* out) = 0;
+};
+
 template <typename K>
-jn_status run_batch_hash(jn_ctx* c, int n, const Cols<K>* Rs, const Cols<K>* Ss, OutPlan* plan,
-                         uint64_t* offsets, uint64_t extra);
+jn_status batch_hash_prepare(jn_ctx* c, int n, const Cols<K>* Rs, const Cols<K>* Ss, std::unique_ptr<BatchRun>* run);
+
+template <typename K>
+jn_status batch_band_prepare(jn_ctx* c, int m, const Cols<K>* Rs, const Cols<K>* Ss, const int* ops,
+                             const int64_t* bands, std::unique_ptr<BatchRun>* run);
+
+// Captures a sequence of launches on the context's private stream and replays
+// it as a CUDA graph on the context's stream (or runs it directly when graphs
+// are off).  The caller's stream may be the legacy default stream, which
+// cannot itself be captured.
+struct GraphPhase {
+    jn_ctx* c;
+    bool on;
+    cudaStream_t user = nullptr;
+    cudaGraph_t g = nullptr;
+    cudaGraphExec_t x = nullptr;
+    GraphPhase(jn_ctx* ctx, bool graphs) : c(ctx), on(graphs) {}
+    ~GraphPhase();
+    jn_status begin();
+    jn_status end_and_run();
+    void abort();
+};
 
 template <typename K>
 jn_status run_nlj(jn_ctx* c, const Cols<K>& R, const Cols<K>& S, const jn_pred& pred, int mode,

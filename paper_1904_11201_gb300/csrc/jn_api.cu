@@ -136,60 +136,47 @@ static jn_status batch_typed(jn_ctx* c, int count, const jn_join* joins, jn_pair
     Scratch s(c);
     std::vector<int> eq, bd;
     for (int i = 0; i < count; i++) (joins[i].band < 0 ? eq : bd).push_back(i);
-    std::vector<Cols<K>> Rs(eq.size()), Ss(eq.size());
+    std::vector<Cols<K>> ER(eq.size()), ES(eq.size()), BR(bd.size()), BS(bd.size());
+    std::vector<int> bops(bd.size());
+    std::vector<int64_t> bbands(bd.size());
     for (size_t j = 0; j < eq.size(); j++) {
-        JN_TRY(stage<K>(c, s, &joins[eq[j]].R, false, &Rs[j]));
-        JN_TRY(stage<K>(c, s, &joins[eq[j]].S, false, &Ss[j]));
+        JN_TRY(stage<K>(c, s, &joins[eq[j]].R, false, &ER[j]));
+        JN_TRY(stage<K>(c, s, &joins[eq[j]].S, false, &ES[j]));
     }
-    // band joins: exact counts first, so the batch allocates once
-    std::vector<Cols<K>> BR(bd.size()), BS(bd.size());
-    std::vector<uint64_t> bcnt(bd.size());
-    uint64_t extra = 0;
     for (size_t j = 0; j < bd.size(); j++) {
         JN_TRY(stage<K>(c, s, &joins[bd[j]].R, true, &BR[j]));
         JN_TRY(stage<K>(c, s, &joins[bd[j]].S, true, &BS[j]));
-        RunResult rr;
-        JN_TRY(run_theta<K>(c, BR[j], BS[j], joins[bd[j]].op, joins[bd[j]].band, MODE_COUNT, nullptr, &rr));
-        bcnt[j] = rr.count;
-        extra += rr.count;
+        bops[j] = joins[bd[j]].op;
+        bbands[j] = joins[bd[j]].band;
     }
+    // every join is counted before the single output allocation
+    std::unique_ptr<BatchRun> he, be;
+    if (!eq.empty()) JN_TRY(batch_hash_prepare<K>(c, (int)eq.size(), ER.data(), ES.data(), &he));
+    if (!bd.empty())
+        JN_TRY(batch_band_prepare<K>(c, (int)bd.size(), BR.data(), BS.data(), bops.data(), bbands.data(), &be));
+    const uint64_t te = he ? he->total : 0, tb = be ? be->total : 0;
     OutPlan plan;
     plan.user_out = out;
     plan.capacity = capacity;
     plan.n_out = n_out;
-    uint64_t eq_total = 0;
-    if (!eq.empty()) {
-        std::vector<uint64_t> off(eq.size() + 1);
-        JN_TRY(run_batch_hash<K>(c, (int)eq.size(), Rs.data(), Ss.data(), &plan, off.data(), extra));
-        for (size_t j = 0; j < eq.size(); j++) {
-            first[eq[j]] = off[j];
-            pairs[eq[j]] = off[j + 1] - off[j];
-        }
-        eq_total = off[eq.size()];
-    } else {
-        JN_TRY(out_prepare(c, s, extra, plan));
-        if (plan.host_copy) return fail(c, JN_ERR_INVALID, "batch outputs must be device memory");
-        JN_TRY(out_finish(c, extra, plan));
+    JN_TRY(out_prepare(c, s, te + tb, plan));
+    if (plan.host_copy) return fail(c, JN_ERR_INVALID, "batch outputs must be device memory");
+    if (he) JN_TRY(he->emit(c, plan.dev));
+    if (be) JN_TRY(be->emit(c, plan.dev + te));
+    for (size_t j = 0; j < eq.size(); j++) {
+        first[eq[j]] = he->offsets[j];
+        pairs[eq[j]] = he->offsets[j + 1] - he->offsets[j];
     }
-    jn_pair* base = *out;
-    uint64_t at = eq_total;
     for (size_t j = 0; j < bd.size(); j++) {
-        first[bd[j]] = at;
-        pairs[bd[j]] = bcnt[j];
-        if (bcnt[j]) {
-            jn_pair* dst = base + at;
-            uint64_t got = 0;
-            OutPlan bp;
-            bp.user_out = &dst;
-            bp.capacity = bcnt[j];
-            bp.n_out = &got;
-            RunResult rr;
-            JN_TRY(run_theta<K>(c, BR[j], BS[j], joins[bd[j]].op, joins[bd[j]].band, MODE_EMIT, &bp, &rr));
-        }
-        at += bcnt[j];
+        first[bd[j]] = te + be->offsets[j];
+        pairs[bd[j]] = be->offsets[j + 1] - be->offsets[j];
     }
-    *n_out = at;
-    c->info.result = at;
+    JN_TRY(out_finish(c, te + tb, plan));
+    uint64_t dummy;
+    uint64_t* d_small;
+    JN_TRY(s.get(&d_small, 1));
+    JN_TRY(read_back(c, d_small, &dummy, 0));  // reports a device wait that ran out
+    c->info.result = te + tb;
     return JN_OK;
 }
 

@@ -251,9 +251,9 @@ k_seg_hist(const K* __restrict__ keys, const uint64_t* __restrict__ seg_begin,
 template <typename K>
 struct SegCols {
     const K* key;
+    const K* key_b;      // second column carried along (band joins), or NULL
     const int32_t* pay;  // NULL = row index
     uint64_t n;
-    uint64_t pad;
 };
 
 // A tile of a batch: rows [beg, beg + cnt) of segment seg.
@@ -404,12 +404,13 @@ __device__ __forceinline__ void scatter_issue(TileDesc* d, const PartIn<K, HB>& 
         return;
     }
     const K* ikey = in.segs ? in.segs[d->seg].key : in.key;
+    const K* ikb = in.segs ? in.segs[d->seg].key_b : in.key_b;
     const int32_t* ipay = in.segs ? in.segs[d->seg].pay : in.pay;
     const uint64_t iok = in.segs ? in.segs[d->seg].n : in.rows_ok;
     uint64_t bk = 0, bb = 0, bp = 0;
     uint32_t nk = 0, nbb = 0, np = 0;
     bool ok = byte_span(ikey, d->beg, d->cnt, sizeof(K), iok, &bk, &nk);
-    if (ok && HB) ok = byte_span(in.key_b, d->beg, d->cnt, sizeof(K), iok, &bb, &nbb);
+    if (ok && HB) ok = byte_span(ikb, d->beg, d->cnt, sizeof(K), iok, &bb, &nbb);
     if (ok && ipay) ok = byte_span(ipay, d->beg, d->cnt, 4, iok, &bp, &np);
     if (!ok) return;
     d->tma = 1;
@@ -422,7 +423,7 @@ __device__ __forceinline__ void scatter_issue(TileDesc* d, const PartIn<K, HB>& 
     fence_proxy_async();
     mbar_arrive_expect_tx(bar, nk + nbb + np);
     tma_load_1d(gk, reinterpret_cast<const unsigned char*>(ikey) + bk, nk, bar);
-    if (HB) tma_load_1d(gb, reinterpret_cast<const unsigned char*>(in.key_b) + bb, nbb, bar);
+    if (HB) tma_load_1d(gb, reinterpret_cast<const unsigned char*>(ikb) + bb, nbb, bar);
     if (ipay) tma_load_1d(gp, reinterpret_cast<const unsigned char*>(ipay) + bp, np, bar);
 }
 
@@ -491,6 +492,7 @@ k_scatter(PartIn<K, HB> in, const uint64_t* __restrict__ seg_begin, const uint64
         const int cnt = d.cnt;
         dg.set_seg(d.seg);
         const K* ikey = in.segs ? in.segs[d.seg].key : in.key;
+        const K* ikb = in.segs ? in.segs[d.seg].key_b : in.key_b;
         const int32_t* ipay = in.segs ? in.segs[d.seg].pay : in.pay;
 
         R v[SC_IPT];
@@ -510,7 +512,7 @@ k_scatter(PartIn<K, HB> in, const uint64_t* __restrict__ seg_begin, const uint64
                     v[j].pay = ipay ? gp[d.poff + i] : (int32_t)(beg + i);
                 } else {
                     v[j].key = ikey[beg + i];
-                    if constexpr (HB) v[j].b = in.key_b[beg + i];
+                    if constexpr (HB) v[j].b = ikb[beg + i];
                     v[j].pay = ipay ? ipay[beg + i] : (int32_t)(beg + i);
                 }
             }

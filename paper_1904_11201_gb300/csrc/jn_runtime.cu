@@ -193,6 +193,51 @@ jn_status scan_u64(jn_ctx* c, const uint64_t* in, uint64_t* out, int64_t n) {
     return scan_impl<uint64_t>(c, in, out, n);
 }
 
+}  // namespace jnx
+#include "jn_algos.h"
+namespace jnx {
+
+GraphPhase::~GraphPhase() {
+    abort();
+    if (x) cudaGraphExecDestroy(x);
+    if (g) cudaGraphDestroy(g);
+}
+
+jn_status GraphPhase::begin() {
+    if (!on) return JN_OK;
+    if (!c->capture_stream) JN_CUDA(c, cudaStreamCreateWithFlags(&c->capture_stream, cudaStreamNonBlocking));
+    user = c->stream;
+    c->stream = c->capture_stream;
+    cudaError_t e = cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeThreadLocal);
+    if (e != cudaSuccess) {
+        c->stream = user;
+        user = nullptr;
+        return cuda_fail(c, e, "cudaStreamBeginCapture");
+    }
+    return JN_OK;
+}
+
+jn_status GraphPhase::end_and_run() {
+    if (!on) return JN_OK;
+    cudaError_t e = cudaStreamEndCapture(c->stream, &g);
+    c->stream = user;
+    user = nullptr;
+    JN_CUDA(c, e);
+    JN_CUDA(c, cudaGraphInstantiate(&x, g, 0));
+    JN_CUDA(c, cudaGraphLaunch(x, c->stream));
+    return JN_OK;
+}
+
+void GraphPhase::abort() {
+    if (!on || !user) return;
+    cudaGraph_t junk = nullptr;
+    cudaStreamEndCapture(c->stream, &junk);
+    if (junk) cudaGraphDestroy(junk);
+    c->stream = user;
+    user = nullptr;
+    cudaGetLastError();
+}
+
 static void resolve_pending(jn_ctx* c) {
     for (auto& p : c->pending) {
         float ms = 0.f;

@@ -820,203 +820,165 @@ __global__ void k_batch_offsets(const uint64_t* __restrict__ item_prefix, const 
 // A batch of equi-joins run as one: every table of every join is a segment
 // of one radix pass (segment i = R of join i, segment n + i = S of join i),
 // partition (i, d) has the global id i * 1024 + d, and the count and emit
-// passes run over the work queue of (partition, R chunk) items of all joins.
-// Each phase is one launch for the whole batch; with graphs on, the phases
-// up to the count read-back and the emit phase are each captured and
-// replayed as a CUDA graph.  offsets (host, n + 1) receives where each join's
-// pairs start in the output.
+// passes run over one work queue of (partition, R chunk) items of all joins.
+// Each phase is one launch for the whole batch; with graphs on, the phases up
+// to the count read-back and the emit phase are each replayed as a CUDA graph.
 template <typename K>
-jn_status run_batch_hash(jn_ctx* c, int n, const Cols<K>* Rs, const Cols<K>* Ss, OutPlan* plan,
-                         uint64_t* offsets, uint64_t extra) {
+struct HashBatchRun : BatchRun {
     using RW = Row<K, false>;
-    const int cap = cap_of<K>();
-    // ---- host plan: per-join fan-out, segment table and tile list ----
-    std::vector<SegCols<K>> segs(2 * (size_t)n);
-    std::vector<int> bits(2 * (size_t)n);
-    std::vector<TileRef> tiles;
-    uint64_t rows = 0, rrows = 0;
-    for (int i = 0; i < n; i++) {
-        const uint64_t nr = (uint64_t)Rs[i].n;
-        int b = ceil_log2(ceil_div(nr, (uint64_t)cap / 2));
-        if (b > 10) b = 10;
-        bits[i] = bits[n + i] = b;
-        segs[i] = SegCols<K>{Rs[i].key, Rs[i].pay, (uint64_t)Rs[i].n, 0};
-        segs[n + i] = SegCols<K>{Ss[i].key, Ss[i].pay, (uint64_t)Ss[i].n, 0};
-        rows += (uint64_t)Rs[i].n + (uint64_t)Ss[i].n;
-        rrows += (uint64_t)Rs[i].n;
-    }
-    for (int sgi = 0; sgi < 2 * n; sgi++)
-        for (uint64_t b = 0; b < segs[sgi].n; b += SC_TILE)
-            tiles.push_back(TileRef{b, sgi, (int)min((uint64_t)SC_TILE, segs[sgi].n - b)});
-    const uint64_t ntiles = tiles.size();
-    const uint64_t P = (uint64_t)n * SC_FMAX;                 // partitions of all joins
-    const uint64_t item_bound = P + rrows / (uint64_t)cap + 1;  // items <= P + sum nr / cap
-    Scratch s(c);
-    SegCols<K>* d_segs;
-    int* d_bits;
-    TileRef* d_tiles;
-    uint64_t* d_ntiles;
-    unsigned long long *hist, *cur;
-    uint64_t *start, *items, *iprefix, *ioff, *d_small, *d_off;
-    RW* prow;
-    Item* idesc;
-    unsigned long long *ival, *chk;
-    JN_TRY(s.get(&d_segs, 2 * (size_t)n));
-    JN_TRY(s.get(&d_bits, 2 * (size_t)n));
-    JN_TRY(s.get(&d_tiles, ntiles + 1));
-    JN_TRY(s.get(&d_ntiles, 1));
-    JN_TRY(s.get(&hist, 2 * P));
-    JN_TRY(s.get(&start, 2 * P + 1));
-    JN_TRY(s.get(&cur, 2 * P));
-    JN_TRY(s.get(&prow, rows + HJ_PAD));
-    JN_TRY(s.get(&items, P));
-    JN_TRY(s.get(&iprefix, P + 1));
-    JN_TRY(s.get(&idesc, item_bound));
-    JN_TRY(s.get(&ival, item_bound));
-    JN_TRY(s.get(&ioff, item_bound + 1));
-    JN_TRY(s.get(&chk, 1));
-    JN_TRY(s.get(&d_small, 2));
-    JN_TRY(s.get(&d_off, (size_t)n + 1));
-    JN_CUDA(c, cudaMemcpyAsync(d_segs, segs.data(), sizeof(SegCols<K>) * segs.size(), cudaMemcpyHostToDevice,
-                               c->stream));
-    JN_CUDA(c, cudaMemcpyAsync(d_bits, bits.data(), sizeof(int) * bits.size(), cudaMemcpyHostToDevice, c->stream));
-    if (ntiles)
-        JN_CUDA(c, cudaMemcpyAsync(d_tiles, tiles.data(), sizeof(TileRef) * ntiles, cudaMemcpyHostToDevice,
-                                   c->stream));
-    JN_CUDA(c, cudaMemcpyAsync(d_ntiles, &ntiles, sizeof(uint64_t), cudaMemcpyHostToDevice, c->stream));
-    JN_CUDA(c, cudaStreamSynchronize(c->stream));  // host vectors go out of scope below
+    std::unique_ptr<Scratch> s;
+    int n = 0;
+    uint64_t P = 0, item_bound = 0;
+    RW* prow = nullptr;
+    Item* idesc = nullptr;
+    uint64_t *iprefix = nullptr, *ioff = nullptr;
 
-    const bool graphs = c->tune.graphs != 0 && !c->profiling;
-    cudaGraph_t g1 = nullptr, g2 = nullptr;
-    cudaGraphExec_t x1 = nullptr, x2 = nullptr;
-    // Phases are captured on a private stream (the caller's stream may be the
-    // legacy default stream, which cannot be captured) and replayed on the
-    // caller's stream, after everything it already holds.
-    cudaStream_t user = c->stream;
-    if (graphs && !c->capture_stream)
-        JN_CUDA(c, cudaStreamCreateWithFlags(&c->capture_stream, cudaStreamNonBlocking));
-    auto begin_capture = [&]() -> jn_status {
-        if (!graphs) return JN_OK;
-        c->stream = c->capture_stream;
-        cudaError_t e = cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeThreadLocal);
-        if (e != cudaSuccess) c->stream = user;
-        JN_CUDA(c, e);
-        return JN_OK;
-    };
-    auto end_replay = [&](cudaGraph_t* g, cudaGraphExec_t* x) -> jn_status {
-        if (!graphs) return JN_OK;
-        cudaError_t e = cudaStreamEndCapture(c->stream, g);
-        c->stream = user;
-        JN_CUDA(c, e);
-        JN_CUDA(c, cudaGraphInstantiate(x, *g, 0));
-        JN_CUDA(c, cudaGraphLaunch(*x, c->stream));
-        return JN_OK;
-    };
-    auto abort_capture = [&]() {
-        if (!graphs || c->stream == user) return;
-        cudaGraph_t junk = nullptr;
-        cudaStreamEndCapture(c->stream, &junk);
-        if (junk) cudaGraphDestroy(junk);
-        c->stream = user;
-        cudaGetLastError();
-    };
-    struct GraphGuard {
-        cudaGraph_t* g[2];
-        cudaGraphExec_t* x[2];
-        ~GraphGuard() {
-            for (int i = 0; i < 2; i++) {
-                if (*x[i]) cudaGraphExecDestroy(*x[i]);
-                if (*g[i]) cudaGraphDestroy(*g[i]);
-            }
+    jn_status prepare(jn_ctx* c, const Cols<K>* Rs, const Cols<K>* Ss) {
+        const int cap = cap_of<K>();
+        s.reset(new Scratch(c));
+        // ---- host plan: per-join fan-out, segment table and tile list ----
+        std::vector<SegCols<K>> segs(2 * (size_t)n);
+        std::vector<int> bits(2 * (size_t)n);
+        std::vector<TileRef> tiles;
+        uint64_t rows = 0, rrows = 0;
+        for (int i = 0; i < n; i++) {
+            int b = ceil_log2(ceil_div((uint64_t)Rs[i].n, (uint64_t)cap / 2));
+            if (b > 10) b = 10;
+            bits[i] = bits[n + i] = b;
+            segs[i] = SegCols<K>{Rs[i].key, nullptr, Rs[i].pay, (uint64_t)Rs[i].n};
+            segs[n + i] = SegCols<K>{Ss[i].key, nullptr, Ss[i].pay, (uint64_t)Ss[i].n};
+            rows += (uint64_t)Rs[i].n + (uint64_t)Ss[i].n;
+            rrows += (uint64_t)Rs[i].n;
         }
-    } guard{{&g1, &g2}, {&x1, &x2}};
+        for (int sgi = 0; sgi < 2 * n; sgi++)
+            for (uint64_t b = 0; b < segs[sgi].n; b += SC_TILE)
+                tiles.push_back(TileRef{b, sgi, (int)min((uint64_t)SC_TILE, segs[sgi].n - b)});
+        const uint64_t ntiles = tiles.size();
+        P = (uint64_t)n * SC_FMAX;
+        item_bound = P + rrows / (uint64_t)cap + 1;  // items <= P + sum nr / cap
+        SegCols<K>* d_segs;
+        int* d_bits;
+        TileRef* d_tiles;
+        uint64_t *d_ntiles, *start, *items, *d_off;
+        unsigned long long *hist, *cur, *ival, *chk;
+        JN_TRY(s->get(&d_segs, 2 * (size_t)n));
+        JN_TRY(s->get(&d_bits, 2 * (size_t)n));
+        JN_TRY(s->get(&d_tiles, ntiles + 1));
+        JN_TRY(s->get(&d_ntiles, 1));
+        JN_TRY(s->get(&hist, 2 * P));
+        JN_TRY(s->get(&start, 2 * P + 1));
+        JN_TRY(s->get(&cur, 2 * P));
+        JN_TRY(s->get(&prow, rows + HJ_PAD));
+        JN_TRY(s->get(&items, P));
+        JN_TRY(s->get(&iprefix, P + 1));
+        JN_TRY(s->get(&idesc, item_bound));
+        JN_TRY(s->get(&ival, item_bound));
+        JN_TRY(s->get(&ioff, item_bound + 1));
+        JN_TRY(s->get(&chk, 1));
+        JN_TRY(s->get(&d_off, (size_t)n + 1));
+        JN_CUDA(c, cudaMemcpyAsync(d_segs, segs.data(), sizeof(SegCols<K>) * segs.size(), cudaMemcpyHostToDevice,
+                                   c->stream));
+        JN_CUDA(c, cudaMemcpyAsync(d_bits, bits.data(), sizeof(int) * bits.size(), cudaMemcpyHostToDevice,
+                                   c->stream));
+        if (ntiles)
+            JN_CUDA(c, cudaMemcpyAsync(d_tiles, tiles.data(), sizeof(TileRef) * ntiles, cudaMemcpyHostToDevice,
+                                       c->stream));
+        JN_CUDA(c, cudaMemcpyAsync(d_ntiles, &ntiles, sizeof(uint64_t), cudaMemcpyHostToDevice, c->stream));
+        JN_CUDA(c, cudaStreamSynchronize(c->stream));  // the host vectors go out of scope below
 
-    // ---- phase 1: histogram, scan, scatter, items, count, scan ----
-    JN_TRY(begin_capture());
-    jn_status st = JN_OK;
-    do {
-        SegHashDigit dg{d_bits, 0};
-        if ((st = zero(c, hist, sizeof(unsigned long long) * 2 * P)) != JN_OK) break;
-        if ((st = zero(c, chk, 8)) != JN_OK) break;
-        if ((st = zero(c, ival, sizeof(unsigned long long) * item_bound)) != JN_OK) break;
-        if ((st = launch(c, K_HIST, k_batch_hist<K>, dim3(4 * c->num_sms), dim3(SC_T), 0,
-                         (const SegCols<K>*)d_segs, (const TileRef*)d_tiles, (const uint64_t*)d_ntiles, dg,
-                         hist)) != JN_OK)
-            break;
-        if ((st = scan_u64(c, reinterpret_cast<const uint64_t*>(hist), start, (int64_t)(2 * P))) != JN_OK) break;
-        if ((st = launch(c, K_MISC, k_init_cursor, dim3((unsigned)ceil_div(2 * P, 256)), dim3(256), 0,
-                         (const uint64_t*)start, cur, (int64_t)(2 * P))) != JN_OK)
-            break;
-        auto ks = k_scatter<K, false, false, SegHashDigit>;
-        const size_t sm = scatter_smem<K, false>();
-        PartIn<K, false> in{nullptr, nullptr, nullptr, nullptr, 0, d_segs, d_tiles};
-        if ((st = launch(c, K_SCATTER, ks, dim3(persistent_grid(c, (const void*)ks, SC_T, sm)), dim3(SC_T), sm, in,
-                         (const uint64_t*)nullptr, (const uint64_t*)nullptr, (const uint64_t*)d_ntiles, 0, dg,
-                         SC_FMAX, (const uint32_t*)nullptr, 0u, cur, prow, c->d_err)) != JN_OK)
-            break;
-        const uint64_t* roff = start;
-        const uint64_t* soff = start + P;
-        if ((st = launch(c, K_ITEMS, k_items, dim3((unsigned)ceil_div(P, 256)), dim3(256), 0, roff, soff, (int)P,
-                         cap, items)) != JN_OK)
-            break;
-        if ((st = scan_u64(c, items, iprefix, (int64_t)P)) != JN_OK) break;
-        if ((st = launch(c, K_ITEMS, k_item_desc, dim3((unsigned)ceil_div(item_bound, 256)), dim3(256), 0, roff,
-                         soff, (const uint64_t*)iprefix, (int)P, cap, idesc)) != JN_OK)
-            break;
-        auto kc = k_hash_join<K, MODE_COUNT, false>;
-        const size_t smc = hash_smem<K>(MODE_COUNT);
-        if ((st = launch(c, K_HASH_COUNT, kc, dim3(persistent_grid(c, (const void*)kc, HJ_T, smc)), dim3(HJ_T), smc,
-                         (const RW*)prow, (const RW*)prow, (const Item*)idesc, (const uint64_t*)(iprefix + P),
-                         SC_FMAX == 1024 ? 10 : 10, ival, chk, (const uint64_t*)nullptr, (jn_pair*)nullptr,
-                         c->d_err)) != JN_OK)
-            break;
-        // items past the real count keep zero counts: scan the whole bound
-        if ((st = scan_u64(c, reinterpret_cast<const uint64_t*>(ival), ioff, (int64_t)item_bound)) != JN_OK) break;
-        if ((st = launch(c, K_MISC, k_batch_offsets, dim3((unsigned)ceil_div((uint64_t)n + 1, 256)), dim3(256), 0,
-                         (const uint64_t*)iprefix, (const uint64_t*)ioff, n, d_off)) != JN_OK)
-            break;
-    } while (0);
-    if (st != JN_OK) {
-        abort_capture();
-        return st;
-    }
-    JN_TRY(end_replay(&g1, &x1));
-    std::vector<uint64_t> hoff((size_t)n + 1);
-    JN_CUDA(c, cudaMemcpyAsync(hoff.data(), d_off, sizeof(uint64_t) * (n + 1), cudaMemcpyDeviceToHost, c->stream));
-    uint64_t dummy;
-    JN_TRY(read_back(c, d_small, &dummy, 0));
-    const uint64_t total = hoff[n];
-    for (int i = 0; i <= n; i++) offsets[i] = hoff[i];
-    // ---- phase 2: one exact allocation (with room for `extra` more pairs), then the emit pass ----
-    JN_TRY(out_prepare(c, s, total + extra, *plan));
-    if (total > 0) {
-        JN_TRY(begin_capture());
-        auto ke = k_hash_join<K, MODE_EMIT>;
-        const size_t sme = hash_smem<K>(MODE_EMIT);
-        st = launch(c, K_HASH_EMIT, ke, dim3(persistent_grid(c, (const void*)ke, HJ_T, sme)), dim3(HJ_T), sme,
-                    (const RW*)prow, (const RW*)prow, (const Item*)idesc, (const uint64_t*)(iprefix + P), 10,
-                    (unsigned long long*)nullptr, (unsigned long long*)nullptr, (const uint64_t*)ioff, plan->dev,
-                    c->d_err);
+        GraphPhase gp(c, c->tune.graphs != 0 && !c->profiling);
+        JN_TRY(gp.begin());
+        jn_status st = JN_OK;
+        do {
+            SegHashDigit dg{d_bits, 0};
+            if ((st = zero(c, hist, sizeof(unsigned long long) * 2 * P)) != JN_OK) break;
+            if ((st = zero(c, chk, 8)) != JN_OK) break;
+            if ((st = zero(c, ival, sizeof(unsigned long long) * item_bound)) != JN_OK) break;
+            if ((st = launch(c, K_HIST, k_batch_hist<K>, dim3(4 * c->num_sms), dim3(SC_T), 0,
+                             (const SegCols<K>*)d_segs, (const TileRef*)d_tiles, (const uint64_t*)d_ntiles, dg,
+                             hist)) != JN_OK)
+                break;
+            if ((st = scan_u64(c, reinterpret_cast<const uint64_t*>(hist), start, (int64_t)(2 * P))) != JN_OK) break;
+            if ((st = launch(c, K_MISC, k_init_cursor, dim3((unsigned)ceil_div(2 * P, 256)), dim3(256), 0,
+                             (const uint64_t*)start, cur, (int64_t)(2 * P))) != JN_OK)
+                break;
+            auto ks = k_scatter<K, false, false, SegHashDigit>;
+            const size_t sm = scatter_smem<K, false>();
+            PartIn<K, false> in{nullptr, nullptr, nullptr, nullptr, 0, d_segs, d_tiles};
+            if ((st = launch(c, K_SCATTER, ks, dim3(persistent_grid(c, (const void*)ks, SC_T, sm)), dim3(SC_T), sm,
+                             in, (const uint64_t*)nullptr, (const uint64_t*)nullptr, (const uint64_t*)d_ntiles, 0,
+                             dg, SC_FMAX, (const uint32_t*)nullptr, 0u, cur, prow, c->d_err)) != JN_OK)
+                break;
+            const uint64_t* roff = start;
+            const uint64_t* soff = start + P;
+            if ((st = launch(c, K_ITEMS, k_items, dim3((unsigned)ceil_div(P, 256)), dim3(256), 0, roff, soff, (int)P,
+                             cap, items)) != JN_OK)
+                break;
+            if ((st = scan_u64(c, items, iprefix, (int64_t)P)) != JN_OK) break;
+            if ((st = launch(c, K_ITEMS, k_item_desc, dim3((unsigned)ceil_div(item_bound, 256)), dim3(256), 0, roff,
+                             soff, (const uint64_t*)iprefix, (int)P, cap, idesc)) != JN_OK)
+                break;
+            auto kc = k_hash_join<K, MODE_COUNT, false>;
+            const size_t smc = hash_smem<K>(MODE_COUNT);
+            if ((st = launch(c, K_HASH_COUNT, kc, dim3(persistent_grid(c, (const void*)kc, HJ_T, smc)), dim3(HJ_T),
+                             smc, (const RW*)prow, (const RW*)prow, (const Item*)idesc,
+                             (const uint64_t*)(iprefix + P), 10, ival, chk, (const uint64_t*)nullptr,
+                             (jn_pair*)nullptr, c->d_err)) != JN_OK)
+                break;
+            // items past the real count keep zero counts: scan the whole bound
+            if ((st = scan_u64(c, reinterpret_cast<const uint64_t*>(ival), ioff, (int64_t)item_bound)) != JN_OK) break;
+            if ((st = launch(c, K_MISC, k_batch_offsets, dim3((unsigned)ceil_div((uint64_t)n + 1, 256)), dim3(256), 0,
+                             (const uint64_t*)iprefix, (const uint64_t*)ioff, n, d_off)) != JN_OK)
+                break;
+        } while (0);
         if (st != JN_OK) {
-            abort_capture();
+            gp.abort();
             return st;
         }
-        JN_TRY(end_replay(&g2, &x2));
+        JN_TRY(gp.end_and_run());
+        offsets.assign((size_t)n + 1, 0);
+        JN_CUDA(c, cudaMemcpyAsync(offsets.data(), d_off, sizeof(uint64_t) * (n + 1), cudaMemcpyDeviceToHost,
+                                   c->stream));
+        uint64_t dummy;
+        JN_TRY(read_back(c, d_off, &dummy, 0));
+        total = offsets[n];
+        return JN_OK;
     }
-    if (plan->host_copy)
-        return fail(c, JN_ERR_INVALID, "batch outputs must be device memory");
-    JN_TRY(out_finish(c, total + extra, *plan));
-    JN_TRY(read_back(c, d_small, &dummy, 0));
-    c->info.result = total;
-    c->info.partitions = P;
-    c->info.work_items = item_bound;
+
+    jn_status emit(jn_ctx* c, jn_pair* out) override {
+        if (total == 0) return JN_OK;
+        GraphPhase gp(c, c->tune.graphs != 0 && !c->profiling);
+        JN_TRY(gp.begin());
+        auto ke = k_hash_join<K, MODE_EMIT>;
+        const size_t sme = hash_smem<K>(MODE_EMIT);
+        jn_status st = launch(c, K_HASH_EMIT, ke, dim3(persistent_grid(c, (const void*)ke, HJ_T, sme)), dim3(HJ_T),
+                              sme, (const RW*)prow, (const RW*)prow, (const Item*)idesc, (const uint64_t*)(iprefix + P),
+                              10, (unsigned long long*)nullptr, (unsigned long long*)nullptr, (const uint64_t*)ioff,
+                              out, c->d_err);
+        if (st != JN_OK) {
+            gp.abort();
+            return st;
+        }
+        JN_TRY(gp.end_and_run());
+        return JN_OK;
+    }
+};
+
+template <typename K>
+jn_status batch_hash_prepare(jn_ctx* c, int n, const Cols<K>* Rs, const Cols<K>* Ss, std::unique_ptr<BatchRun>* run) {
+    std::unique_ptr<HashBatchRun<K>> r(new HashBatchRun<K>());
+    r->n = n;
+    JN_TRY(r->prepare(c, Rs, Ss));
+    c->info.partitions += r->P;
+    c->info.work_items += r->item_bound;
+    run->reset(r.release());
     return JN_OK;
 }
 
-template jn_status run_batch_hash<int32_t>(jn_ctx*, int, const Cols<int32_t>*, const Cols<int32_t>*, OutPlan*,
-                                           uint64_t*, uint64_t);
-template jn_status run_batch_hash<int64_t>(jn_ctx*, int, const Cols<int64_t>*, const Cols<int64_t>*, OutPlan*,
-                                           uint64_t*, uint64_t);
+template jn_status batch_hash_prepare<int32_t>(jn_ctx*, int, const Cols<int32_t>*, const Cols<int32_t>*,
+                                               std::unique_ptr<BatchRun>*);
+template jn_status batch_hash_prepare<int64_t>(jn_ctx*, int, const Cols<int64_t>*, const Cols<int64_t>*,
+                                               std::unique_ptr<BatchRun>*);
 
 template jn_status run_hash<int32_t>(jn_ctx*, const Cols<int32_t>&, const Cols<int32_t>&, int,
                                      OutPlan*, RunResult*);

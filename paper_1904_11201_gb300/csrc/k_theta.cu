@@ -95,17 +95,39 @@ __device__ __forceinline__ int band_groups(const RangeParams& p, long long band,
     return d > (uint64_t)G ? G : (int)d;
 }
 
-// items[y] = R chunks of y's window x S chunks of group y.
-__global__ void k_theta_items(const uint64_t* __restrict__ roff, const uint64_t* __restrict__ soff,
-                              const RangeParams* __restrict__ prm, int G, long long band,
-                              uint64_t* __restrict__ items) {
-    int y = blockIdx.x * blockDim.x + threadIdx.x;
-    if (y >= G) return;
-    const int dg = band_groups(*prm, band, G);
-    const int x0 = max(0, y - dg), x1 = min(G - 1, y + dg);
+// Joins of one launch: join i owns partitions [i << lg, (i + 1) << lg) (its
+// groups y = p & (2^lg - 1), of which the first groups[i] are in use) and has
+// its own range parameters, band and op.  A single join is the case of one.
+struct ThetaSet {
+    const RangeParams* prm;
+    const long long* band;
+    const int* op;
+    const int* groups;
+    int lg;
+};
+
+__global__ void k_set_theta_one(long long* band, int* op, int* groups, long long b, int o, int g) {
+    *band = b;
+    *op = o;
+    *groups = g;
+}
+
+// items[p] = R chunks of the window of group y of its join x S chunks of y.
+__global__ void k_theta_items(const uint64_t* __restrict__ roff, const uint64_t* __restrict__ soff, ThetaSet ts,
+                              int P, uint64_t* __restrict__ items) {
+    const int p = blockIdx.x * blockDim.x + threadIdx.x;
+    if (p >= P) return;
+    const int inst = p >> ts.lg, y = p & ((1 << ts.lg) - 1), G = ts.groups[inst];
+    if (y >= G) {
+        items[p] = 0;
+        return;
+    }
+    const int dg = band_groups(ts.prm[inst], ts.band[inst], G);
+    const int base = inst << ts.lg;
+    const int x0 = base + max(0, y - dg), x1 = base + min(G - 1, y + dg);
     const uint64_t nrw = roff[x1 + 1] - roff[x0];
-    const uint64_t ns = soff[y + 1] - soff[y];
-    items[y] = (nrw && ns) ? ((nrw + TH_RCAP - 1) / TH_RCAP) * ((ns + TH_SCH - 1) / TH_SCH) : 0;
+    const uint64_t ns = soff[p + 1] - soff[p];
+    items[p] = (nrw && ns) ? ((nrw + TH_RCAP - 1) / TH_RCAP) * ((ns + TH_SCH - 1) / TH_SCH) : 0;
 }
 
 // BAND: window + fine buckets; !BAND: diagonal group, every pair compared.
@@ -120,10 +142,10 @@ __device__ __forceinline__ K col_a(const Row<K, BAND>& x) {
 template <typename K, int MODE, bool BAND>
 __global__ void __launch_bounds__(TH_T)
 k_theta_join(const Row<K, BAND>* __restrict__ rrows, const uint64_t* __restrict__ roff,
-             const Row<K, BAND>* __restrict__ srows, const uint64_t* __restrict__ soff,
-             const RangeParams* __restrict__ prm, const uint64_t* __restrict__ item_prefix, int G, int op,
-             long long band, unsigned long long* __restrict__ item_val, unsigned long long* __restrict__ chk,
-             const uint64_t* __restrict__ item_off, jn_pair* __restrict__ out, unsigned int* __restrict__ work) {
+             const Row<K, BAND>* __restrict__ srows, const uint64_t* __restrict__ soff, ThetaSet ts, int Ptot,
+             const uint64_t* __restrict__ item_prefix, unsigned long long* __restrict__ item_val,
+             unsigned long long* __restrict__ chk, const uint64_t* __restrict__ item_off, jn_pair* __restrict__ out,
+             unsigned int* __restrict__ work) {
     extern __shared__ __align__(16) unsigned char smem[];
     K* s_k = reinterpret_cast<K*>(smem);
     K* s_a = s_k + TH_RCAP;
@@ -134,10 +156,8 @@ k_theta_join(const Row<K, BAND>* __restrict__ rrows, const uint64_t* __restrict_
     __shared__ unsigned int s_item;
     __shared__ uint32_t s_cursor, s_rows;
 
-    const RangeParams P = *prm;
-    const uint64_t nitems = item_prefix[G];
+    const uint64_t nitems = item_prefix[Ptot];
     const int lane = threadIdx.x & 31;
-    const int dg = BAND ? band_groups(P, band, G) : 0;
     while (true) {
         if (threadIdx.x == 0) {
             s_item = atomicAdd(work, 1u);
@@ -147,16 +167,22 @@ k_theta_join(const Row<K, BAND>* __restrict__ rrows, const uint64_t* __restrict_
         __syncthreads();
         const uint64_t it = s_item;
         if (it >= nitems) break;
-        const int y = find_segment(item_prefix, G, it);
-        const int x0 = max(0, y - dg), x1 = min(G - 1, y + dg);
+        const int p = find_segment(item_prefix, Ptot, it);
+        const int inst = p >> ts.lg, y = p & ((1 << ts.lg) - 1), G = ts.groups[inst];
+        const RangeParams P = ts.prm[inst];
+        const long long band = ts.band[inst];
+        const int op = ts.op[inst];
+        const int dg = BAND ? band_groups(P, band, G) : 0;
+        const int gbase = inst << ts.lg;
+        const int x0 = gbase + max(0, y - dg), x1 = gbase + min(G - 1, y + dg);
         const uint64_t wbeg = roff[x0], nrw = roff[x1 + 1] - wbeg;
-        const uint64_t ns = soff[y + 1] - soff[y];
+        const uint64_t ns = soff[p + 1] - soff[p];
         const uint64_t nrc = (nrw + TH_RCAP - 1) / TH_RCAP;
-        const uint64_t local = it - item_prefix[y];
+        const uint64_t local = it - item_prefix[p];
         const uint64_t rc = local % nrc, sc = local / nrc;
         const uint64_t rbeg = wbeg + rc * TH_RCAP;
         const int rn = (int)min((uint64_t)TH_RCAP, nrw - rc * TH_RCAP);
-        const uint64_t sbeg = soff[y] + sc * TH_SCH;
+        const uint64_t sbeg = soff[p] + sc * TH_SCH;
         const int sn = (int)min((uint64_t)TH_SCH, ns - sc * TH_SCH);
 
         uint64_t wlo = 0, whi = 0;
@@ -445,11 +471,19 @@ static jn_status run_theta_t(jn_ctx* c, const Cols<K>& R, const Cols<K>& S, int 
     JN_TRY((range_partition<K, B>(c, s, R, rg, B ? R.key : nullptr, prm, G, work, &rrows, &roff)));
     JN_TRY((range_partition<K, B>(c, s, S, sg, B ? S.key : nullptr, prm, G, work, &srows, &soff)));
     // ---- compared regions (band window or diagonal) ----
+    long long* d_band;
+    int *d_op, *d_groups;
+    JN_TRY(s.get(&d_band, 1));
+    JN_TRY(s.get(&d_op, 2));
+    d_groups = d_op + 1;
+    JN_TRY(launch(c, K_MISC, k_set_theta_one, dim3(1), dim3(1), 0, d_band, d_op, d_groups,
+                  (long long)(B ? band : -1), op, G));
+    const ThetaSet ts{prm, d_band, d_op, d_groups, g};
     uint64_t *items, *ipre;
     JN_TRY(s.get(&items, G));
     JN_TRY(s.get(&ipre, G + 1));
     JN_TRY(launch(c, K_ITEMS, k_theta_items, dim3((G + 255) / 256), dim3(256), 0, (const uint64_t*)roff,
-                  (const uint64_t*)soff, (const RangeParams*)prm, G, (long long)(B ? band : -1), items));
+                  (const uint64_t*)soff, ts, G, items));
     JN_TRY(scan_u64(c, items, ipre, G));
     // ---- cross regions (one-column predicate only) ----
     uint64_t *cross = nullptr, *coff = nullptr, *chunks = nullptr, *cpre = nullptr;
@@ -490,9 +524,8 @@ static jn_status run_theta_t(jn_ctx* c, const Cols<K>& R, const Cols<K>& S, int 
         auto kc = pick(cm);
         JN_TRY(zero(c, work, 4));
         JN_TRY(launch(c, K_THETA_COUNT, kc, dim3(grid_of((const void*)kc)), dim3(TH_T), smj, (const RW*)rrows,
-                      (const uint64_t*)roff, (const RW*)srows, (const uint64_t*)soff, (const RangeParams*)prm,
-                      (const uint64_t*)ipre, G, op, (long long)(B ? band : -1), ival, chk,
-                      (const uint64_t*)nullptr, (jn_pair*)nullptr, work));
+                      (const uint64_t*)roff, (const RW*)srows, (const uint64_t*)soff, ts, G, (const uint64_t*)ipre,
+                      ival, chk, (const uint64_t*)nullptr, (jn_pair*)nullptr, work));
     }
     JN_TRY(scan_u64(c, reinterpret_cast<const uint64_t*>(ival), ioff, (int64_t)nitems));
     if (has_cross && mode == MODE_AGG) {
@@ -526,9 +559,9 @@ static jn_status run_theta_t(jn_ctx* c, const Cols<K>& R, const Cols<K>& S, int 
         auto ke = pick(MODE_EMIT);
         JN_TRY(zero(c, work, 4));
         JN_TRY(launch(c, K_THETA_EMIT, ke, dim3(grid_of((const void*)ke)), dim3(TH_T), smj, (const RW*)rrows,
-                      (const uint64_t*)roff, (const RW*)srows, (const uint64_t*)soff, (const RangeParams*)prm,
-                      (const uint64_t*)ipre, G, op, (long long)(B ? band : -1), (unsigned long long*)nullptr,
-                      (unsigned long long*)nullptr, (const uint64_t*)ioff, plan->dev, work));
+                      (const uint64_t*)roff, (const RW*)srows, (const uint64_t*)soff, ts, G, (const uint64_t*)ipre,
+                      (unsigned long long*)nullptr, (unsigned long long*)nullptr, (const uint64_t*)ioff, plan->dev,
+                      work));
     }
     if (crossn) {
         JN_TRY(zero(c, work, 4));
@@ -555,6 +588,333 @@ jn_status run_theta(jn_ctx* c, const Cols<K>& R, const Cols<K>& S, int op, int64
     if (band >= 0) return run_theta_t<K, true>(c, R, S, op, band, mode, plan, res);
     return run_theta_t<K, false>(c, R, S, op, band, mode, plan, res);
 }
+
+// ------------------------------------------------------------- batches --
+// Digit of a batch's range pass: segment s belongs to join s % m, whose
+// range parameters give the group.
+struct SegRangeDigit {
+    static constexpr int kFilterWords = 0;
+    const RangeParams* prm;
+    int m;
+    long long lo;
+    int shift;
+    __device__ __forceinline__ void bind(uint32_t*) {}
+    __device__ __forceinline__ void set_seg(int s) {
+        const RangeParams& p = prm[s % m];
+        lo = p.lo;
+        shift = p.shift;
+    }
+    __device__ __forceinline__ bool is_special(uint32_t) const { return false; }
+    template <typename K>
+    __device__ __forceinline__ uint32_t operator()(K k) const {
+        return (uint32_t)(((uint64_t)((int64_t)k - lo)) >> shift);
+    }
+};
+
+__global__ void k_bmm_init(long long* mm, int m) {
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < m; i += gridDim.x * blockDim.x) {
+        mm[2 * i] = LLONG_MAX;
+        mm[2 * i + 1] = LLONG_MIN;
+    }
+}
+
+// Per-join minimum and maximum of the grouped column over both tables.
+template <typename K>
+__global__ void k_batch_minmax(const SegCols<K>* __restrict__ segs, const TileRef* __restrict__ tiles,
+                               const uint64_t* __restrict__ ntiles_p, int m, long long* __restrict__ mm) {
+    const uint64_t ntiles = *ntiles_p;
+    for (uint64_t t = blockIdx.x; t < ntiles; t += gridDim.x) {
+        const TileRef x = tiles[t];
+        const K* k = segs[x.seg].key;
+        long long lo = LLONG_MAX, hi = LLONG_MIN;
+        for (int i = threadIdx.x; i < x.cnt; i += blockDim.x) {
+            const long long v = (long long)k[x.beg + i];
+            lo = v < lo ? v : lo;
+            hi = v > hi ? v : hi;
+        }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            const long long a = __shfl_xor_sync(0xffffffffu, lo, o);
+            const long long b = __shfl_xor_sync(0xffffffffu, hi, o);
+            lo = a < lo ? a : lo;
+            hi = b > hi ? b : hi;
+        }
+        if ((threadIdx.x & 31) == 0 && lo <= hi) {
+            atomicMin(&mm[2 * (x.seg % m)], lo);
+            atomicMax(&mm[2 * (x.seg % m) + 1], hi);
+        }
+    }
+}
+
+__global__ void k_batch_range_setup(const long long* __restrict__ mm, const int* __restrict__ groups, int m,
+                                    RangeParams* __restrict__ p) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= m) return;
+    long long lo = mm[2 * i], hi = mm[2 * i + 1];
+    if (lo > hi) { lo = 0; hi = 0; }
+    const uint64_t span = (uint64_t)hi - (uint64_t)lo;
+    int s = 0;
+    while (s < 63 && (span >> s) >= (uint64_t)groups[i]) s++;
+    p[i].lo = lo;
+    p[i].hi = hi;
+    p[i].shift = s;
+    p[i].groups = (int)(span >> s) + 1;
+    p[i].fshift = 0;
+    p[i].pad = 0;
+}
+
+template <typename K, typename Digit>
+__global__ void __launch_bounds__(SC_T)
+k_batch_hist_any(const SegCols<K>* __restrict__ segs, const TileRef* __restrict__ tiles,
+                 const uint64_t* __restrict__ ntiles_p, Digit dg, unsigned long long* __restrict__ hist) {
+    __shared__ uint32_t s_h[SC_FMAX];
+    const uint64_t ntiles = *ntiles_p;
+    for (uint64_t t = blockIdx.x; t < ntiles; t += gridDim.x) {
+        const TileRef x = tiles[t];
+        dg.set_seg(x.seg);
+        for (int i = threadIdx.x; i < SC_FMAX; i += blockDim.x) s_h[i] = 0;
+        __syncthreads();
+        const K* k = segs[x.seg].key;
+        for (int i = threadIdx.x; i < x.cnt; i += blockDim.x) atomicAdd(&s_h[dg(k[x.beg + i])], 1u);
+        __syncthreads();
+        for (int i = threadIdx.x; i < SC_FMAX; i += blockDim.x)
+            if (s_h[i]) atomicAdd(&hist[(uint64_t)x.seg * SC_FMAX + i], (unsigned long long)s_h[i]);
+        __syncthreads();
+    }
+}
+
+__global__ void k_band_offsets(const uint64_t* __restrict__ item_prefix, const uint64_t* __restrict__ ioff,
+                               int count, uint64_t* __restrict__ out_off) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i > count) return;
+    out_off[i] = ioff[item_prefix[(uint64_t)i * SC_FMAX]];
+}
+
+__global__ void k_set_words(long long* band, int* op, int* groups, const long long* hb, const int* hop,
+                            const int* hg, int m) {
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < m; i += gridDim.x * blockDim.x) {
+        band[i] = hb[i];
+        op[i] = hop[i];
+        groups[i] = hg[i];
+    }
+}
+
+// A batch of band joins run as one: join i's R table is segment i and its S
+// table segment m + i of one range pass on column k, join i owns partitions
+// [i * 1024, i * 1024 + groups_i), and the count and emit passes run over one
+// work queue of (join, group, R chunk, S chunk) items of all joins.
+template <typename K>
+struct BandBatchRun : BatchRun {
+    using RW = Row<K, true>;
+    std::unique_ptr<Scratch> s;
+    int m = 0;
+    uint64_t P = 0, nitems = 0;
+    RW* prow = nullptr;
+    uint64_t *start = nullptr, *ipre = nullptr, *ioff = nullptr;
+    ThetaSet ts{};
+    unsigned int* work = nullptr;
+    size_t smj = 0;
+
+    jn_status prepare(jn_ctx* c, const Cols<K>* Rs, const Cols<K>* Ss, const int* ops, const int64_t* bands) {
+        s.reset(new Scratch(c));
+        std::vector<SegCols<K>> segs(2 * (size_t)m);
+        std::vector<TileRef> tiles;
+        std::vector<int> groups(m), hop(m);
+        std::vector<long long> hb(m);
+        uint64_t rows = 0;
+        for (int i = 0; i < m; i++) {
+            int g = ceil_log2(ceil_div((uint64_t)max(Rs[i].n, (int64_t)1), 1024));
+            if (g < 2) g = 2;
+            if (g > 10) g = 10;
+            groups[i] = 1 << g;
+            hop[i] = ops[i];
+            hb[i] = bands[i];
+            segs[i] = SegCols<K>{Rs[i].key2, Rs[i].key, Rs[i].pay, (uint64_t)Rs[i].n};
+            segs[m + i] = SegCols<K>{Ss[i].key2, Ss[i].key, Ss[i].pay, (uint64_t)Ss[i].n};
+            rows += (uint64_t)Rs[i].n + (uint64_t)Ss[i].n;
+        }
+        for (int sgi = 0; sgi < 2 * m; sgi++)
+            for (uint64_t b = 0; b < segs[sgi].n; b += SC_TILE)
+                tiles.push_back(TileRef{b, sgi, (int)min((uint64_t)SC_TILE, segs[sgi].n - b)});
+        const uint64_t ntiles = tiles.size();
+        P = (uint64_t)m * SC_FMAX;
+        SegCols<K>* d_segs;
+        TileRef* d_tiles;
+        uint64_t *d_ntiles, *items;
+        long long *mm, *d_band, *h_band;
+        int *d_op, *d_groups, *h_op, *h_groups;
+        RangeParams* prm;
+        unsigned long long *hist, *cur;
+        JN_TRY(s->get(&d_segs, 2 * (size_t)m));
+        JN_TRY(s->get(&d_tiles, ntiles + 1));
+        JN_TRY(s->get(&d_ntiles, 1));
+        JN_TRY(s->get(&mm, 2 * (size_t)m));
+        JN_TRY(s->get(&prm, (size_t)m));
+        JN_TRY(s->get(&d_band, (size_t)m));
+        JN_TRY(s->get(&h_band, (size_t)m));
+        JN_TRY(s->get(&d_op, (size_t)m));
+        JN_TRY(s->get(&h_op, (size_t)m));
+        JN_TRY(s->get(&d_groups, (size_t)m));
+        JN_TRY(s->get(&h_groups, (size_t)m));
+        JN_TRY(s->get(&hist, 2 * P));
+        JN_TRY(s->get(&start, 2 * P + 1));
+        JN_TRY(s->get(&cur, 2 * P));
+        JN_TRY(s->get(&prow, rows + 16));
+        JN_TRY(s->get(&items, P));
+        JN_TRY(s->get(&ipre, P + 1));
+        JN_TRY(s->get(&work, 4));
+        JN_CUDA(c, cudaMemcpyAsync(d_segs, segs.data(), sizeof(SegCols<K>) * segs.size(), cudaMemcpyHostToDevice,
+                                   c->stream));
+        if (ntiles)
+            JN_CUDA(c, cudaMemcpyAsync(d_tiles, tiles.data(), sizeof(TileRef) * ntiles, cudaMemcpyHostToDevice,
+                                       c->stream));
+        JN_CUDA(c, cudaMemcpyAsync(d_ntiles, &ntiles, sizeof(uint64_t), cudaMemcpyHostToDevice, c->stream));
+        JN_CUDA(c, cudaMemcpyAsync(h_band, hb.data(), sizeof(long long) * m, cudaMemcpyHostToDevice, c->stream));
+        JN_CUDA(c, cudaMemcpyAsync(h_op, hop.data(), sizeof(int) * m, cudaMemcpyHostToDevice, c->stream));
+        JN_CUDA(c, cudaMemcpyAsync(h_groups, groups.data(), sizeof(int) * m, cudaMemcpyHostToDevice, c->stream));
+        JN_CUDA(c, cudaStreamSynchronize(c->stream));  // the host vectors go out of scope below
+        ts = ThetaSet{prm, d_band, d_op, d_groups, 10};
+        smj = (size_t)TH_RCAP * (2 * sizeof(K) + 4) + sizeof(uint32_t) * TH_NFB;
+
+        // ---- phase 1a: ranges, range partition and work items ----
+        {
+            GraphPhase gp(c, c->tune.graphs != 0 && !c->profiling);
+            JN_TRY(gp.begin());
+            jn_status st = JN_OK;
+            do {
+                const unsigned gm = (unsigned)ceil_div((uint64_t)m, 256);
+                if ((st = launch(c, K_MISC, k_set_words, dim3(gm), dim3(256), 0, d_band, d_op, d_groups,
+                                 (const long long*)h_band, (const int*)h_op, (const int*)h_groups, m)) != JN_OK)
+                    break;
+                if ((st = launch(c, K_MINMAX, k_bmm_init, dim3(gm), dim3(256), 0, mm, m)) != JN_OK) break;
+                if ((st = launch(c, K_MINMAX, k_batch_minmax<K>, dim3(4 * c->num_sms), dim3(256), 0,
+                                 (const SegCols<K>*)d_segs, (const TileRef*)d_tiles, (const uint64_t*)d_ntiles, m,
+                                 mm)) != JN_OK)
+                    break;
+                if ((st = launch(c, K_MINMAX, k_batch_range_setup, dim3(gm), dim3(256), 0, (const long long*)mm,
+                                 (const int*)d_groups, m, prm)) != JN_OK)
+                    break;
+                SegRangeDigit dg{prm, m, 0, 0};
+                if ((st = zero(c, hist, sizeof(unsigned long long) * 2 * P)) != JN_OK) break;
+                if ((st = launch(c, K_HIST, k_batch_hist_any<K, SegRangeDigit>, dim3(4 * c->num_sms), dim3(SC_T), 0,
+                                 (const SegCols<K>*)d_segs, (const TileRef*)d_tiles, (const uint64_t*)d_ntiles, dg,
+                                 hist)) != JN_OK)
+                    break;
+                if ((st = scan_u64(c, reinterpret_cast<const uint64_t*>(hist), start, (int64_t)(2 * P))) != JN_OK)
+                    break;
+                if ((st = launch(c, K_MISC, k_init_cursor, dim3((unsigned)ceil_div(2 * P, 256)), dim3(256), 0,
+                                 (const uint64_t*)start, cur, (int64_t)(2 * P))) != JN_OK)
+                    break;
+                auto ks = k_scatter<K, true, false, SegRangeDigit>;
+                const size_t sm = scatter_smem<K, true>();
+                ensure_smem((const void*)ks, sm);
+                int per = 0;
+                cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, ks, SC_T, sm);
+                PartIn<K, true> in{nullptr, nullptr, nullptr, nullptr, 0, d_segs, d_tiles};
+                if ((st = launch(c, K_SCATTER, ks, dim3(max(per, 1) * c->num_sms), dim3(SC_T), sm, in,
+                                 (const uint64_t*)nullptr, (const uint64_t*)nullptr, (const uint64_t*)d_ntiles, 0, dg,
+                                 SC_FMAX, (const uint32_t*)nullptr, 0u, cur, prow, c->d_err)) != JN_OK)
+                    break;
+                if ((st = launch(c, K_ITEMS, k_theta_items, dim3((unsigned)ceil_div(P, 256)), dim3(256), 0,
+                                 (const uint64_t*)start, (const uint64_t*)(start + P), ts, (int)P, items)) != JN_OK)
+                    break;
+                if ((st = scan_u64(c, items, ipre, (int64_t)P)) != JN_OK) break;
+            } while (0);
+            if (st != JN_OK) {
+                gp.abort();
+                return st;
+            }
+            JN_TRY(gp.end_and_run());
+        }
+        uint64_t* d_small;
+        JN_TRY(s->get(&d_small, 2));
+        JN_CUDA(c, cudaMemcpyAsync(d_small, ipre + P, 8, cudaMemcpyDeviceToDevice, c->stream));
+        JN_TRY(read_back(c, d_small, &nitems, 1));
+        // ---- phase 1b: count pass, scan, per-join offsets ----
+        unsigned long long *ival, *chk;
+        uint64_t* d_off;
+        JN_TRY(s->get(&ival, nitems + 1));
+        JN_TRY(s->get(&ioff, nitems + 1));
+        JN_TRY(s->get(&chk, 1));
+        JN_TRY(s->get(&d_off, (size_t)m + 1));
+        {
+            GraphPhase gp(c, c->tune.graphs != 0 && !c->profiling);
+            JN_TRY(gp.begin());
+            jn_status st = JN_OK;
+            do {
+                if ((st = zero(c, chk, 8)) != JN_OK) break;
+                if ((st = zero(c, work, 4)) != JN_OK) break;
+                if (nitems) {
+                    auto kc = k_theta_join<K, MODE_COUNT, true>;
+                    ensure_smem((const void*)kc, smj);
+                    int per = 0;
+                    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, kc, TH_T, smj);
+                    if ((st = launch(c, K_THETA_COUNT, kc, dim3(max(per, 1) * c->num_sms), dim3(TH_T), smj,
+                                     (const RW*)prow, (const uint64_t*)start, (const RW*)prow,
+                                     (const uint64_t*)(start + P), ts, (int)P, (const uint64_t*)ipre, ival, chk,
+                                     (const uint64_t*)nullptr, (jn_pair*)nullptr, work)) != JN_OK)
+                        break;
+                }
+                if ((st = scan_u64(c, reinterpret_cast<const uint64_t*>(ival), ioff, (int64_t)nitems)) != JN_OK) break;
+                if ((st = launch(c, K_MISC, k_band_offsets, dim3((unsigned)ceil_div((uint64_t)m + 1, 256)), dim3(256),
+                                 0, (const uint64_t*)ipre, (const uint64_t*)ioff, m, d_off)) != JN_OK)
+                    break;
+            } while (0);
+            if (st != JN_OK) {
+                gp.abort();
+                return st;
+            }
+            JN_TRY(gp.end_and_run());
+        }
+        offsets.assign((size_t)m + 1, 0);
+        JN_CUDA(c, cudaMemcpyAsync(offsets.data(), d_off, sizeof(uint64_t) * (m + 1), cudaMemcpyDeviceToHost,
+                                   c->stream));
+        uint64_t dummy;
+        JN_TRY(read_back(c, d_small, &dummy, 0));
+        total = offsets[m];
+        return JN_OK;
+    }
+
+    jn_status emit(jn_ctx* c, jn_pair* out) override {
+        if (total == 0) return JN_OK;
+        GraphPhase gp(c, c->tune.graphs != 0 && !c->profiling);
+        JN_TRY(gp.begin());
+        jn_status st = zero(c, work, 4);
+        if (st == JN_OK) {
+            auto ke = k_theta_join<K, MODE_EMIT, true>;
+            ensure_smem((const void*)ke, smj);
+            int per = 0;
+            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, ke, TH_T, smj);
+            st = launch(c, K_THETA_EMIT, ke, dim3(max(per, 1) * c->num_sms), dim3(TH_T), smj, (const RW*)prow,
+                        (const uint64_t*)start, (const RW*)prow, (const uint64_t*)(start + P), ts, (int)P,
+                        (const uint64_t*)ipre, (unsigned long long*)nullptr, (unsigned long long*)nullptr,
+                        (const uint64_t*)ioff, out, work);
+        }
+        if (st != JN_OK) {
+            gp.abort();
+            return st;
+        }
+        JN_TRY(gp.end_and_run());
+        return JN_OK;
+    }
+};
+
+template <typename K>
+jn_status batch_band_prepare(jn_ctx* c, int m, const Cols<K>* Rs, const Cols<K>* Ss, const int* ops,
+                             const int64_t* bands, std::unique_ptr<BatchRun>* run) {
+    std::unique_ptr<BandBatchRun<K>> r(new BandBatchRun<K>());
+    r->m = m;
+    JN_TRY(r->prepare(c, Rs, Ss, ops, bands));
+    c->info.partitions += r->P;
+    c->info.work_items += r->nitems;
+    run->reset(r.release());
+    return JN_OK;
+}
+
+template jn_status batch_band_prepare<int32_t>(jn_ctx*, int, const Cols<int32_t>*, const Cols<int32_t>*, const int*,
+                                               const int64_t*, std::unique_ptr<BatchRun>*);
+template jn_status batch_band_prepare<int64_t>(jn_ctx*, int, const Cols<int64_t>*, const Cols<int64_t>*, const int*,
+                                               const int64_t*, std::unique_ptr<BatchRun>*);
 
 template jn_status run_theta<int32_t>(jn_ctx*, const Cols<int32_t>&, const Cols<int32_t>&, int, int64_t,
                                       int, OutPlan*, RunResult*);
