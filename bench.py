@@ -249,6 +249,315 @@ def cpu_baseline(kind, budget_s=12.0):
             "sample": "nested loop (oracle O1), 4K x 64K, %.1f s" % dt}
 
 
+# ------------------------------------------------------- batched joins --
+
+def make_batch(dev, count, lo, hi, seed=4):
+    """Independent join instances: |R|, |S| log-uniform in [lo, hi], selectivity
+    log-uniform in [1e-6, 1e-3]; even instances are equi-joins over a key
+    domain of 1/sel values, odd ones band joins R.a < S.a and |R.k - S.k| <= w
+    with k over (2w + 1) / (2 sel) values.  Where that domain would give more
+    pairs than input rows it is widened to keep |result| <= max(|R|, |S|)."""
+    import math
+    from paper_1904_11201_gb300 import datagen as D
+    nr = D.log_uniform_int(count, lo, hi, seed, 0).tolist()
+    ns = D.log_uniform_int(count, lo, hi, seed, 1).tolist()
+    u = D.uniform_float(count, seed, 2).tolist()
+    ws = D.uniform_int(count, 0, 17, seed, 3).tolist()
+    inst = []
+    for i in range(count):
+        sel = math.exp(math.log(1e-6) + u[i] * (math.log(1e-3) - math.log(1e-6)))
+        big = max(nr[i], ns[i])
+        if i % 2 == 0:
+            dom = min(max(int(math.ceil(1.0 / sel)), big), 1 << 31)
+            r = D.uniform_keys(nr[i], 0, dom, seed + 10 + i, 0, device=dev)
+            s = D.uniform_keys(ns[i], 0, dom, seed + 10 + i, 1, device=dev)
+            inst.append({"band": -1, "op": 0, "R": (r, None), "S": (s, None), "domain": dom})
+        else:
+            w = ws[i]
+            dom = min(max(int(math.ceil((2 * w + 1) / (2 * sel))), (2 * w + 1) * big // 2 + 1), 1 << 31)
+            ra = D.uniform_keys(nr[i], 0, 1 << 24, seed + 10 + i, 2, device=dev)
+            rk = D.uniform_keys(nr[i], 0, dom, seed + 10 + i, 3, device=dev)
+            sa = D.uniform_keys(ns[i], 0, 1 << 24, seed + 10 + i, 4, device=dev)
+            sk = D.uniform_keys(ns[i], 0, dom, seed + 10 + i, 5, device=dev)
+            inst.append({"band": w, "op": 2, "R": (ra, rk), "S": (sa, sk), "domain": dom})
+    return inst
+
+
+def batch_main(args, world, rank, local, dev, stream, jn, ctx):
+    """A step is one jn_batch call over all instances (one exact allocation)."""
+    count, lo, hi = (256, 1000, 1 << 16) if args.small else (args.batch_count, 1000, 4 << 20)
+    inst = make_batch(dev, count, lo, hi)
+    joins = [(jn.table(*x["R"]), jn.table(*x["S"]), x["op"], x["band"]) for x in inst]
+    rows = sum(x["R"][0].shape[0] + x["S"][0].shape[0] for x in inst)
+    eq_rows = sum(x["R"][0].shape[0] + x["S"][0].shape[0] for x in inst if x["band"] < 0)
+    torch.cuda.synchronize()
+    tune = jn.jn_autotune_batch(ctx, joins)
+    counts = jn.jn_batch_count(ctx, joins)
+    m = sum(counts)
+    m_eq = sum(c for c, x in zip(counts, inst) if x["band"] < 0)
+    clk = ClockSampler(local)
+    clk.start()
+    for _ in range(args.warmup):
+        out, first, cnt = jn.jn_batch(ctx, joins)
+        del out
+    assert cnt == counts
+    l0 = ctx.launch_count()
+    barrier(world)
+    torch.cuda.synchronize()
+    tw0 = time.time()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(args.steps):
+        out, first, cnt = jn.jn_batch(ctx, joins)
+        del out
+    e1.record(stream)
+    torch.cuda.synchronize()
+    clk.mark(tw0, time.time())
+    barrier(world)
+    clocks = clk.stop()
+    launches = ctx.launch_count() - l0
+    ms = max_over_ranks(e0.elapsed_time(e1) / args.steps, world, dev)
+
+    # one at a time: the same joins, each its own library call
+    reps = max(1, min(args.steps, 3))
+    one_counts = []
+    torch.cuda.synchronize()
+    o0 = torch.cuda.Event(enable_timing=True)
+    o1 = torch.cuda.Event(enable_timing=True)
+    o0.record(stream)
+    for rep in range(reps):
+        for R, S, op, band in joins:
+            res = jn.jn_hash(ctx, R, S) if band < 0 else jn.jn_theta(ctx, R, S, op, band)
+            if rep == 0:
+                one_counts.append(res.shape[0])
+            del res
+    o1.record(stream)
+    torch.cuda.synchronize()
+    ms_one = o0.elapsed_time(o1) / reps
+
+    # kernel breakdown from profiled steps (per-launch events; graphs off)
+    ctx.reset_stats()
+    ctx.set_profiling(True)
+    psteps = 2
+    for _ in range(psteps):
+        out, first, cnt = jn.jn_batch(ctx, joins)
+        del out
+    torch.cuda.synchronize()
+    stats = ctx.kernel_stats()
+    ctx.set_profiling(False)
+    bn = rows - eq_rows
+    abytes = {"histogram": 4 * eq_rows + 4 * bn, "scatter": 12 * eq_rows + 20 * bn, "hash_count": 8 * eq_rows,
+              "hash_emit": 8 * eq_rows + 8 * m_eq, "minmax": 4 * bn, "theta_count": 12 * bn,
+              "theta_emit": 12 * bn + 8 * (m - m_eq)}
+    kern, roof = kernel_table(stats, psteps, abytes)
+    units = rows + m
+    value = world * units / (ms * 1e-3)
+    if rank == 0:
+        line = {"metric": "join tuples/s in+out", "value": value, "unit": "tuples/s", "n_gpus": world,
+                "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
+                "scaling": "weak", "vs_baseline": None, "dtype": "int32", "data": "synthetic",
+                "config": {"workload": "batched joins: %d instances (half equi, half band R.a < S.a and "
+                                       "|R.k - S.k| <= w), |R|, |S| log-uniform in [%d, %d], selectivity "
+                                       "log-uniform in [1e-6, 1e-3], int32 keys, no payload" % (count, lo, hi),
+                           "instances": count, "input_rows": rows, "result_pairs": m, "tuning": tune,
+                           "l2": "inputs larger than L2 (no flush needed)" if 4 * rows > (129 << 20)
+                           else "inputs fit in L2",
+                           "parallelism": "replicas" if world > 1 else "1 GPU",
+                           "algo": "jn_batch: one partition pass, one count and one emit launch per phase"},
+                "one_at_a_time": {"ms_per_step": ms_one, "value": world * units / (ms_one * 1e-3),
+                                  "counts_match": one_counts == counts, "speedup_of_batch": ms_one / ms},
+                "roofline": roof, "cpu_baseline": None,
+                "e2e": None, "e2e_note": "batched inputs and outputs stay in device memory",
+                "clocks": clocks, "gpu_launches": launches, "kernels": kern}
+        print(json.dumps(line), flush=True)
+
+
+def kernel_table(stats, steps, abytes):
+    pk, pk_kind = peaks()
+    hbm = pk.get("hbm_gbs", 6800.0)
+    kern = {}
+    for name, (cnt, tms) in stats.items():
+        kern[name] = {"launches_per_step": cnt / steps, "ms_per_step": tms / steps, "share": 0.0,
+                      "avg_launch_ms": tms / max(cnt, 1)}
+        if name in abytes and tms > 0:
+            kern[name]["algorithmic_gb_per_step"] = abytes[name] / 1e9
+            kern[name]["achieved_gbs"] = abytes[name] / (tms / steps * 1e-3) / 1e9
+    tot = sum(v["ms_per_step"] for v in kern.values()) or 1.0
+    for v in kern.values():
+        v["share"] = v["ms_per_step"] / tot
+    dom = max((k for k in kern if "achieved_gbs" in kern[k]), key=lambda k: kern[k]["ms_per_step"], default=None)
+    roof = None
+    if dom:
+        a = kern[dom]["achieved_gbs"]
+        roof = {"bound": "hbm", "kernel": dom, "achieved": a, "peak": hbm, "unit": "GB/s", "frac": a / hbm,
+                "peak_kind": pk_kind + " (copy bandwidth, MEASURED_PEAKS.json hbm_gbs)", "traffic": None,
+                "algorithmic_bytes_per_launch": abytes[dom] / max(kern[dom]["launches_per_step"], 1)}
+    return kern, roof
+
+
+# --------------------------------------------------------------- serving --
+
+def make_pool(dev, n_i32, n_i64, lo, hi, seed=5):
+    """Device tables with Zipf(theta ~ U[0, 1]) keys over 2^28 ranks; every
+    table maps ranks to keys with its own rotation of one shared bijection, so
+    the popular keys of two tables are different keys.  int64 keys sit above
+    2^40.  A second column a, uniform in [0, 2^24), serves band requests."""
+    from paper_1904_11201_gb300 import datagen as D
+    bits = 28
+    sizes = D.log_uniform_int(n_i32 + n_i64, lo, hi, seed, 0).tolist()
+    th = D.uniform_float(n_i32 + n_i64, seed, 1).tolist()
+    rot = D.uniform_int(n_i32 + n_i64, 0, 1 << bits, seed, 2, dtype=torch.int64).tolist()
+    pool = []
+    for i, n in enumerate(sizes):
+        i64 = i >= n_i32
+        ranks = D.zipf_ranks(n, th[i], 1 << bits, seed + 20 + i, 0, dev)
+        ranks = (ranks + rot[i]) & ((1 << bits) - 1)
+        k = D.rank_to_key32(ranks, bits, seed).to(torch.int64 if i64 else torch.int32)
+        if i64:
+            k = k + (0x5A5A << 32)
+        a = D.uniform_int(n, 0, 1 << 24, seed + 20 + i, 1, dev, torch.int64 if i64 else torch.int32)
+        pool.append({"key": k, "a": a, "i64": i64, "theta": th[i], "rows": n})
+        del ranks
+    return pool
+
+
+def serve_main(args, world, rank, local, dev, stream, jn, ctx):
+    """Open-loop Poisson request streams against jn_server at fractions of the
+    one-at-a-time capacity; a step is one request."""
+    import random
+    small = args.small
+    pool = make_pool(dev, 6 if small else 12, 3 if small else 6, 10000, (1 << 20) if small else (64 << 20))
+    n_req = 120 if small else args.serve_requests
+    rng = random.Random(7)
+    i32 = [i for i, t in enumerate(pool) if not t["i64"]]
+    i64 = [i for i, t in enumerate(pool) if t["i64"]]
+    resident = set(i32[: len(i32) // 2] + i64[: len(i64) // 2])
+    reqs = []
+    for q in range(n_req):
+        ids = i32 if rng.random() < 2.0 / 3 else i64
+        r, s = rng.choice(ids), rng.choice(ids)
+        if rng.random() < 0.7:
+            # 5/7 of the equi requests (half of all) name a resident R by handle
+            use_h = rng.random() < 5.0 / 7
+            if use_h:
+                r = rng.choice([i for i in ids if i in resident])
+            reqs.append({"kind": "equi", "r": r, "s": s, "op": 0, "band": -1, "resident": use_h})
+        else:
+            reqs.append({"kind": "band", "r": r, "s": s, "op": 2, "band": rng.randint(0, 4), "resident": False})
+    eq_t = {i: jn.table(t["key"]) for i, t in enumerate(pool)}
+    bd_t = {i: jn.table(t["a"], t["key"]) for i, t in enumerate(pool)}
+    torch.cuda.synchronize()
+
+    # one at a time, through the library on one context
+    def one(q):
+        if q["kind"] == "equi":
+            return jn.jn_hash(ctx, eq_t[q["r"]], eq_t[q["s"]])
+        return jn.jn_theta(ctx, bd_t[q["r"]], bd_t[q["s"]], q["op"], q["band"])
+
+    for q in reqs[:8]:
+        del_ = one(q)
+        del del_
+    torch.cuda.synchronize()
+    m_of = []
+    t0 = time.perf_counter()
+    for q in reqs:
+        res = one(q)
+        m_of.append(res.shape[0])
+        del res
+    torch.cuda.synchronize()
+    t_one = time.perf_counter() - t0
+    rows = [pool[q["r"]]["rows"] + pool[q["s"]]["rows"] for q in reqs]
+    units = sum(rows) + sum(m_of)
+    cap_rps = n_req / t_one
+
+    srv = jn.Server(local, slots=args.serve_slots, coalesce_rows=1 << 18, max_batch=64,
+                    memory_budget=96 << 30, graphs=False)
+    handles = {i: srv.register(eq_t[i]) for i in resident}
+
+    def submit(q):
+        if q["resident"]:
+            return srv.submit(None, eq_t[q["s"]], 0, -1, r_handle=handles[q["r"]])
+        if q["kind"] == "equi":
+            return srv.submit(eq_t[q["r"]], eq_t[q["s"]], 0, -1)
+        return srv.submit(bd_t[q["r"]], bd_t[q["s"]], q["op"], q["band"])
+
+    def run_stream(rate):
+        """rate None: everything submitted at once (saturation)."""
+        arr = [0.0] * n_req
+        if rate:
+            g = random.Random(11)
+            t = 0.0
+            for i in range(n_req):
+                t += g.expovariate(rate)
+                arr[i] = t
+        tickets = [None] * n_req
+        lat = [0.0] * n_req
+        status = [0] * n_req
+        got_m = [0] * n_req
+
+        def waiter():
+            for i in range(n_req):
+                while tickets[i] is None:
+                    time.sleep(0.0002)
+                res = srv.wait(tickets[i])
+                status[i] = res["status"]
+                lat[i] = res["total_ms"]
+                got_m[i] = res["pairs"]
+                srv.release(tickets[i])
+
+        th = threading.Thread(target=waiter)
+        th.start()
+        start = time.perf_counter()
+        for i, q in enumerate(reqs):
+            d = start + arr[i] - time.perf_counter()
+            if d > 0:
+                time.sleep(d)
+            tickets[i] = submit(q)
+        th.join()
+        wall = time.perf_counter() - start
+        ok = [i for i in range(n_req) if status[i] == 0]
+        ls = sorted(lat[i] for i in ok)
+        pct = (lambda p: ls[min(len(ls) - 1, int(p * len(ls)))] if ls else None)
+        return {"offered_req_s": rate, "achieved_req_s": len(ok) / wall, "wall_s": wall, "ok": len(ok),
+                "refused_or_failed": n_req - len(ok), "p50_ms": pct(0.5), "p99_ms": pct(0.99),
+                "tuples_per_s": sum(rows[i] + got_m[i] for i in ok) / wall,
+                "results_match": all(got_m[i] == m_of[i] for i in ok)}
+
+    clk = ClockSampler(local)
+    clk.start()
+    run_stream(None)  # warm-up: worker contexts, pools
+    tw0 = time.time()
+    sat = run_stream(None)
+    rates = [dict(run_stream(f * cap_rps), fraction=f) for f in (0.5, 0.8, 0.95)]
+    clk.mark(tw0, time.time())
+    clocks = clk.stop()
+    st = srv.stats()
+    srv.close()
+    if rank == 0:
+        line = {"metric": "join tuples/s in+out", "value": world * sat["tuples_per_s"], "unit": "tuples/s",
+                "n_gpus": world, "steps": n_req, "warmup": n_req, "ms_per_step": 1e3 * sat["wall_s"] / n_req,
+                "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "int32+int64",
+                "data": "synthetic",
+                "config": {"workload": "serving: %d requests (70%% equi, 30%% band R.a < S.a and |R.k - S.k| <= w),"
+                                       " tables of %d-%d rows, int32/int64 Zipf(theta ~ U[0,1]) keys, equi "
+                                       "requests on resident tables by handle" % (n_req, 10000, pool_hi(small)),
+                           "pool_tables": len(pool), "slots": args.serve_slots, "coalesce_rows": 1 << 18,
+                           "resident_requests": sum(q["resident"] for q in reqs),
+                           "l2": "tables up to 64M rows; no flush between requests",
+                           "parallelism": "replicas" if world > 1 else "1 GPU"},
+                "one_at_a_time": {"req_s": cap_rps, "tuples_per_s": units / t_one},
+                "saturation": sat, "poisson": rates, "server_stats": st,
+                "roofline": None, "cpu_baseline": None, "e2e": None,
+                "e2e_note": "requests name device-resident columns; latency is submit to pairs ready",
+                "clocks": clocks, "gpu_launches": None}
+        print(json.dumps(line), flush=True)
+
+
+def pool_hi(small):
+    return (1 << 20) if small else (64 << 20)
+
+
 # ------------------------------------------------------------------ main --
 
 def dist_setup(args):
@@ -323,6 +632,9 @@ def main():
                     help="count + checksum without storing pairs (results too large to store)")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--batch-count", type=int, default=4096, help="batch workload: number of joins")
+    ap.add_argument("--serve-requests", type=int, default=400, help="serve workload: requests per stream")
+    ap.add_argument("--serve-slots", type=int, default=4, help="serve workload: server worker slots")
     args = ap.parse_args()
     world, rank, local = dist_setup(args)
     if args.impl == "reference":
@@ -343,6 +655,13 @@ def main():
     ctx = jn.Context(local, stream)
     if args.prefilter != -1 or args.radix_bits:
         ctx.set_tuning(prefilter=args.prefilter, radix_bits=args.radix_bits)
+    if args.workload in ("batch", "serve"):
+        (batch_main if args.workload == "batch" else serve_main)(args, world, rank, local, dev, stream, jn, ctx)
+        ctx.close()
+        if world > 1:
+            import torch.distributed as dist
+            dist.destroy_process_group()
+        return
     w = make_workload(args.workload, args.theta, dev, args.small, args.rows_log2)
     if args.aggregate:
         w["aggregate"] = True

@@ -98,7 +98,8 @@ typedef struct {
     int32_t theta_groups;  /* log2 of the theta/band group count (0 = auto, <= 10)      */
     int32_t nlj_tile_r;    /* R rows per nested-loop tile (0 = auto; multiple of 256)   */
     int32_t graphs;        /* 1: jn_batch captures and replays its phases as CUDA graphs */
-    int32_t reserved[8];
+    int32_t part_rows;     /* jn_batch: R rows per partition of an equi-join (0 = auto)  */
+    int32_t reserved[7];
 } jn_tuning;
 
 /* Per-kernel launch statistics (profiling mode). */
@@ -256,6 +257,26 @@ jn_status jn_nested_loop_noalloc(const jn_table* R, const jn_table* S, const jn_
  * stream; with ctx == NULL, on the legacy default stream, so results may
  * outlive their context). */
 void jn_free(jn_ctx* ctx, jn_pair* p);
+
+/* Counts every join of a batch, as jn_batch would emit them, and writes no
+ * pair: pairs[i] receives join i's result size, *total (may be NULL) their
+ * sum.  Same arguments and checks as jn_batch; it runs the batch's shared
+ * partition and count phases only, so a caller can size one output buffer
+ * (or decide whether it fits) first. */
+jn_status jn_batch_count(jn_ctx* ctx, int32_t count, const jn_join* joins, uint64_t* pairs, uint64_t* total);
+
+/* Autotuner: times candidate tunings on these inputs through the count pass
+ * (every phase but the writing of pairs), applies the fastest to the context
+ * and caches it per (algorithm, key type, size class); *best (may be NULL)
+ * receives it.  The knobs tried never change a result: the hash join's
+ * partition bits and pre-filter, the theta join's group count, the nested
+ * loop's R tile.  It stands in for the hand sweep of the partition parameter
+ * alpha in Sec. 5.1.4 and 5.2.4. */
+jn_status jn_autotune(jn_ctx* ctx, int32_t algo, const jn_table* R, const jn_table* S, const jn_pred* pred,
+                      jn_tuning* best);
+/* The same for a batch (rows per partition of its equi-joins, graphs on or
+ * off), timing the batch's count phases. */
+jn_status jn_autotune_batch(jn_ctx* ctx, int32_t count, const jn_join* joins, jn_tuning* best);
 
 /* ------------------------------------------------------------- serving --- */
 

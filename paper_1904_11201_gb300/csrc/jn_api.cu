@@ -132,7 +132,7 @@ static jn_status run(jn_ctx* c, int algo, const jn_table* R, const jn_table* S, 
 
 template <typename K>
 static jn_status batch_typed(jn_ctx* c, int count, const jn_join* joins, jn_pair** out, uint64_t capacity,
-                             uint64_t* n_out, uint64_t* first, uint64_t* pairs) {
+                             uint64_t* n_out, uint64_t* first, uint64_t* pairs, bool count_only) {
     Scratch s(c);
     std::vector<int> eq, bd;
     for (int i = 0; i < count; i++) (joins[i].band < 0 ? eq : bd).push_back(i);
@@ -155,6 +155,13 @@ static jn_status batch_typed(jn_ctx* c, int count, const jn_join* joins, jn_pair
     if (!bd.empty())
         JN_TRY(batch_band_prepare<K>(c, (int)bd.size(), BR.data(), BS.data(), bops.data(), bbands.data(), &be));
     const uint64_t te = he ? he->total : 0, tb = be ? be->total : 0;
+    if (count_only) {
+        for (size_t j = 0; j < eq.size(); j++) pairs[eq[j]] = he->offsets[j + 1] - he->offsets[j];
+        for (size_t j = 0; j < bd.size(); j++) pairs[bd[j]] = be->offsets[j + 1] - be->offsets[j];
+        *n_out = te + tb;
+        c->info.result = te + tb;
+        return JN_OK;
+    }
     OutPlan plan;
     plan.user_out = out;
     plan.capacity = capacity;
@@ -206,8 +213,8 @@ jn_status jn_hash(jn_ctx* ctx, const jn_table* R, const jn_table* S, jn_pair** o
     return run(ctx, JN_ALGO_HASH, R, S, nullptr, MODE_EMIT, out, capacity, n_out, nullptr, nullptr);
 }
 
-jn_status jn_batch(jn_ctx* ctx, int32_t count, const jn_join* joins, jn_pair** out, uint64_t capacity,
-                   uint64_t* n_out, uint64_t* first, uint64_t* pairs) {
+static jn_status batch_entry(jn_ctx* ctx, int32_t count, const jn_join* joins, jn_pair** out, uint64_t capacity,
+                             uint64_t* n_out, uint64_t* first, uint64_t* pairs, bool count_only) {
     if (!ctx) return JN_ERR_INVALID;
     ctx->err.clear();
     if (count < 0 || (count > 0 && (!joins || !first || !pairs)) || !out || !n_out)
@@ -231,9 +238,26 @@ jn_status jn_batch(jn_ctx* ctx, int32_t count, const jn_join* joins, jn_pair** o
     JN_CUDA(ctx, cudaSetDevice(ctx->device));
     ctx->info = jn_run_info();
     const uint64_t l0 = ctx->launches_total;
-    jn_status st = kt == JN_KEY_I32 ? batch_typed<int32_t>(ctx, count, joins, out, capacity, n_out, first, pairs)
-                                    : batch_typed<int64_t>(ctx, count, joins, out, capacity, n_out, first, pairs);
+    jn_status st = kt == JN_KEY_I32
+                       ? batch_typed<int32_t>(ctx, count, joins, out, capacity, n_out, first, pairs, count_only)
+                       : batch_typed<int64_t>(ctx, count, joins, out, capacity, n_out, first, pairs, count_only);
     ctx->info.kernel_launches = ctx->launches_total - l0;
+    return st;
+}
+
+jn_status jn_batch(jn_ctx* ctx, int32_t count, const jn_join* joins, jn_pair** out, uint64_t capacity,
+                   uint64_t* n_out, uint64_t* first, uint64_t* pairs) {
+    return batch_entry(ctx, count, joins, out, capacity, n_out, first, pairs, false);
+}
+
+jn_status jn_batch_count(jn_ctx* ctx, int32_t count, const jn_join* joins, uint64_t* pairs, uint64_t* total) {
+    if (!ctx) return JN_ERR_INVALID;
+    if (count > 0 && !pairs) return fail(ctx, JN_ERR_INVALID, "jn_batch_count: NULL pairs");
+    std::vector<uint64_t> first(count > 0 ? count : 1);
+    jn_pair* none = nullptr;
+    uint64_t n = 0;
+    const jn_status st = batch_entry(ctx, count, joins, &none, 0, &n, first.data(), pairs, true);
+    if (st == JN_OK && total) *total = n;
     return st;
 }
 

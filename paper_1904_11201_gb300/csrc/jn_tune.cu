@@ -1,0 +1,147 @@
+// Autotuner: picks tuning knobs by timing them.
+//
+// The knobs that shape the work without changing the result -- the hash
+// join's partition bits and pre-filter, the theta join's group count, the
+// nested loop's R tile, a batch's rows per partition -- are tried on the
+// caller's own inputs through the count pass (every phase except writing the
+// pairs), the fastest is applied to the context, and the choice is cached per
+// (algorithm, key type, log2 |R|, log2 |S|) so a later call for the same size
+// class costs nothing.  This plays the part of the paper's choice of alpha
+// (Sec. 5.1.4 and 5.2.4 sweep it by hand and report the best range).
+#include <algorithm>
+#include <chrono>
+#include <functional>
+#include <map>
+#include <mutex>
+#include <tuple>
+#include <vector>
+
+#include "jn_common.cuh"
+
+namespace {
+
+using Key = std::tuple<int, int, int, int>;
+std::mutex g_mu;
+std::map<Key, jn_tuning> g_cache;
+
+double time_call(jn_ctx* c, const std::function<jn_status()>& f, jn_status* st) {
+    const auto t0 = std::chrono::steady_clock::now();
+    *st = f();
+    const auto t1 = std::chrono::steady_clock::now();
+    (void)c;
+    return std::chrono::duration<double, std::milli>(t1 - t0).count();
+}
+
+}  // namespace
+
+extern "C" {
+
+jn_status jn_autotune(jn_ctx* c, int32_t algo, const jn_table* R, const jn_table* S, const jn_pred* pred,
+                      jn_tuning* best) {
+    if (!c || !R || !S) return JN_ERR_INVALID;
+    const Key key{algo, R->key_type, jnx::ceil_log2((uint64_t)R->n + 1), jnx::ceil_log2((uint64_t)S->n + 1)};
+    {
+        std::lock_guard<std::mutex> g(g_mu);
+        auto it = g_cache.find(key);
+        if (it != g_cache.end()) {
+            c->tune = it->second;
+            if (best) *best = it->second;
+            return JN_OK;
+        }
+    }
+    const jn_tuning base = c->tune;
+    std::vector<jn_tuning> cands;
+    if (algo == JN_ALGO_HASH) {
+        const int cap = R->key_type == JN_KEY_I32 ? 4096 : 2048;
+        for (int pre : {0, 1}) {
+            const uint64_t target = pre ? cap : cap / 2;
+            int b = jnx::ceil_log2(jnx::ceil_div((uint64_t)R->n + 1, target));
+            for (int d = -1; d <= 1; d++) {
+                jn_tuning t = base;
+                t.prefilter = pre;
+                t.radix_bits = std::max(1, std::min(20, b + d));
+                t.radix_bits1 = 0;
+                cands.push_back(t);
+            }
+        }
+    } else if (algo == JN_ALGO_THETA) {
+        for (int g = 2; g <= 10; g += 2) {
+            jn_tuning t = base;
+            t.theta_groups = g;
+            cands.push_back(t);
+        }
+    } else if (algo == JN_ALGO_NLJ) {
+        for (int tr : {512, 1024, 2048}) {
+            jn_tuning t = base;
+            t.nlj_tile_r = tr;
+            cands.push_back(t);
+        }
+    } else {
+        return JN_ERR_INVALID;
+    }
+    uint64_t cnt = 0;
+    jn_status st = jn_count(c, algo, R, S, pred, &cnt);  // warm-up (and argument check)
+    if (st != JN_OK) return st;
+    double best_ms = 1e30;
+    jn_tuning pick = base;
+    for (const jn_tuning& t : cands) {
+        c->tune = t;
+        const double ms = time_call(c, [&] { return jn_count(c, algo, R, S, pred, &cnt); }, &st);
+        if (st == JN_OK && ms < best_ms) {
+            best_ms = ms;
+            pick = t;
+        }
+    }
+    c->tune = pick;
+    {
+        std::lock_guard<std::mutex> g(g_mu);
+        g_cache[key] = pick;
+    }
+    if (best) *best = pick;
+    return JN_OK;
+}
+
+jn_status jn_autotune_batch(jn_ctx* c, int32_t count, const jn_join* joins, jn_tuning* best) {
+    if (!c || count < 1 || !joins) return JN_ERR_INVALID;
+    uint64_t rows = 0;
+    for (int i = 0; i < count; i++) rows += (uint64_t)joins[i].R.n + (uint64_t)joins[i].S.n;
+    const Key key{100, joins[0].R.key_type, jnx::ceil_log2((uint64_t)count), jnx::ceil_log2(rows + 1)};
+    {
+        std::lock_guard<std::mutex> g(g_mu);
+        auto it = g_cache.find(key);
+        if (it != g_cache.end()) {
+            c->tune = it->second;
+            if (best) *best = it->second;
+            return JN_OK;
+        }
+    }
+    const jn_tuning base = c->tune;
+    std::vector<uint64_t> pairs(count);
+    auto trial = [&](jn_status* st) { *st = jn_batch_count(c, count, joins, pairs.data(), nullptr); };
+    jn_status st;
+    trial(&st);  // warm-up
+    double best_ms = 1e30;
+    jn_tuning pick = base;
+    for (int rows_per_part : {1024, 2048, 4096}) {
+        for (int graphs : {0, 1}) {
+            jn_tuning t = base;
+            t.part_rows = rows_per_part;
+            t.graphs = graphs;
+            c->tune = t;
+            const double ms = time_call(c, [&] { trial(&st); return st; }, &st);
+            if (st == JN_OK && ms < best_ms) {
+                best_ms = ms;
+                pick = t;
+            }
+        }
+    }
+    c->tune = pick;
+    {
+        std::lock_guard<std::mutex> g(g_mu);
+        g_cache[key] = pick;
+    }
+    if (best) *best = pick;
+    return JN_OK;
+}
+
+}  // extern "C"

@@ -841,8 +841,9 @@ struct HashBatchRun : BatchRun {
         std::vector<int> bits(2 * (size_t)n);
         std::vector<TileRef> tiles;
         uint64_t rows = 0, rrows = 0;
+        const uint64_t part_rows = c->tune.part_rows > 0 ? (uint64_t)c->tune.part_rows : (uint64_t)cap / 2;
         for (int i = 0; i < n; i++) {
-            int b = ceil_log2(ceil_div((uint64_t)Rs[i].n, (uint64_t)cap / 2));
+            int b = ceil_log2(ceil_div((uint64_t)Rs[i].n, part_rows));
             if (b > 10) b = 10;
             bits[i] = bits[n + i] = b;
             segs[i] = SegCols<K>{Rs[i].key, nullptr, Rs[i].pay, (uint64_t)Rs[i].n};

@@ -48,7 +48,7 @@ class Tuning(ctypes.Structure):
                 ("radix_bits1", ctypes.c_int32), ("filter_bits", ctypes.c_int32),
                 ("heavy", ctypes.c_int32), ("theta_groups", ctypes.c_int32),
                 ("nlj_tile_r", ctypes.c_int32), ("graphs", ctypes.c_int32),
-                ("reserved", ctypes.c_int32 * 8)]
+                ("part_rows", ctypes.c_int32), ("reserved", ctypes.c_int32 * 7)]
 
 
 class Join(ctypes.Structure):
@@ -124,6 +124,10 @@ _SIGS = {
                                 ctypes.POINTER(ctypes.c_uint64), ctypes.POINTER(ctypes.c_uint64),
                                 ctypes.POINTER(ctypes.c_uint64)]),
     "jn_free": (None, [_P, _P]),
+    "jn_batch_count": (ctypes.c_int, [_P, ctypes.c_int32, ctypes.POINTER(Join), _P, _P]),
+    "jn_autotune": (ctypes.c_int, [_P, ctypes.c_int32, ctypes.POINTER(Table), ctypes.POINTER(Table),
+                                   ctypes.POINTER(Pred), ctypes.POINTER(Tuning)]),
+    "jn_autotune_batch": (ctypes.c_int, [_P, ctypes.c_int32, ctypes.POINTER(Join), ctypes.POINTER(Tuning)]),
     "jn_nested_loop_noalloc": (ctypes.c_int, [ctypes.POINTER(Table), ctypes.POINTER(Table), ctypes.POINTER(Pred),
                                               _P, ctypes.c_uint64, ctypes.POINTER(ctypes.c_uint64), _P]),
     "jn_server_create": (ctypes.c_int, [ctypes.POINTER(_P), ctypes.c_int, ctypes.POINTER(ServerConfig)]),
@@ -463,3 +467,33 @@ def jn_nested_loop_noalloc(R: TableRef, S: TableRef, pr: Pred = None, out=None, 
     if rc != JN_OK:
         raise JoinError(rc, load().jn_status_str(rc).decode(), int(n.value) if rc == JN_ERR_CAPACITY else None)
     return out[:int(n.value)]
+
+
+def jn_autotune(ctx: Context, algo: int, R: TableRef, S: TableRef, pr: Pred = None) -> dict:
+    """Times candidate tunings through the count pass; applies and returns the fastest."""
+    t = Tuning()
+    st = load().jn_autotune(ctx.handle, algo, ctypes.byref(R.t), ctypes.byref(S.t),
+                            ctypes.byref(pr) if pr is not None else None, ctypes.byref(t))
+    _check(ctx, st)
+    return {f: getattr(t, f) for f, _ in Tuning._fields_ if f != "reserved"}
+
+
+def jn_autotune_batch(ctx: Context, joins) -> dict:
+    n = len(joins)
+    arr = (Join * max(n, 1))()
+    for i, (R, S, op, band) in enumerate(joins):
+        arr[i] = Join(R.t, S.t, op, 0, band)
+    t = Tuning()
+    _check(ctx, load().jn_autotune_batch(ctx.handle, n, arr, ctypes.byref(t)))
+    return {f: getattr(t, f) for f, _ in Tuning._fields_ if f != "reserved"}
+
+
+def jn_batch_count(ctx: Context, joins) -> list:
+    """Per-join result sizes of a batch [(R, S, op, band), ...] without emitting pairs."""
+    n = len(joins)
+    arr = (Join * max(n, 1))()
+    for i, (R, S, op, band) in enumerate(joins):
+        arr[i] = Join(R.t, S.t, op, 0, band)
+    cnt = (ctypes.c_uint64 * max(n, 1))()
+    _check(ctx, load().jn_batch_count(ctx.handle, n, arr, cnt, None))
+    return [int(cnt[i]) for i in range(n)]
