@@ -132,8 +132,8 @@ def algorithmic_bytes(kind, info, nr, ns, m, ksize):
             "scatter": row * (nr + ns) + row * surv + 2 * row * surv,
             "histogram": ksize * surv,
             "hash_count": row * surv,
-            "hash_emit": row * surv + 8 * m,
-            "cross_emit": 8 * m,
+            "hash_emit": row * surv + 8 * (m - info.get("heavy_pairs", 0)),
+            "cross_emit": 8 * info.get("heavy_pairs", 0),
         }
     if kind == "band":
         return {
@@ -427,52 +427,56 @@ def serve_main(args, world, rank, local, dev, stream, jn, ctx):
     one-at-a-time capacity; a step is one request."""
     import random
     small = args.small
-    pool = make_pool(dev, 6 if small else 12, 3 if small else 6, 10000, (1 << 20) if small else (64 << 20))
-    n_req = 120 if small else args.serve_requests
-    rng = random.Random(7)
+    pool = make_pool(dev, 5 if small else 9, 5 if small else 9, 10000, pool_hi(small))
+    n_req = 200 if small else args.serve_requests
+    budget = 32 << 30
+    rng = random.Random(0)
     i32 = [i for i, t in enumerate(pool) if not t["i64"]]
     i64 = [i for i, t in enumerate(pool) if t["i64"]]
     resident = set(i32[: len(i32) // 2] + i64[: len(i64) // 2])
-    reqs = []
-    for q in range(n_req):
-        ids = i32 if rng.random() < 2.0 / 3 else i64
-        r, s = rng.choice(ids), rng.choice(ids)
-        if rng.random() < 0.7:
-            # 5/7 of the equi requests (half of all) name a resident R by handle
-            use_h = rng.random() < 5.0 / 7
-            if use_h:
-                r = rng.choice([i for i in ids if i in resident])
-            reqs.append({"kind": "equi", "r": r, "s": s, "op": 0, "band": -1, "resident": use_h})
-        else:
-            reqs.append({"kind": "band", "r": r, "s": s, "op": 2, "band": rng.randint(0, 4), "resident": False})
     eq_t = {i: jn.table(t["key"]) for i, t in enumerate(pool)}
     bd_t = {i: jn.table(t["a"], t["key"]) for i, t in enumerate(pool)}
     torch.cuda.synchronize()
+    reqs = []
+    for _ in range(n_req):
+        ids = i32 if rng.random() < 0.5 else i64
+        s = rng.choice(ids)
+        if rng.random() < 0.7:
+            # 5/7 of the equi requests (half of all) name a resident R by handle
+            use_h = rng.random() < 5.0 / 7
+            r = rng.choice([i for i in ids if i != s and (i in resident or not use_h)])
+            reqs.append({"kind": "equi", "r": r, "s": s, "op": 0, "band": -1, "resident": use_h})
+        else:
+            r = rng.choice([i for i in ids if i != s])  # two different tables: their popular keys differ
+            reqs.append({"kind": "band", "r": r, "s": s, "op": 2, "band": rng.randint(0, 4), "resident": False})
 
-    # one at a time, through the library on one context
+    # one at a time, through the library on one context, admitted by the same budget
+    ctx.set_memory_limit(budget)
+
     def one(q):
-        if q["kind"] == "equi":
-            return jn.jn_hash(ctx, eq_t[q["r"]], eq_t[q["s"]])
-        return jn.jn_theta(ctx, bd_t[q["r"]], bd_t[q["s"]], q["op"], q["band"])
+        try:
+            if q["kind"] == "equi":
+                return jn.jn_hash(ctx, eq_t[q["r"]], eq_t[q["s"]]).shape[0]
+            return jn.jn_theta(ctx, bd_t[q["r"]], bd_t[q["s"]], q["op"], q["band"]).shape[0]
+        except jn.JoinError as e:
+            if e.status != jn.JN_ERR_OOM:
+                raise
+            return -1
 
-    for q in reqs[:8]:
-        del_ = one(q)
-        del del_
+    for q in reqs[:16]:
+        one(q)
     torch.cuda.synchronize()
-    m_of = []
     t0 = time.perf_counter()
-    for q in reqs:
-        res = one(q)
-        m_of.append(res.shape[0])
-        del res
+    m_of = [one(q) for q in reqs]
     torch.cuda.synchronize()
     t_one = time.perf_counter() - t0
+    ctx.set_memory_limit(0)
     rows = [pool[q["r"]]["rows"] + pool[q["s"]]["rows"] for q in reqs]
-    units = sum(rows) + sum(m_of)
+    units = sum(rows[i] + m_of[i] for i in range(n_req) if m_of[i] >= 0)
     cap_rps = n_req / t_one
 
     srv = jn.Server(local, slots=args.serve_slots, coalesce_rows=1 << 18, max_batch=64,
-                    memory_budget=96 << 30, graphs=False)
+                    memory_budget=budget, graphs=False)
     handles = {i: srv.register(eq_t[i]) for i in resident}
 
     def submit(q):
@@ -482,22 +486,22 @@ def serve_main(args, world, rank, local, dev, stream, jn, ctx):
             return srv.submit(eq_t[q["r"]], eq_t[q["s"]], 0, -1)
         return srv.submit(bd_t[q["r"]], bd_t[q["s"]], q["op"], q["band"])
 
-    def run_stream(rate):
+    def run_stream(rate, count):
         """rate None: everything submitted at once (saturation)."""
-        arr = [0.0] * n_req
+        arr = [0.0] * count
         if rate:
             g = random.Random(11)
             t = 0.0
-            for i in range(n_req):
+            for i in range(count):
                 t += g.expovariate(rate)
                 arr[i] = t
-        tickets = [None] * n_req
-        lat = [0.0] * n_req
-        status = [0] * n_req
-        got_m = [0] * n_req
+        tickets = [None] * count
+        lat = [0.0] * count
+        status = [0] * count
+        got_m = [0] * count
 
         def waiter():
-            for i in range(n_req):
+            for i in range(count):
                 while tickets[i] is None:
                     time.sleep(0.0002)
                 res = srv.wait(tickets[i])
@@ -509,44 +513,50 @@ def serve_main(args, world, rank, local, dev, stream, jn, ctx):
         th = threading.Thread(target=waiter)
         th.start()
         start = time.perf_counter()
-        for i, q in enumerate(reqs):
+        for i in range(count):
             d = start + arr[i] - time.perf_counter()
             if d > 0:
                 time.sleep(d)
-            tickets[i] = submit(q)
+            tickets[i] = submit(reqs[i])
         th.join()
         wall = time.perf_counter() - start
-        ok = [i for i in range(n_req) if status[i] == 0]
+        ok = [i for i in range(count) if status[i] == 0]
         ls = sorted(lat[i] for i in ok)
         pct = (lambda p: ls[min(len(ls) - 1, int(p * len(ls)))] if ls else None)
+        refused = [i for i in range(count) if status[i] == jn.JN_ERR_OOM]
         return {"offered_req_s": rate, "achieved_req_s": len(ok) / wall, "wall_s": wall, "ok": len(ok),
-                "refused_or_failed": n_req - len(ok), "p50_ms": pct(0.5), "p99_ms": pct(0.99),
+                "refused_oom": len(refused), "failed": count - len(ok) - len(refused),
+                "p50_ms": pct(0.5), "p99_ms": pct(0.99),
                 "tuples_per_s": sum(rows[i] + got_m[i] for i in ok) / wall,
-                "results_match": all(got_m[i] == m_of[i] for i in ok)}
+                "results_match": all(got_m[i] == m_of[i] for i in ok)
+                and all(m_of[i] < 0 for i in refused)}
 
     clk = ClockSampler(local)
     clk.start()
-    run_stream(None)  # warm-up: worker contexts, pools
+    run_stream(None, min(n_req, 500))  # warm-up: worker contexts, pools
     tw0 = time.time()
-    sat = run_stream(None)
-    rates = [dict(run_stream(f * cap_rps), fraction=f) for f in (0.5, 0.8, 0.95)]
+    sat = run_stream(None, n_req)
+    rates = [dict(run_stream(f * cap_rps, n_req), fraction=f) for f in (0.5, 0.8, 0.95)]
     clk.mark(tw0, time.time())
     clocks = clk.stop()
     st = srv.stats()
     srv.close()
     if rank == 0:
         line = {"metric": "join tuples/s in+out", "value": world * sat["tuples_per_s"], "unit": "tuples/s",
-                "n_gpus": world, "steps": n_req, "warmup": n_req, "ms_per_step": 1e3 * sat["wall_s"] / n_req,
+                "n_gpus": world, "steps": n_req, "warmup": min(n_req, 500),
+                "ms_per_step": 1e3 * sat["wall_s"] / n_req,
                 "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "int32+int64",
                 "data": "synthetic",
                 "config": {"workload": "serving: %d requests (70%% equi, 30%% band R.a < S.a and |R.k - S.k| <= w),"
-                                       " tables of %d-%d rows, int32/int64 Zipf(theta ~ U[0,1]) keys, equi "
-                                       "requests on resident tables by handle" % (n_req, 10000, pool_hi(small)),
+                                       " tables of %d-%d rows, int32/int64 50/50, Zipf(theta ~ U[0,1]) keys over "
+                                       "2^28 ranks, half the requests on resident tables by handle"
+                                       % (n_req, 10000, pool_hi(small)),
                            "pool_tables": len(pool), "slots": args.serve_slots, "coalesce_rows": 1 << 18,
-                           "resident_requests": sum(q["resident"] for q in reqs),
+                           "memory_budget": budget, "resident_requests": sum(q["resident"] for q in reqs),
                            "l2": "tables up to 64M rows; no flush between requests",
                            "parallelism": "replicas" if world > 1 else "1 GPU"},
-                "one_at_a_time": {"req_s": cap_rps, "tuples_per_s": units / t_one},
+                "one_at_a_time": {"req_s": cap_rps, "tuples_per_s": units / t_one,
+                                  "refused_oom": sum(1 for x in m_of if x < 0)},
                 "saturation": sat, "poisson": rates, "server_stats": st,
                 "roofline": None, "cpu_baseline": None, "e2e": None,
                 "e2e_note": "requests name device-resident columns; latency is submit to pairs ready",
@@ -632,8 +642,9 @@ def main():
                     help="count + checksum without storing pairs (results too large to store)")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--no-autotune", action="store_true", help="keep the library's default tuning")
     ap.add_argument("--batch-count", type=int, default=4096, help="batch workload: number of joins")
-    ap.add_argument("--serve-requests", type=int, default=400, help="serve workload: requests per stream")
+    ap.add_argument("--serve-requests", type=int, default=10000, help="serve workload: requests per stream")
     ap.add_argument("--serve-slots", type=int, default=4, help="serve workload: server worker slots")
     args = ap.parse_args()
     world, rank, local = dist_setup(args)
@@ -673,6 +684,16 @@ def main():
     nr, ns = rk.shape[0], sk.shape[0]
     ksize = rk.element_size()
     torch.cuda.synchronize()
+    if args.prefilter == -1 and not args.radix_bits and not args.no_autotune:
+        # the library's autotuner times its candidate tunings before the warm-up
+        algo = {"hash": jn.JN_ALGO_HASH, "band": jn.JN_ALGO_THETA, "nlj": jn.JN_ALGO_NLJ}[w["kind"]]
+        pr = None
+        if w["kind"] == "band":
+            pr = jn.pred(w["op"], jn.JN_ANY, w["band"])
+        elif "pred" in w:
+            pr = jn.pred(*w["pred"])
+        w["config"]["tuning"] = jn.jn_autotune(ctx, algo, R, S, pr)
+        w["config"]["autotuned"] = True
 
     clk = ClockSampler(local)
     clk.start()

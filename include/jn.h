@@ -122,7 +122,9 @@ typedef struct {
     int32_t radix_bits;
     int32_t radix_bits1;
     int32_t filter_bits;
-    uint64_t reserved[6];
+    uint64_t scratch_peak;      /* most scratch bytes the call held at once         */
+    uint64_t heavy_pairs;       /* pairs emitted by the cross-product path          */
+    uint64_t reserved[4];
 } jn_run_info;
 
 typedef struct jn_ctx jn_ctx;
@@ -336,6 +338,22 @@ jn_status jn_server_release(jn_server* s, uint64_t ticket);  /* frees the pairs 
 jn_status jn_server_stats_get(jn_server* s, jn_server_stats* out);
 
 /* ------------------------------------------------------- introspection --- */
+
+/* Admission.  Every join finds its exact result size (the count pass) before
+ * it allocates its output.  At that point a context
+ *   - with a memory limit (bytes, 0 = none) refuses a run whose output plus
+ *     the scratch it holds exceeds the limit: JN_ERR_OOM, nothing written,
+ *     *n_out = the exact pair count;
+ *   - with an admission hook calls it with the output bytes it is about to
+ *     allocate (0 when the caller supplied device memory) and the scratch
+ *     bytes it holds; any status but JN_OK stops the run with that status the
+ *     same way.  The hook runs on the calling thread, between the count and
+ *     the emit pass, and must not call into the same context.
+ * This is how a caller admits work by exact bytes without a separate count
+ * pass (jn_server uses it). */
+typedef jn_status (*jn_admit_fn)(void* user, uint64_t out_bytes, uint64_t scratch_bytes);
+jn_status jn_set_memory_limit(jn_ctx* ctx, uint64_t bytes);
+jn_status jn_set_admission(jn_ctx* ctx, jn_admit_fn fn, void* user);  /* fn NULL: no hook */
 
 jn_status jn_set_profiling(jn_ctx* ctx, int32_t on);  /* CUDA events around each launch */
 /* Copies up to max entries (kernels with at least one launch) into out; *n =

@@ -39,6 +39,9 @@ struct RunResult {
     uint64_t checksum = 0;
 };
 
+// R rows one hash-join work item holds in shared memory, by key type.
+int hash_cap(int32_t key_type);
+
 template <typename K>
 jn_status run_hash(jn_ctx* c, const Cols<K>& R, const Cols<K>& S, int mode, OutPlan* plan,
                    RunResult* res);

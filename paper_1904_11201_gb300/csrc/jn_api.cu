@@ -8,10 +8,30 @@
 
 namespace jnx {
 
+// Admission by exact bytes: the count is known, nothing is allocated yet.
+static jn_status admit(jn_ctx* c, uint64_t m, uint64_t out_bytes, OutPlan& plan) {
+    if (c->mem_limit && out_bytes + c->scratch_bytes > c->mem_limit) {
+        *plan.n_out = m;
+        return fail(c, JN_ERR_OOM, "the exact result and the scratch held exceed the memory limit");
+    }
+    if (c->admit) {
+        const jn_status st = c->admit(c->admit_user, out_bytes, c->scratch_bytes);
+        if (st != JN_OK) {
+            *plan.n_out = m;
+            return fail(c, st, "the admission hook refused the run");
+        }
+    }
+    return JN_OK;
+}
+
 jn_status out_prepare(jn_ctx* c, Scratch& s, uint64_t m, OutPlan& plan) {
     jn_pair* user = *plan.user_out;
     plan.host_copy = false;
     plan.lib_alloc = false;
+    {
+        const bool dev_out = user != nullptr && (m == 0 || m > plan.capacity || is_device_pointer(user));
+        JN_TRY(admit(c, m, dev_out ? 0 : m * sizeof(jn_pair), plan));
+    }
     if (user == nullptr) {
         plan.lib_alloc = true;
         plan.dev = nullptr;

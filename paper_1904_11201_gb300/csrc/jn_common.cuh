@@ -71,6 +71,10 @@ struct jn_ctx {
     uint64_t launches_at_call = 0;
     std::string err;
     jn_run_info info{};
+    uint64_t scratch_bytes = 0;  // bytes held by live Scratch sets
+    uint64_t mem_limit = 0;      // admission: output + scratch bound (0 = none)
+    jn_admit_fn admit = nullptr;
+    void* admit_user = nullptr;
 };
 
 namespace jnx {
@@ -100,9 +104,11 @@ void dfree(jn_ctx* c, void* p);
 struct Scratch {
     jn_ctx* c;
     std::vector<void*> ptrs;
+    uint64_t held = 0;
     explicit Scratch(jn_ctx* ctx) : c(ctx) {}
     ~Scratch() {
         for (void* p : ptrs) dfree(c, p);
+        c->scratch_bytes -= held;
     }
     template <typename T>
     jn_status get(T** p, size_t count) {
@@ -112,6 +118,9 @@ struct Scratch {
         jn_status s = dalloc(c, &q, bytes);
         if (s != JN_OK) return s;
         ptrs.push_back(q);
+        held += bytes;
+        c->scratch_bytes += bytes;
+        if (c->scratch_bytes > c->info.scratch_peak) c->info.scratch_peak = c->scratch_bytes;
         *p = static_cast<T*>(q);
         return JN_OK;
     }

@@ -363,6 +363,19 @@ void jn_free(jn_ctx* c, jn_pair* p) {
     if (p) cudaFreeAsync(p, c ? c->stream : (cudaStream_t)0);
 }
 
+jn_status jn_set_memory_limit(jn_ctx* c, uint64_t bytes) {
+    if (!c) return JN_ERR_INVALID;
+    c->mem_limit = bytes;
+    return JN_OK;
+}
+
+jn_status jn_set_admission(jn_ctx* c, jn_admit_fn fn, void* user) {
+    if (!c) return JN_ERR_INVALID;
+    c->admit = fn;
+    c->admit_user = user;
+    return JN_OK;
+}
+
 jn_status jn_set_profiling(jn_ctx* c, int32_t on) {
     if (!c) return JN_ERR_INVALID;
     c->profiling = on != 0;

@@ -8,10 +8,12 @@
 // current group ends).  A worker that finds small requests at the head of the
 // queue takes up to max_batch of them and runs them as one jn_batch (one
 // launch sequence for the group); a large request runs alone.  Admission is
-// by device memory: a large request is first counted exactly (the count pass
-// that sizes every output) and waits until its scratch estimate plus its
-// exact output fits in the budget next to the outputs still held; a request
-// that can never fit is refused with JN_ERR_OOM.  Tables registered with the
+// by device memory: a request reserves its scratch estimate, and the join's
+// own exact count pass, through the context's admission hook, reserves the
+// exact output bytes before the output is allocated.  A run that does not fit
+// next to the outputs still held frees its scratch, waits until output and
+// scratch fit together, and runs again; a request that can never fit is
+// refused with JN_ERR_OOM.  Tables registered with the
 // server stay resident on the device across requests.
 //
 // The engine only calls the public entry points of jn.h; it adds no join
@@ -138,23 +140,77 @@ void unreserve(jn_server* s, uint64_t bytes) {
     s->cv_mem.notify_all();
 }
 
-void run_single(jn_server* s, jn_ctx* ctx, cudaStream_t stream, const std::shared_ptr<Job>& j) {
+// Admission state of one worker, read by its context's admission hook.  The
+// join calls the hook once its exact count is known and before it allocates
+// the output, so a request is admitted by its exact output bytes without a
+// count pass of its own.
+struct Admit {
+    jn_server* s = nullptr;
+    uint64_t granted = 0;  // output bytes the hook reserved for the current run
+    uint64_t prepaid = 0;  // output bytes reserved before a second run
+    uint64_t wanted = 0;   // output bytes the last hook call asked for
+    bool asked = false;
+    bool never = false;    // output plus scratch exceed the whole budget
+    void reset() {
+        granted = prepaid = wanted = 0;
+        asked = never = false;
+    }
+};
+
+jn_status admit_hook(void* user, uint64_t out_bytes, uint64_t scratch_bytes) {
+    Admit* a = static_cast<Admit*>(user);
+    jn_server* s = a->s;
+    std::lock_guard<std::mutex> g(s->mu);
+    a->asked = true;
+    a->wanted = out_bytes;
+    if (a->prepaid >= out_bytes) {  // a second run, its bytes already reserved
+        a->granted = a->prepaid;
+        a->prepaid = 0;
+        return JN_OK;
+    }
+    if (out_bytes + scratch_bytes > s->cfg.memory_budget) {
+        a->never = true;
+        return JN_ERR_OOM;
+    }
+    if (s->mem_held + out_bytes > s->cfg.memory_budget) return JN_ERR_OOM;  // not now
+    s->mem_held += out_bytes;
+    if (s->mem_held > s->stats.peak_bytes) s->stats.peak_bytes = s->mem_held;
+    a->granted = out_bytes;
+    return JN_OK;
+}
+
+// Runs `call` under admission: scratch is reserved first (its estimate); a
+// run the hook turned away for lack of memory frees its scratch, waits until
+// output and scratch fit together, and runs once more with the output bytes
+// reserved in advance.  Returns the status; a->granted holds the reserved
+// output bytes of a successful run.
+template <typename Call>
+jn_status admitted_run(jn_server* s, Admit* a, cudaStream_t stream, uint64_t scratch, Call call) {
+    a->reset();
+    if (!reserve(s, scratch)) return JN_ERR_OOM;
+    jn_status st = call();
+    if (st == JN_ERR_OOM && a->asked && !a->never && a->granted == 0) {
+        unreserve(s, scratch);
+        const uint64_t need = a->wanted;
+        a->reset();
+        if (!reserve(s, need + scratch)) return JN_ERR_OOM;
+        a->prepaid = need;
+        st = call();
+    }
+    if (st == JN_OK && cudaStreamSynchronize(stream) != cudaSuccess) {
+        cudaGetLastError();
+        st = JN_ERR_CUDA;
+    }
+    unreserve(s, scratch + (st == JN_OK ? 0 : a->granted) + a->prepaid);
+    if (st != JN_OK) a->granted = 0;
+    a->prepaid = 0;
+    return st;
+}
+
+void run_single(jn_server* s, jn_ctx* ctx, Admit* a, cudaStream_t stream, const std::shared_ptr<Job>& j) {
     jn_request r;
     if (resolve(s, j->req, &r) != JN_OK) {
         finish(s, j, JN_ERR_INVALID, 0, nullptr, nullptr, "unknown table handle");
-        return;
-    }
-    jn_pred pr{r.op, JN_ANY, r.band};
-    const int algo = r.band >= 0 ? JN_ALGO_THETA : JN_ALGO_HASH;
-    uint64_t m = 0;
-    jn_status st = jn_count(ctx, algo, &r.R, &r.S, r.band >= 0 ? &pr : nullptr, &m);
-    if (st != JN_OK) {
-        finish(s, j, st, 0, nullptr, nullptr, jn_last_error(ctx));
-        return;
-    }
-    const uint64_t out_bytes = m * sizeof(jn_pair), scratch = scratch_estimate(r);
-    if (!reserve(s, out_bytes + scratch)) {
-        finish(s, j, JN_ERR_OOM, m, nullptr, nullptr, "request does not fit the memory budget");
         return;
     }
     {
@@ -163,26 +219,25 @@ void run_single(jn_server* s, jn_ctx* ctx, cudaStream_t stream, const std::share
     }
     jn_pair* out = nullptr;
     uint64_t n = 0;
-    st = r.band >= 0 ? jn_theta(ctx, &r.R, &r.S, r.op, r.band, &out, 0, &n)
-                     : jn_hash(ctx, &r.R, &r.S, &out, 0, &n);
-    if (st == JN_OK && cudaStreamSynchronize(stream) != cudaSuccess) {
-        cudaGetLastError();
-        st = JN_ERR_CUDA;
-    }
-    unreserve(s, scratch);
+    const jn_status st = admitted_run(s, a, stream, scratch_estimate(r), [&] {
+        out = nullptr;
+        n = 0;
+        return r.band >= 0 ? jn_theta(ctx, &r.R, &r.S, r.op, r.band, &out, 0, &n)
+                           : jn_hash(ctx, &r.R, &r.S, &out, 0, &n);
+    });
     if (st != JN_OK) {
-        unreserve(s, out_bytes);
-        finish(s, j, st, 0, nullptr, nullptr, jn_last_error(ctx));
+        finish(s, j, st, st == JN_ERR_OOM ? n : 0, nullptr, nullptr,
+               st == JN_ERR_OOM ? "request does not fit the memory budget" : jn_last_error(ctx));
         return;
     }
     auto buf = std::make_shared<OutBuf>();
     buf->ptr = out;
-    buf->bytes = out_bytes;
+    buf->bytes = a->granted;
     buf->refs = 1;
     finish(s, j, JN_OK, n, out, buf, nullptr);
 }
 
-void run_group(jn_server* s, jn_ctx* ctx, cudaStream_t stream, std::vector<std::shared_ptr<Job>>& g) {
+void run_group(jn_server* s, jn_ctx* ctx, Admit* a, cudaStream_t stream, std::vector<std::shared_ptr<Job>>& g) {
     std::vector<jn_join> joins;
     std::vector<std::shared_ptr<Job>> live;
     uint64_t scratch = 0;
@@ -203,10 +258,6 @@ void run_group(jn_server* s, jn_ctx* ctx, cudaStream_t stream, std::vector<std::
         scratch += scratch_estimate(r);
     }
     if (live.empty()) return;
-    if (!reserve(s, scratch)) {
-        for (auto& j : live) finish(s, j, JN_ERR_OOM, 0, nullptr, nullptr, "batch does not fit the memory budget");
-        return;
-    }
     {
         std::lock_guard<std::mutex> lk(s->mu);
         const auto now = Clock::now();
@@ -216,26 +267,22 @@ void run_group(jn_server* s, jn_ctx* ctx, cudaStream_t stream, std::vector<std::
     std::vector<uint64_t> first(live.size()), cnt(live.size());
     jn_pair* out = nullptr;
     uint64_t total = 0;
-    jn_status st = jn_batch(ctx, (int32_t)joins.size(), joins.data(), &out, 0, &total, first.data(), cnt.data());
-    if (st == JN_OK && cudaStreamSynchronize(stream) != cudaSuccess) {
-        cudaGetLastError();
-        st = JN_ERR_CUDA;
-    }
-    unreserve(s, scratch);
+    const jn_status st = admitted_run(s, a, stream, scratch, [&] {
+        out = nullptr;
+        total = 0;
+        return jn_batch(ctx, (int32_t)joins.size(), joins.data(), &out, 0, &total, first.data(), cnt.data());
+    });
     if (st != JN_OK) {
-        for (auto& j : live) finish(s, j, st, 0, nullptr, nullptr, jn_last_error(ctx));
+        for (auto& j : live)
+            finish(s, j, st, 0, nullptr, nullptr,
+                   st == JN_ERR_OOM ? "batch does not fit the memory budget" : jn_last_error(ctx));
         return;
     }
-    // outputs of a group are one allocation: account for it until all are released
+    // outputs of a group are one allocation: accounted for until all are released
     auto buf = std::make_shared<OutBuf>();
     buf->ptr = out;
-    buf->bytes = total * sizeof(jn_pair);
+    buf->bytes = a->granted;
     buf->refs = (int)live.size();
-    {
-        std::lock_guard<std::mutex> lk(s->mu);
-        s->mem_held += buf->bytes;
-        if (s->mem_held > s->stats.peak_bytes) s->stats.peak_bytes = s->mem_held;
-    }
     for (size_t i = 0; i < live.size(); i++) finish(s, live[i], JN_OK, cnt[i], out ? out + first[i] : nullptr, buf, nullptr);
 }
 
@@ -252,6 +299,9 @@ void worker_main(jn_server* s, int slot) {
     jn_get_tuning(ctx, &t);
     t.graphs = s->cfg.graphs ? 1 : 0;
     jn_set_tuning(ctx, &t);
+    Admit adm;
+    adm.s = s;
+    jn_set_admission(ctx, admit_hook, &adm);
     (void)slot;
     while (true) {
         std::vector<std::shared_ptr<Job>> take;
@@ -276,9 +326,9 @@ void worker_main(jn_server* s, int slot) {
             }
         }
         if (take.size() == 1 && rows_of(take[0]->req) >= (uint64_t)s->cfg.coalesce_rows)
-            run_single(s, ctx, stream, take[0]);
+            run_single(s, ctx, &adm, stream, take[0]);
         else
-            run_group(s, ctx, stream, take);
+            run_group(s, ctx, &adm, stream, take);
     }
     jn_destroy(ctx);
     cudaStreamDestroy(stream);

@@ -16,6 +16,7 @@
 #include <tuple>
 #include <vector>
 
+#include "jn_algos.h"
 #include "jn_common.cuh"
 
 namespace {
@@ -52,7 +53,7 @@ jn_status jn_autotune(jn_ctx* c, int32_t algo, const jn_table* R, const jn_table
     const jn_tuning base = c->tune;
     std::vector<jn_tuning> cands;
     if (algo == JN_ALGO_HASH) {
-        const int cap = R->key_type == JN_KEY_I32 ? 4096 : 2048;
+        const int cap = jnx::hash_cap(R->key_type);
         for (int pre : {0, 1}) {
             const uint64_t target = pre ? cap : cap / 2;
             int b = jnx::ceil_log2(jnx::ceil_div((uint64_t)R->n + 1, target));
@@ -86,7 +87,12 @@ jn_status jn_autotune(jn_ctx* c, int32_t algo, const jn_table* R, const jn_table
     jn_tuning pick = base;
     for (const jn_tuning& t : cands) {
         c->tune = t;
-        const double ms = time_call(c, [&] { return jn_count(c, algo, R, S, pred, &cnt); }, &st);
+        double ms = 1e30;
+        for (int rep = 0; rep < 2; rep++) {  // the faster of two runs: host noise only adds time
+            const double x = time_call(c, [&] { return jn_count(c, algo, R, S, pred, &cnt); }, &st);
+            if (st != JN_OK) break;
+            ms = std::min(ms, x);
+        }
         if (st == JN_OK && ms < best_ms) {
             best_ms = ms;
             pick = t;

@@ -25,10 +25,29 @@
 
 namespace jnx {
 
-constexpr int HJ_T = 512;          // threads per join block
-constexpr int HJ_CAP = 4096;       // R rows per shared-memory table (int32 keys)
-constexpr int HJ_SCH = 2048;       // S rows per staged chunk
-constexpr int HJ_LGNB_MAX = 11;    // at most 2048 buckets
+// Join block shape (build-time knobs): threads, R rows per table, S rows per
+// staged chunk, most buckets, and blocks per SM the register budget allows.
+#ifndef JN_HJ_T
+#define JN_HJ_T 512
+#endif
+#ifndef JN_HJ_CAP
+#define JN_HJ_CAP 4096
+#endif
+#ifndef JN_HJ_SCH
+#define JN_HJ_SCH 2048
+#endif
+#ifndef JN_HJ_MINB
+#define JN_HJ_MINB 2
+#endif
+constexpr int HJ_T = JN_HJ_T;        // threads per join block
+constexpr int HJ_CAP = JN_HJ_CAP;    // R rows per shared-memory table (int32 keys)
+constexpr int HJ_SCH = JN_HJ_SCH;    // S rows per staged chunk
+constexpr int HJ_LGNB_MAX = [] {     // about two R rows per bucket: at most CAP / 2 buckets
+    int lg = 0;
+    while ((2 << lg) < HJ_CAP) lg++;
+    return lg;
+}();
+static_assert(4 * HJ_T >= (1 << HJ_LGNB_MAX), "the bucket scan covers four buckets per thread");
 constexpr int HJ_PAD = 16;         // rows of slack for 16-byte widened copies
 constexpr uint64_t CE_PAIRS = 1u << 16;  // cross-product pairs per work chunk
 
@@ -138,7 +157,7 @@ __device__ __forceinline__ uint32_t oa_slot(uint32_t h, int bits, int ts) {
 // The partitioned rows are library scratch, 16-byte aligned and padded by
 // HJ_PAD rows, so every widened copy stays inside its allocation.
 template <typename K, int MODE, bool MERGE = false>
-__global__ void __launch_bounds__(HJ_T, 2)
+__global__ void __launch_bounds__(HJ_T, JN_HJ_MINB)
 k_hash_join(const Row<K, false>* __restrict__ rrows, const Row<K, false>* __restrict__ srows,
             const Item* __restrict__ items, const uint64_t* __restrict__ nitems_p, int bits,
             unsigned long long* __restrict__ item_val,
@@ -765,6 +784,7 @@ jn_status run_hash(jn_ctx* c, const Cols<K>& R, const Cols<K>& S, int mode, OutP
     res->checksum = hc[1];
     info.result = total;
     info.heavy_keys = heavy ? (hc[3] & 0xffffffffu) : 0;
+    info.heavy_pairs = heavy_pairs;
     if (mode != MODE_EMIT) return JN_OK;
     // ---- 5. exact allocation and the emit pass ----
     JN_TRY(out_prepare(c, s, total, *plan));
@@ -980,6 +1000,8 @@ template jn_status batch_hash_prepare<int32_t>(jn_ctx*, int, const Cols<int32_t>
                                                std::unique_ptr<BatchRun>*);
 template jn_status batch_hash_prepare<int64_t>(jn_ctx*, int, const Cols<int64_t>*, const Cols<int64_t>*,
                                                std::unique_ptr<BatchRun>*);
+
+int hash_cap(int32_t key_type) { return key_type == JN_KEY_I32 ? cap_of<int32_t>() : cap_of<int64_t>(); }
 
 template jn_status run_hash<int32_t>(jn_ctx*, const Cols<int32_t>&, const Cols<int32_t>&, int,
                                      OutPlan*, RunResult*);

@@ -87,7 +87,11 @@ class RunInfo(ctypes.Structure):
                 ("work_items", ctypes.c_uint64), ("heavy_keys", ctypes.c_uint64),
                 ("kernel_launches", ctypes.c_uint64), ("prefilter", ctypes.c_int32),
                 ("radix_bits", ctypes.c_int32), ("radix_bits1", ctypes.c_int32),
-                ("filter_bits", ctypes.c_int32), ("reserved", ctypes.c_uint64 * 6)]
+                ("filter_bits", ctypes.c_int32), ("scratch_peak", ctypes.c_uint64),
+                ("heavy_pairs", ctypes.c_uint64), ("reserved", ctypes.c_uint64 * 4)]
+
+
+ADMIT_FN = ctypes.CFUNCTYPE(ctypes.c_int, ctypes.c_void_p, ctypes.c_uint64, ctypes.c_uint64)
 
 
 class Pair(ctypes.Structure):
@@ -139,6 +143,8 @@ _SIGS = {
     "jn_server_release": (ctypes.c_int, [_P, ctypes.c_uint64]),
     "jn_server_stats_get": (ctypes.c_int, [_P, ctypes.POINTER(ServerStats)]),
     "jn_set_profiling": (ctypes.c_int, [_P, ctypes.c_int32]),
+    "jn_set_memory_limit": (ctypes.c_int, [_P, ctypes.c_uint64]),
+    "jn_set_admission": (ctypes.c_int, [_P, _P, _P]),
     "jn_kernel_stats": (ctypes.c_int, [_P, ctypes.POINTER(KernelStat), ctypes.c_int32,
                                        ctypes.POINTER(ctypes.c_int32)]),
     "jn_reset_stats": (ctypes.c_int, [_P]),
@@ -215,6 +221,21 @@ class Context:
         t = Tuning()
         load().jn_get_tuning(self.handle, ctypes.byref(t))
         return {f: getattr(t, f) for f, _ in Tuning._fields_ if f != "reserved"}
+
+    def set_memory_limit(self, nbytes: int):
+        """Refuse (JN_ERR_OOM, after the exact count) runs whose output + scratch exceed nbytes."""
+        _check(self, load().jn_set_memory_limit(self.handle, nbytes))
+
+    def set_admission(self, fn):
+        """fn(out_bytes, scratch_bytes) -> status, called between the count and
+        the output allocation; None removes the hook."""
+        if fn is None:
+            self._admit = None
+            _check(self, load().jn_set_admission(self.handle, None, None))
+            return
+        cb = ADMIT_FN(lambda user, ob, sb: int(fn(int(ob), int(sb))))
+        self._admit = cb  # keeps the callback alive while the context holds it
+        _check(self, load().jn_set_admission(self.handle, ctypes.cast(cb, _P), None))
 
     def set_profiling(self, on: bool):
         _check(self, load().jn_set_profiling(self.handle, 1 if on else 0))
@@ -300,7 +321,7 @@ def _emit(ctx, fn, args, out):
         p = _P(out.data_ptr())
         cap = out.shape[0]
     st = fn(ctx.handle, *args, ctypes.byref(p), cap, ctypes.byref(n))
-    _check(ctx, st, required=int(n.value) if st == JN_ERR_CAPACITY else None)
+    _check(ctx, st, required=int(n.value) if st in (JN_ERR_CAPACITY, JN_ERR_OOM) else None)
     return _result(ctx, p, int(n.value), out)
 
 

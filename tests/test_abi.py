@@ -21,6 +21,7 @@ def lib_path():
 def header_functions():
     text = open(os.path.join(ROOT, "include", "jn.h")).read()
     text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    text = re.sub(r"typedef\s+\w+\s*\(\s*\*\s*\w+\s*\)\s*\([^)]*\)\s*;", "", text)  # function-pointer types
     names = re.findall(r"\b(jn_[a-z_0-9]+)\s*\(", text)
     return sorted(set(names))
 
