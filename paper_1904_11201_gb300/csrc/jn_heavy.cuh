@@ -106,15 +106,70 @@ __global__ void k_sample(const K* __restrict__ keys, int64_t n, int64_t stride, 
     }
 }
 
-// Picks keys whose sampled count (either side) reaches `thr`, at most HV_MAX
-// of them, into keys[0 .. *count).
+// Sampled counts are binned exactly below HV_CBINS - 1; the top bin holds
+// every larger count.
+constexpr int HV_CBINS = 4096;
+
+// Histogram of each sampled key's larger count (over the two sides), for
+// counts that reach `thr`.
 template <typename K>
-__global__ void k_heavy_collect(const K* __restrict__ tk, const unsigned int* __restrict__ tc, unsigned int thr,
-                                K* __restrict__ keys, int* __restrict__ count) {
+__global__ void k_heavy_hist(const K* __restrict__ tk, const unsigned int* __restrict__ tc, unsigned int thr,
+                             unsigned int* __restrict__ hist) {
+    __shared__ unsigned int sh[HV_CBINS];
+    for (int i = threadIdx.x; i < HV_CBINS; i += blockDim.x) sh[i] = 0;
+    __syncthreads();
     const int slots = 1 << HV_SAMPLE_LOG;
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < slots; i += gridDim.x * blockDim.x) {
         if (tk[i] == key_sentinel<K>()) continue;
-        if (tc[2 * i] >= thr || tc[2 * i + 1] >= thr) {
+        const unsigned int c = max(tc[2 * i], tc[2 * i + 1]);
+        if (c >= thr) atomicAdd(&sh[min(c, (unsigned int)HV_CBINS - 1)], 1u);
+    }
+    __syncthreads();
+    for (int i = threadIdx.x; i < HV_CBINS; i += blockDim.x)
+        if (sh[i]) atomicAdd(&hist[i], sh[i]);
+}
+
+// One warp: the smallest count t >= thr that at most HV_MAX sampled keys
+// reach, so the keys picked are the most frequent ones.
+static __global__ void k_heavy_thr(const unsigned int* __restrict__ hist, unsigned int thr, unsigned int* __restrict__ t_out) {
+    constexpr int PER = HV_CBINS / 32;
+    const int lane = threadIdx.x;
+    unsigned int part = 0;  // keys in this lane's bins
+    for (int j = 0; j < PER; j++) part += hist[lane * PER + j];
+    // keys in the bins of the lanes above this one
+    unsigned int above = 0;
+    for (int l = 31; l > 0; l--) {
+        const unsigned int v = __shfl_sync(0xffffffffu, part, l);
+        if (l > lane) above += v;
+    }
+    // the lane whose bins hold the crossing point finds it
+    unsigned int t = 0;
+    const bool cross = above <= (unsigned)HV_MAX && above + part > (unsigned)HV_MAX;
+    if (cross) {
+        unsigned int acc = above;
+        t = (unsigned int)(lane * PER + PER);
+        for (int j = PER - 1; j >= 0; j--) {
+            acc += hist[lane * PER + j];
+            if (acc > (unsigned)HV_MAX) break;
+            t = (unsigned int)(lane * PER + j);
+        }
+        if (t == (unsigned int)HV_CBINS) t = HV_CBINS - 1;  // the top bin alone holds more than HV_MAX keys
+    }
+    const unsigned int any = __ballot_sync(0xffffffffu, cross);
+    if (any) t = __shfl_sync(0xffffffffu, t, __ffs(any) - 1);
+    if (lane == 0) *t_out = max(any ? t : 0u, thr);
+}
+
+// Picks keys whose sampled count (the larger side) reaches *thr, at most
+// HV_MAX of them, into keys[0 .. *count).
+template <typename K>
+__global__ void k_heavy_collect(const K* __restrict__ tk, const unsigned int* __restrict__ tc,
+                                const unsigned int* __restrict__ thr_p, K* __restrict__ keys, int* __restrict__ count) {
+    const int slots = 1 << HV_SAMPLE_LOG;
+    const unsigned int thr = *thr_p;
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < slots; i += gridDim.x * blockDim.x) {
+        if (tk[i] == key_sentinel<K>()) continue;
+        if (max(tc[2 * i], tc[2 * i + 1]) >= thr) {
             const int at = atomicAdd(count, 1);
             if (at < HV_MAX) keys[at] = tk[i];
         }

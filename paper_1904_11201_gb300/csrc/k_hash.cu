@@ -666,9 +666,16 @@ jn_status run_hash(jn_ctx* c, const Cols<K>& R, const Cols<K>& S, int mode, OutP
         JN_TRY(launch(c, K_HEAVY_SAMPLE, k_sample_init<K>, dim3(256), dim3(256), 0, tk, tc, slots));
         JN_TRY(launch(c, K_HEAVY_SAMPLE, k_sample<K>, dim3(256), dim3(256), 0, R.key, R.n, sr, 0, tk, tc));
         JN_TRY(launch(c, K_HEAVY_SAMPLE, k_sample<K>, dim3(256), dim3(256), 0, S.key, S.n, ss, 1, tk, tc));
+        unsigned int *chist, *d_thr;
+        JN_TRY(s.get(&chist, HV_CBINS));
+        JN_TRY(s.get(&d_thr, 1));
+        JN_TRY(zero(c, chist, sizeof(unsigned int) * HV_CBINS));
         JN_TRY(zero(c, d_hcount, sizeof(int)));
+        JN_TRY(launch(c, K_HEAVY_SELECT, k_heavy_hist<K>, dim3(c->num_sms), dim3(1024), 0, (const K*)tk,
+                      (const unsigned int*)tc, thr, chist));
+        JN_TRY(launch(c, K_HEAVY_SELECT, k_heavy_thr, dim3(1), dim3(32), 0, (const unsigned int*)chist, thr, d_thr));
         JN_TRY(launch(c, K_HEAVY_SELECT, k_heavy_collect<K>, dim3(2 * c->num_sms), dim3(256), 0, (const K*)tk,
-                      (const unsigned int*)tc, thr, hkeys, d_hcount));
+                      (const unsigned int*)tc, (const unsigned int*)d_thr, hkeys, d_hcount));
         JN_TRY(launch(c, K_HEAVY_SELECT, k_heavy_table<K>, dim3(1), dim3(1024), 0, (const K*)hkeys, htk, htidx,
                       d_hcount));
         hs = HeavySet<K>{htk, htidx, hkeys, d_hcount};

@@ -355,3 +355,23 @@ def test_batch_capacity_and_empty(ctx):
     assert e.value.status == jn.JN_ERR_CAPACITY and e.value.required == m
     pairs, first, cnt = jn.jn_batch(ctx, joins)
     assert cnt == [m, 0]
+
+
+def test_heavy_keys_are_the_most_frequent(ctx):
+    # 3000 keys of 100 rows and one of 5000 rows on each side: more candidates
+    # than the heavy set holds, so the threshold rises and the largest key is
+    # taken (its 25M pairs go through the cross-product path)
+    base = torch.arange(3000, dtype=torch.int32).repeat_interleave(100)
+    big = torch.full((5000,), 7_777_777, dtype=torch.int32)
+    r = torch.cat([base, big])[datagen.uniform_int(305000, 0, 1 << 30, 41, 0, dtype=torch.int64).argsort()]
+    s = torch.cat([base, big])[datagen.uniform_int(305000, 0, 1 << 30, 41, 1, dtype=torch.int64).argsort()]
+    cnt, chk = O.equi_count_checksum(r.numpy(), s.numpy())
+    R, S = jn.table(r.to(DEV)), jn.table(s.to(DEV))
+    ctx.set_tuning(heavy=64)
+    try:
+        assert jn.jn_aggregate(ctx, jn.JN_ALGO_HASH, R, S) == (cnt, chk)
+        info = ctx.run_info()
+        assert info["heavy_keys"] <= 1024
+        assert info["heavy_pairs"] >= 5000 * 5000
+    finally:
+        ctx.set_tuning(heavy=-1)
