@@ -306,7 +306,18 @@ k_seg_hist_rows(const R* __restrict__ rows, const uint64_t* __restrict__ seg_beg
         const uint64_t off = (t - s_tp[seg]) * SC_TILE;
         const uint64_t beg = seg_begin[seg] + off;
         const int cnt = (int)min((uint64_t)SC_TILE, seg_count[seg] - off);
-        for (int i = threadIdx.x; i < cnt; i += blockDim.x) atomicAdd(&s_h[dg(rows[beg + i].key)], 1u);
+        // all of a thread's keys of the tile are loaded before the first count,
+        // so their loads are in flight together
+        constexpr int PER = SC_TILE / SC_T;
+        decltype(rows[0].key) k[PER];
+#pragma unroll
+        for (int j = 0; j < PER; j++) {
+            const int i = j * SC_T + threadIdx.x;
+            if (i < cnt) k[j] = rows[beg + i].key;
+        }
+#pragma unroll
+        for (int j = 0; j < PER; j++)
+            if (j * SC_T + (int)threadIdx.x < cnt) atomicAdd(&s_h[dg(k[j])], 1u);
     }
     __syncthreads();
     if (seg_held >= 0)

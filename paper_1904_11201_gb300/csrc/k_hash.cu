@@ -601,7 +601,7 @@ jn_status run_hash(jn_ctx* c, const Cols<K>& R, const Cols<K>& S, int mode, OutP
     }
     const jn_tuning& tu = c->tune;
     // ---- parameters ----
-    const bool heavy = tu.heavy >= 1 || (tu.heavy == -1 && nr + ns >= (1u << 20));
+    bool heavy = tu.heavy >= 1 || (tu.heavy == -1 && nr + ns >= (1u << 20));
     const int64_t heavy_rows = tu.heavy >= 2 ? tu.heavy : cap_of<K>() / 4;  // rows that make a key heavy
     bool pre = tu.prefilter == 1 || (tu.prefilter == -1 && nr + ns >= (1u << 22));
     int b = tu.radix_bits;
@@ -656,12 +656,13 @@ jn_status run_hash(jn_ctx* c, const Cols<K>& R, const Cols<K>& S, int mode, OutP
         JN_TRY(s.get(&hkeys, HV_MAX));
         JN_TRY(s.get(&htk, HV_SLOTS));
         JN_TRY(s.get(&htidx, HV_SLOTS));
-        JN_TRY(s.get(&d_hcount, 1));
+        JN_TRY(s.get(&d_hcount, 2));
         const int64_t target = 1 << 19;  // samples per table
         const int64_t sr = max((int64_t)1, (int64_t)nr / target), ss = max((int64_t)1, (int64_t)ns / target);
         // a key is heavy when about heavy_rows rows of one table carry it
-        const unsigned thr_r = (unsigned)max((int64_t)(sr > 1 ? 3 : 1), heavy_rows / sr);
-        const unsigned thr_s = (unsigned)max((int64_t)(ss > 1 ? 3 : 1), heavy_rows / ss);
+        // (at least 8 sampled rows when sampling, so chance repeats do not qualify)
+        const unsigned thr_r = (unsigned)max((int64_t)(sr > 1 ? 8 : 1), heavy_rows / sr);
+        const unsigned thr_s = (unsigned)max((int64_t)(ss > 1 ? 8 : 1), heavy_rows / ss);
         const unsigned thr = thr_r < thr_s ? thr_r : thr_s;
         JN_TRY(launch(c, K_HEAVY_SAMPLE, k_sample_init<K>, dim3(256), dim3(256), 0, tk, tc, slots));
         JN_TRY(launch(c, K_HEAVY_SAMPLE, k_sample<K>, dim3(256), dim3(256), 0, R.key, R.n, sr, 0, tk, tc));
@@ -670,7 +671,7 @@ jn_status run_hash(jn_ctx* c, const Cols<K>& R, const Cols<K>& S, int mode, OutP
         JN_TRY(s.get(&chist, HV_CBINS));
         JN_TRY(s.get(&d_thr, 1));
         JN_TRY(zero(c, chist, sizeof(unsigned int) * HV_CBINS));
-        JN_TRY(zero(c, d_hcount, sizeof(int)));
+        JN_TRY(zero(c, d_hcount, 2 * sizeof(int)));
         JN_TRY(launch(c, K_HEAVY_SELECT, k_heavy_hist<K>, dim3(c->num_sms), dim3(1024), 0, (const K*)tk,
                       (const unsigned int*)tc, thr, chist));
         JN_TRY(launch(c, K_HEAVY_SELECT, k_heavy_thr, dim3(1), dim3(32), 0, (const unsigned int*)chist, thr, d_thr));
@@ -679,7 +680,13 @@ jn_status run_hash(jn_ctx* c, const Cols<K>& R, const Cols<K>& S, int mode, OutP
         JN_TRY(launch(c, K_HEAVY_SELECT, k_heavy_table<K>, dim3(1), dim3(1024), 0, (const K*)hkeys, htk, htidx,
                       d_hcount));
         hs = HeavySet<K>{htk, htidx, hkeys, d_hcount};
-        if (pre) JN_TRY(launch(c, K_HEAVY_SELECT, k_heavy_bits<K>, dim3(1), dim3(1024), 0, hs, bmR, bmS, fmask));
+        uint64_t hcw = 0;
+        JN_TRY(read_back(c, reinterpret_cast<const uint64_t*>(d_hcount), &hcw, 1));
+        if ((hcw & 0xffffffffu) == 0) {
+            heavy = false;  // no frequent key: the plain path
+        } else if (pre) {
+            JN_TRY(launch(c, K_HEAVY_SELECT, k_heavy_bits<K>, dim3(1), dim3(1024), 0, hs, bmR, bmS, fmask));
+        }
     }
     // ---- 1. presence bitmaps + first-pass histograms ----
     Partitioned<K> PR, PS;
