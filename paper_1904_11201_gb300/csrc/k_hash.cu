@@ -26,7 +26,7 @@
 namespace jnx {
 
 // Join block shape (build-time knobs): threads, R rows per table, S rows per
-// staged chunk, most buckets, and blocks per SM the register budget allows.
+// staged chunk, and blocks per SM the register budget allows.
 #ifndef JN_HJ_T
 #define JN_HJ_T 512
 #endif
@@ -34,7 +34,7 @@ namespace jnx {
 #define JN_HJ_CAP 4096
 #endif
 #ifndef JN_HJ_SCH
-#define JN_HJ_SCH 2048
+#define JN_HJ_SCH 1536
 #endif
 #ifndef JN_HJ_MINB
 #define JN_HJ_MINB 2
@@ -42,12 +42,7 @@ namespace jnx {
 constexpr int HJ_T = JN_HJ_T;        // threads per join block
 constexpr int HJ_CAP = JN_HJ_CAP;    // R rows per shared-memory table (int32 keys)
 constexpr int HJ_SCH = JN_HJ_SCH;    // S rows per staged chunk
-constexpr int HJ_LGNB_MAX = [] {     // about two R rows per bucket: at most CAP / 2 buckets
-    int lg = 0;
-    while ((2 << lg) < HJ_CAP) lg++;
-    return lg;
-}();
-static_assert(4 * HJ_T >= (1 << HJ_LGNB_MAX), "the bucket scan covers four buckets per thread");
+
 constexpr int HJ_PAD = 16;         // rows of slack for 16-byte widened copies
 constexpr uint64_t CE_PAIRS = 1u << 16;  // cross-product pairs per work chunk
 
@@ -65,17 +60,6 @@ __global__ void k_items(const uint64_t* __restrict__ roff, const uint64_t* __res
 template <typename K>
 __host__ __device__ constexpr int cap_of() {
     return sizeof(K) == 4 ? HJ_CAP : HJ_CAP / 2;
-}
-
-__device__ __forceinline__ int bucket_bits(int rn) {
-    int lg = 0;
-    while ((1 << lg) < rn) lg++;
-    lg -= 1;  // about two rows per bucket
-    return lg < 0 ? 0 : (lg > HJ_LGNB_MAX ? HJ_LGNB_MAX : lg);
-}
-
-__device__ __forceinline__ uint32_t bucket_of(uint32_t h, int bits, int lg) {
-    return lg == 0 ? 0u : ((h << bits) >> (32 - lg));
 }
 
 // One work item: rows [rbeg, rbeg + rn) of R against all rows
@@ -118,6 +102,15 @@ __device__ __forceinline__ uint32_t span_off(uint64_t beg) {
     return (uint32_t)(beg * sizeof(R) - ((beg * sizeof(R)) & ~15ull));
 }
 
+// Emit-mode slot of the open-addressing table: a key and, packed in one
+// word, its multiplicity (high half) and the cursor of its payload run (low
+// half), so one load gives the key, the count and where its payloads sit.
+template <typename K>
+struct alignas(2 * sizeof(K)) RunSlot {
+    K key;
+    uint32_t packed;
+};
+
 // Shared-memory layout of the join kernel (bytes), shared by host and device.
 template <typename K, int MODE>
 struct JoinSmem {
@@ -125,13 +118,15 @@ struct JoinSmem {
     static constexpr int CAP = cap_of<K>();
     static constexpr int GR = CAP + 32 / (int)sizeof(R) + 2;     // staged R rows (widened span)
     static constexpr int GS = HJ_SCH + 32 / (int)sizeof(R) + 2;  // staged S rows per buffer
-    static constexpr int TS = (CAP * 5) / 4;                     // open-addressing slots (count modes)
+    static constexpr int TS = (CAP * 5) / 4;                     // open-addressing slots
     static constexpr size_t STAGE = (size_t)(GR + 2 * GS) * sizeof(R);
+    // emit: TS slots and one for the sentinel key, then the payloads grouped by slot
     static constexpr size_t TABLE =
-        MODE == MODE_EMIT ? (size_t)CAP * (sizeof(K) + 4) + 4u * (1u << HJ_LGNB_MAX)
+        MODE == MODE_EMIT ? (size_t)(TS + 1) * sizeof(RunSlot<K>) + (size_t)CAP * 4
                           : (size_t)TS * (sizeof(K) + 4) + (MODE == MODE_AGG ? (size_t)TS * 8 : 0);
     static constexpr size_t BYTES = STAGE + TABLE;
 };
+static_assert(cap_of<int32_t>() < (1 << 16), "run cursors and counts fit half a word");
 
 // Slot of a key in the open-addressing table of a partition: the hash bits
 // below the partition bits, spread over TS slots.
@@ -149,8 +144,9 @@ __device__ __forceinline__ uint32_t oa_slot(uint32_t h, int bits, int ts) {
 // chunks are staged in shared memory by TMA bulk copies: the next item's R
 // rows load while this item probes, and S chunks stream through two buffers,
 // the next chunk loading while the current one is probed.
-//   emit:         R is counting-sorted into buckets (key, payload) and every
-//                 match is written;
+//   emit:         each distinct R key gets one slot holding its multiplicity
+//                 and the run of its payloads in a slot-grouped array, so a
+//                 match is one lookup and a contiguous copy;
 //   count / agg:  equal R keys are folded into one open-addressing slot
 //                 (key, multiplicity [, sum of f]), so a probe costs one
 //                 lookup however many rows share the key.
@@ -172,10 +168,10 @@ k_hash_join(const Row<K, false>* __restrict__ rrows, const Row<K, false>* __rest
     unsigned char* g_s0 = g_r + L::GR * sizeof(R);
     unsigned char* g_s1 = g_s0 + L::GS * sizeof(R);
     unsigned char* tab = g_s1 + L::GS * sizeof(R);
-    // emit table
-    K* s_key = reinterpret_cast<K*>(tab);
-    int32_t* s_pay = reinterpret_cast<int32_t*>(s_key + CAP);
-    uint32_t* s_off = reinterpret_cast<uint32_t*>(s_pay + CAP);
+    // emit table: slots (slot TS holds the sentinel key) and slot-grouped payloads
+    RunSlot<K>* e_tab = reinterpret_cast<RunSlot<K>*>(tab);
+    int32_t* s_pay = reinterpret_cast<int32_t*>(e_tab + TS + 1);
+    constexpr int PER = (TS + 1 + HJ_T - 1) / HJ_T;  // slots per thread in the run-start scan
     // count-mode table
     K* o_key = reinterpret_cast<K*>(tab);
     uint32_t* o_cnt = reinterpret_cast<uint32_t*>(o_key + TS);
@@ -237,11 +233,11 @@ k_hash_join(const Row<K, false>* __restrict__ rrows, const Row<K, false>* __rest
         Item dn;
         if (has_next) dn = items[itn];  // its R rows load once this item's R staging is free
         const int rn = d.rn;
-        int lg = 0, nb = 1;
         if (MODE == MODE_EMIT) {
-            lg = bucket_bits(rn);
-            nb = 1 << lg;
-            for (int i = threadIdx.x; i < nb; i += HJ_T) s_off[i] = 0;
+            for (int i = threadIdx.x; i <= TS; i += HJ_T) {
+                e_tab[i].key = KMIN;
+                e_tab[i].packed = 0;
+            }
         } else {
             for (int i = threadIdx.x; i < TS; i += HJ_T) {
                 o_key[i] = KMIN;
@@ -261,34 +257,88 @@ k_hash_join(const Row<K, false>* __restrict__ rrows, const Row<K, false>* __rest
         r_pending = false;
         const R* rrow = reinterpret_cast<const R*>(g_r + span_off<R>(d.rbeg));
         if (MODE == MODE_EMIT) {
-            // ---- build: counting sort of the staged R chunk by bucket ----
-            for (int i = threadIdx.x; i < rn; i += HJ_T)
-                atomicAdd(&s_off[bucket_of(khash(rrow[i].key), bits, lg)], 1u);
-            __syncthreads();
-            uint32_t v[4];
-            uint32_t sum = 0;
-#pragma unroll
-            for (int j = 0; j < 4; j++) {
-                const int i = threadIdx.x * 4 + j;
-                v[j] = i < nb ? s_off[i] : 0u;
-                sum += v[j];
+            // ---- build: one slot per distinct key, then its payloads as one run ----
+            // MERGE (skewed input): lanes of a warp holding the same key update
+            // their slot once, to spare contended shared atomics
+            const int rnw = MERGE ? (rn + 31) & ~31 : rn;
+            for (int i = threadIdx.x; i < rnw; i += HJ_T) {
+                const bool in = i < rn;
+                R x;
+                x.key = KMIN;
+                x.pay = 0;
+                if (in) x = rrow[i];
+                uint32_t cnt = 1;
+                if (MERGE) {
+                    const unsigned act = __ballot_sync(0xffffffffu, in);
+                    if (!in) continue;
+                    const unsigned peers = __match_any_sync(act, x.key);
+                    if (lane != __ffs(peers) - 1) continue;
+                    cnt = __popc(peers);
+                }
+                uint32_t h = TS;  // the sentinel key keeps its own slot
+                if (x.key != KMIN) {
+                    h = oa_slot(khash(x.key), bits, TS);
+                    for (int probe = 0; probe < TS; probe++) {
+                        K old;
+                        if (sizeof(K) == 4)
+                            old = (K)atomicCAS(reinterpret_cast<int*>(&e_tab[h].key), (int)KMIN, (int)x.key);
+                        else
+                            old = (K)atomicCAS(reinterpret_cast<unsigned long long*>(&e_tab[h].key),
+                                               (unsigned long long)KMIN, (unsigned long long)x.key);
+                        if (old == KMIN || old == x.key) break;
+                        h = (h + 1 == (uint32_t)TS) ? 0u : h + 1;
+                    }
+                }
+                atomicAdd(&e_tab[h].packed, cnt << 16);
             }
-            uint32_t tot;
-            uint32_t pre = block_excl_scan(sum, tmp32, &tot);
+            __syncthreads();
+            // run starts: exclusive scan of the slot counts into the low halves
+            {
+                const int i0 = threadIdx.x * PER;
+                uint32_t sum = 0;
 #pragma unroll
-            for (int j = 0; j < 4; j++) {
-                const int i = threadIdx.x * 4 + j;
-                if (i < nb) s_off[i] = pre;
-                pre += v[j];
+                for (int k = 0; k < PER; k++)
+                    if (i0 + k <= TS) sum += e_tab[i0 + k].packed >> 16;
+                uint32_t tot;
+                uint32_t pre = block_excl_scan(sum, tmp32, &tot);
+#pragma unroll
+                for (int k = 0; k < PER; k++)
+                    if (i0 + k <= TS) {
+                        const uint32_t p = e_tab[i0 + k].packed;
+                        e_tab[i0 + k].packed = p + pre;
+                        pre += p >> 16;
+                    }
             }
             __syncthreads();
-            for (int i = threadIdx.x; i < rn; i += HJ_T) {
-                const R x = rrow[i];
-                const uint32_t pos = atomicAdd(&s_off[bucket_of(khash(x.key), bits, lg)], 1u);
-                s_key[pos] = x.key;
+            // payloads into their runs; each cursor ends at its run's end
+            for (int i = threadIdx.x; i < rnw; i += HJ_T) {
+                const bool in = i < rn;
+                R x;
+                x.key = KMIN;
+                x.pay = 0;
+                if (in) x = rrow[i];
+                uint32_t h = TS;
+                if (in && x.key != KMIN) {
+                    h = oa_slot(khash(x.key), bits, TS);
+                    for (int probe = 0; probe < TS && e_tab[h].key != x.key; probe++)
+                        h = (h + 1 == (uint32_t)TS) ? 0u : h + 1;
+                }
+                uint32_t pos;
+                if (MERGE) {
+                    const unsigned act = __ballot_sync(0xffffffffu, in);
+                    if (!in) continue;
+                    const unsigned peers = __match_any_sync(act, x.key);
+                    const int leader = __ffs(peers) - 1;
+                    uint32_t b0 = 0;
+                    if (lane == leader) b0 = atomicAdd(&e_tab[h].packed, (uint32_t)__popc(peers));
+                    b0 = __shfl_sync(peers, b0, leader);
+                    pos = (b0 & 0xffffu) + __popc(peers & ((1u << lane) - 1));
+                } else {
+                    if (!in) continue;
+                    pos = atomicAdd(&e_tab[h].packed, 1u) & 0xffffu;
+                }
                 s_pay[pos] = x.pay;
             }
-            // bucket b now holds rows [b ? s_off[b-1] : 0, s_off[b])
         } else {
             // ---- build: fold equal keys into one slot (key, count [, sum f]) ----
             // MERGE (skewed input): lanes of a warp holding the same key insert
@@ -344,6 +394,7 @@ k_hash_join(const Row<K, false>* __restrict__ rrows, const Row<K, false>* __rest
         r_pending = has_next;
         // ---- probe with every S chunk of the partition ----
         unsigned long long acc = 0, csum = 0;
+        const uint64_t ibase = MODE == MODE_EMIT ? item_off[it] : 0;
         const int nsc = (d.sn + HJ_SCH - 1) / HJ_SCH;
         for (int sc = 0; sc < nsc; sc++) {
             const uint32_t b = qc & 1, ph = (qc >> 1) & 1;
@@ -360,16 +411,28 @@ k_hash_join(const Row<K, false>* __restrict__ rrows, const Row<K, false>* __rest
                 R x;
                 x.key = 0;
                 x.pay = 0;
-                uint32_t m = 0;
+                uint32_t m = 0, beg = 0;
                 unsigned long long fs = 0;
-                uint32_t lo = 0, hi = 0;
                 if (j < sn) {
                     x = srow[j];
                     if (MODE == MODE_EMIT) {
-                        const uint32_t bk = bucket_of(khash(x.key), bits, lg);
-                        lo = bk ? s_off[bk - 1] : 0u;
-                        hi = s_off[bk];
-                        for (uint32_t e = lo; e < hi; e++) m += (s_key[e] == x.key);
+                        uint32_t p = 0;
+                        if (x.key == KMIN) {
+                            p = e_tab[TS].packed;
+                        } else {
+                            uint32_t h = oa_slot(khash(x.key), bits, TS);
+                            for (int probe = 0; probe < TS; probe++) {
+                                const RunSlot<K> t = e_tab[h];
+                                if (t.key == x.key) {
+                                    p = t.packed;
+                                    break;
+                                }
+                                if (t.key == KMIN) break;
+                                h = (h + 1 == (uint32_t)TS) ? 0u : h + 1;
+                            }
+                        }
+                        m = p >> 16;
+                        beg = (p & 0xffffu) - m;
                     } else if (x.key == KMIN) {
                         m = s_mincnt;
                         if (MODE == MODE_AGG) fs = s_minf;
@@ -393,40 +456,20 @@ k_hash_join(const Row<K, false>* __restrict__ rrows, const Row<K, false>* __rest
                     uint32_t base = 0;
                     if (lane == 0 && wt) base = atomicAdd(&s_cursor, wt);
                     base = __shfl_sync(0xffffffffu, base, 0);
-                    const uint64_t wbase = item_off[it] + base;
-                    // long buckets are written by the whole warp, 32 entries at a
-                    // time, so their pairs go out in coalesced runs
-                    const bool longb = (hi - lo) > 32;
-                    if (m && !longb) {
-                        uint64_t o = wbase + (incl - m);
-                        for (uint32_t e = lo; e < hi; e++) {
-                            if (s_key[e] == x.key) {
-                                jn_pair q;
-                                q.r = s_pay[e];
-                                q.s = x.pay;
-                                out[o++] = q;
-                            }
-                        }
-                    }
-                    for (unsigned lanes = __ballot_sync(0xffffffffu, m && longb); lanes; lanes &= lanes - 1) {
+                    const uint64_t o = ibase + base + (incl - m);
+                    // a short run is written by its lane (the lanes' first pairs
+                    // are neighbours and go out together); a long run by the
+                    // whole warp, 32 pairs at a time
+                    const bool longr = m > 4;
+                    if (!longr)
+                        for (uint32_t i = 0; i < m; i++) out[o + i] = jn_pair{s_pay[beg + i], x.pay};
+                    for (unsigned lanes = __ballot_sync(0xffffffffu, longr); lanes; lanes &= lanes - 1) {
                         const int src = __ffs(lanes) - 1;
-                        const uint32_t blo = __shfl_sync(0xffffffffu, lo, src);
-                        const uint32_t bhi = __shfl_sync(0xffffffffu, hi, src);
-                        const K bk = __shfl_sync(0xffffffffu, x.key, src);
+                        const uint32_t bm = __shfl_sync(0xffffffffu, m, src);
+                        const uint32_t bb = __shfl_sync(0xffffffffu, beg, src);
                         const int32_t bp = __shfl_sync(0xffffffffu, x.pay, src);
-                        uint64_t o = wbase + __shfl_sync(0xffffffffu, incl - m, src);
-                        for (uint32_t e0 = blo; e0 < bhi; e0 += 32) {
-                            const uint32_t e = e0 + lane;
-                            const bool hit = e < bhi && s_key[e] == bk;
-                            const unsigned hm = __ballot_sync(0xffffffffu, hit);
-                            if (hit) {
-                                jn_pair q;
-                                q.r = s_pay[e];
-                                q.s = bp;
-                                out[o + __popc(hm & ((1u << lane) - 1))] = q;
-                            }
-                            o += __popc(hm);
-                        }
+                        const uint64_t bo = __shfl_sync(0xffffffffu, o, src);
+                        for (uint32_t i = lane; i < bm; i += 32) out[bo + i] = jn_pair{s_pay[bb + i], bp};
                     }
                 } else {
                     acc += m;
@@ -803,7 +846,7 @@ jn_status run_hash(jn_ctx* c, const Cols<K>& R, const Cols<K>& S, int mode, OutP
     // ---- 5. exact allocation and the emit pass ----
     JN_TRY(out_prepare(c, s, total, *plan));
     if (normal > 0) {
-        auto ke = k_hash_join<K, MODE_EMIT>;
+        auto ke = skewed ? k_hash_join<K, MODE_EMIT, true> : k_hash_join<K, MODE_EMIT, false>;
         const size_t sme = hash_smem<K>(MODE_EMIT);
         const int ge = (int)min((uint64_t)persistent_grid(c, (const void*)ke, HJ_T, sme), nitems);
         JN_TRY(launch(c, K_HASH_EMIT, ke, dim3(ge), dim3(HJ_T), sme, (const RW*)PR.rows, (const RW*)PS.rows,
