@@ -361,7 +361,7 @@ struct ScatterSmem {
                ~(size_t)127;
     }
     __host__ __device__ static constexpr size_t bytes() {
-        return staging_bytes() + (size_t)SC_TILE * sizeof(R) + (size_t)SC_TILE * 2 + (size_t)SC_FMAX * 16;
+        return staging_bytes() + (size_t)SC_TILE * sizeof(R) + (size_t)SC_FMAX * 16;
     }
 };
 
@@ -449,8 +449,7 @@ k_scatter(PartIn<K, HB> in, const uint64_t* __restrict__ seg_begin, const uint64
     extern __shared__ __align__(128) unsigned char smem[];
     unsigned char* stage = smem;
     R* s_row = reinterpret_cast<R*>(smem + SM::staging_bytes());
-    uint16_t* s_dig = reinterpret_cast<uint16_t*>(s_row + SC_TILE);
-    uint32_t* s_cnt = reinterpret_cast<uint32_t*>(s_dig + SC_TILE);
+    uint32_t* s_cnt = reinterpret_cast<uint32_t*>(s_row + SC_TILE);
     uint32_t* s_start = s_cnt + SC_FMAX;
     unsigned long long* s_delta = reinterpret_cast<unsigned long long*>(s_start + SC_FMAX);
     __shared__ uint32_t tmp[33];
@@ -569,11 +568,15 @@ k_scatter(PartIn<K, HB> in, const uint64_t* __restrict__ seg_begin, const uint64
             if (dd[j] != SC_DROP) {
                 const uint32_t pos = s_start[dd[j]] + rk[j];
                 s_row[pos] = v[j];
-                s_dig[pos] = (uint16_t)dd[j];
             }
         }
         __syncthreads();
-        for (uint32_t pos = threadIdx.x; pos < total; pos += SC_T) out[s_delta[s_dig[pos]] + pos] = s_row[pos];
+        // a staged row's digit is recomputed from its key (cheaper than
+        // keeping it in shared memory next to the row)
+        for (uint32_t pos = threadIdx.x; pos < total; pos += SC_T) {
+            const R x = s_row[pos];
+            out[s_delta[dg(x.key)] + pos] = x;
+        }
         for (int i = threadIdx.x; i < nd; i += SC_T) s_cnt[i] = 0;
         __syncthreads();
         cur ^= 1;
