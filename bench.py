@@ -690,6 +690,8 @@ def main():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-autotune", action="store_true", help="keep the library's default tuning")
+    ap.add_argument("--host-io", type=int, default=0,
+                    help="e2e: 0 copy host buffers, 1 read inputs in place, 2 write pairs in place, 3 both")
     ap.add_argument("--batch-count", type=int, default=4096, help="batch workload: number of joins")
     ap.add_argument("--serve-requests", type=int, default=10000, help="serve workload: requests per stream")
     ap.add_argument("--serve-slots", type=int, default=4, help="serve workload: server worker slots")
@@ -835,6 +837,8 @@ def main():
         hs = tuple(None if t is None else t.cpu().pin_memory() for t in w["S"])
         HR, HS = jn.table(*hr), jn.table(*hs)
         hout = torch.empty((m, 2), dtype=torch.int32).pin_memory()
+        if args.host_io:
+            ctx.set_tuning(host_io=args.host_io)
         run_step(jn, ctx, w, HR, HS, out=hout)  # warm-up of the staging path
         torch.cuda.synchronize()
         barrier(world)
@@ -846,7 +850,7 @@ def main():
         te = max_over_ranks(te, world, dev)
         hb = sum(t.numel() * t.element_size() for t in hr + hs if t is not None)
         e2e = {"value": world * units / te, "unit": "tuples/s", "h2d_bytes_per_step": hb,
-               "d2h_bytes_per_step": 8 * m, "ms_per_step": te * 1e3}
+               "d2h_bytes_per_step": 8 * m, "ms_per_step": te * 1e3, "host_io": args.host_io}
         del got, hout, hr, hs
 
     cb = cb_all = None

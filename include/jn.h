@@ -99,7 +99,10 @@ typedef struct {
     int32_t nlj_tile_r;    /* R rows per nested-loop tile (0 = auto; multiple of 256)   */
     int32_t graphs;        /* 1: jn_batch captures and replays its phases as CUDA graphs */
     int32_t part_rows;     /* jn_batch: R rows per partition of an equi-join (0 = auto)  */
-    int32_t reserved[7];
+    int32_t host_io;       /* page-locked host buffers: bit 0 = the hash join reads its
+                              input columns in place, bit 1 = emitted pairs are written in
+                              place; otherwise copied (0 = copy both)                  */
+    int32_t reserved[6];
 } jn_tuning;
 
 /* Per-kernel launch statistics (profiling mode). */

@@ -17,6 +17,7 @@ struct Cols {
     const K* key2;
     const int32_t* pay;  // NULL = row index
     int64_t n;
+    bool host = false;   // columns read in place from page-locked host memory
 };
 
 // Where the pairs of an emitting run go (see jn.h's output convention).
@@ -25,8 +26,9 @@ struct OutPlan {
     uint64_t capacity = 0;
     uint64_t* n_out = nullptr;
     jn_pair* dev = nullptr;      // device buffer the kernels write
-    bool host_copy = false;      // caller buffer is host memory
+    bool host_copy = false;      // caller buffer is host memory, filled by a copy
     bool lib_alloc = false;      // library allocated the result
+    bool mapped = false;         // caller buffer is page-locked host memory written in place
 };
 
 // Sizes the output for `m` pairs (allocating or checking the caller buffer).

@@ -28,8 +28,11 @@ jn_status out_prepare(jn_ctx* c, Scratch& s, uint64_t m, OutPlan& plan) {
     jn_pair* user = *plan.user_out;
     plan.host_copy = false;
     plan.lib_alloc = false;
+    const jn_pair* mapped =
+        user && (c->tune.host_io & 2) ? static_cast<const jn_pair*>(host_mapped(user)) : nullptr;
     {
-        const bool dev_out = user != nullptr && (m == 0 || m > plan.capacity || is_device_pointer(user));
+        const bool dev_out =
+            user != nullptr && (m == 0 || m > plan.capacity || mapped || is_device_pointer(user));
         JN_TRY(admit(c, m, dev_out ? 0 : m * sizeof(jn_pair), plan));
     }
     if (user == nullptr) {
@@ -50,11 +53,17 @@ jn_status out_prepare(jn_ctx* c, Scratch& s, uint64_t m, OutPlan& plan) {
         plan.dev = user;
         return JN_OK;
     }
+    if (mapped) {  // page-locked host memory: the kernels write the pairs in place
+        plan.dev = const_cast<jn_pair*>(mapped);
+        plan.mapped = true;
+        return JN_OK;
+    }
     plan.host_copy = true;
     return s.get(&plan.dev, m);
 }
 
 jn_status out_finish(jn_ctx* c, uint64_t m, OutPlan& plan) {
+    if (plan.mapped && m > 0) JN_CUDA(c, cudaStreamSynchronize(c->stream));  // pairs visible to the host
     if (plan.host_copy && m > 0) {
         JN_CUDA(c, cudaMemcpyAsync(*plan.user_out, plan.dev, m * sizeof(jn_pair), cudaMemcpyDeviceToHost,
                                    c->stream));
@@ -81,12 +90,23 @@ static jn_status check_table(jn_ctx* c, const jn_table* t, const char* name, boo
 static bool valid_op(int op) { return op >= JN_EQ && op <= JN_ANY; }
 
 template <typename K>
-static jn_status stage(jn_ctx* c, Scratch& s, const jn_table* t, bool use_key2, Cols<K>* out) {
+static jn_status stage(jn_ctx* c, Scratch& s, const jn_table* t, bool use_key2, Cols<K>* out,
+                       bool in_place = false) {
     const size_t kb = (size_t)t->n * sizeof(K);
     const void *k = nullptr, *k2 = nullptr, *p = nullptr;
-    JN_TRY(device_column(c, s, t->key, kb, &k));
-    if (use_key2 && t->key2) JN_TRY(device_column(c, s, t->key2, kb, &k2));
-    if (t->payload) JN_TRY(device_column(c, s, t->payload, (size_t)t->n * 4, &p));
+    // a path that reads each column in a couple of streaming passes reads
+    // page-locked host columns in place instead of copying them first
+    const void* mk = in_place ? host_mapped(t->key) : nullptr;
+    const void* mp = in_place && t->payload ? host_mapped(t->payload) : nullptr;
+    out->host = mk && (mp || !t->payload) && !(use_key2 && t->key2);
+    if (out->host) {
+        k = mk;
+        p = mp;
+    } else {
+        JN_TRY(device_column(c, s, t->key, kb, &k));
+        if (use_key2 && t->key2) JN_TRY(device_column(c, s, t->key2, kb, &k2));
+        if (t->payload) JN_TRY(device_column(c, s, t->payload, (size_t)t->n * 4, &p));
+    }
     out->key = static_cast<const K*>(k);
     out->key2 = static_cast<const K*>(k2);
     out->pay = static_cast<const int32_t*>(p);
@@ -100,8 +120,10 @@ static jn_status dispatch(jn_ctx* c, int algo, const jn_table* R, const jn_table
     Scratch s(c);
     Cols<K> r, q;
     const bool use2 = algo != JN_ALGO_HASH;
-    JN_TRY(stage<K>(c, s, R, use2, &r));
-    JN_TRY(stage<K>(c, s, S, use2, &q));
+    // the hash join samples a column, then reads it in two streaming passes
+    const bool in_place = algo == JN_ALGO_HASH && (c->tune.host_io & 1);
+    JN_TRY(stage<K>(c, s, R, use2, &r, in_place));
+    JN_TRY(stage<K>(c, s, S, use2, &q, in_place));
     switch (algo) {
         case JN_ALGO_HASH: return run_hash<K>(c, r, q, mode, plan, res);
         case JN_ALGO_NLJ: return run_nlj<K>(c, r, q, pr, mode, plan, res);

@@ -165,6 +165,9 @@ jn_status scan_u64(jn_ctx* c, const uint64_t* in, uint64_t* out, int64_t n);
 // Host-side column staging: returns a device pointer for a column that may
 // be host memory (copied into scratch) or device memory (returned as is).
 jn_status device_column(jn_ctx* c, Scratch& s, const void* p, size_t bytes, const void** dp);
+// Device address of page-locked host memory the kernels may read and write
+// in place (over the CPU-GPU link), or NULL for any other pointer.
+const void* host_mapped(const void* p);
 bool is_device_pointer(const void* p);
 
 // ------------------------------------------------------------- helpers --

@@ -272,6 +272,7 @@ struct PartIn {
     uint64_t rows_ok;       // rows that may be read (allocation size)
     const SegCols<K>* segs; // batches: per-segment columns (key, pay), else NULL
     const TileRef* tiles;   // batches: tile list, else NULL (tiles from the segment prefix)
+    bool plain = false;     // columns in page-locked host memory: plain loads, no bulk copies
 };
 
 // Digit histogram of every segment of a row array (see k_seg_hist).
@@ -414,6 +415,7 @@ __device__ __forceinline__ void scatter_issue(TileDesc* d, const PartIn<K, HB>& 
         tma_load_1d(stage, reinterpret_cast<const unsigned char*>(in.rows) + b0, nb, bar);
         return;
     }
+    if (in.plain) return;
     const K* ikey = in.segs ? in.segs[d->seg].key : in.key;
     const K* ikb = in.segs ? in.segs[d->seg].key_b : in.key_b;
     const int32_t* ipay = in.segs ? in.segs[d->seg].pay : in.pay;

@@ -102,6 +102,15 @@ bool is_device_pointer(const void* p) {
     return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
 }
 
+const void* host_mapped(const void* p) {
+    cudaPointerAttributes a;
+    if (!p || cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+        cudaGetLastError();
+        return nullptr;
+    }
+    return a.type == cudaMemoryTypeHost ? a.devicePointer : nullptr;
+}
+
 jn_status device_column(jn_ctx* c, Scratch& s, const void* p, size_t bytes, const void** dp) {
     if (p == nullptr || bytes == 0 || is_device_pointer(p)) {
         *dp = p;
@@ -347,7 +356,8 @@ jn_status jn_set_tuning(jn_ctx* c, const jn_tuning* t) {
     }
     if (t->radix_bits < 0 || t->radix_bits > 20 || t->radix_bits1 < 0 || t->radix_bits1 > 10 ||
         t->filter_bits < 0 || t->filter_bits > 30 || t->theta_groups < 0 || t->theta_groups > 10 ||
-        t->nlj_tile_r < 0 || (t->nlj_tile_r % 256) != 0 || t->nlj_tile_r > 4096 || t->part_rows < 0)
+        t->nlj_tile_r < 0 || (t->nlj_tile_r % 256) != 0 || t->nlj_tile_r > 4096 || t->part_rows < 0 ||
+        t->host_io < 0 || t->host_io > 3)
         return fail(c, JN_ERR_INVALID, "tuning value out of range");
     c->tune = *t;
     return JN_OK;

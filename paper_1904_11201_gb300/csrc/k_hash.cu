@@ -559,7 +559,7 @@ static jn_status partition_table(jn_ctx* c, Scratch& s, const Cols<K>& T, int b1
     const size_t sm = scatter_smem<K, false>();
     auto kern1 = other_bitmap ? k_scatter<K, false, true, D1> : k_scatter<K, false, false, D1>;
     const int g1 = persistent_grid(c, (const void*)kern1, SC_T, sm);
-    PartIn<K, false> in1{T.key, nullptr, T.pay, nullptr, n, nullptr, nullptr};
+    PartIn<K, false> in1{T.key, nullptr, T.pay, nullptr, n, nullptr, nullptr, T.host};
     JN_TRY(launch(c, K_SCATTER, kern1, dim3(g1), dim3(SC_T), sm, in1, (const uint64_t*)seg_b,
                   (const uint64_t*)seg_c, (const uint64_t*)tp, 1, d1, nd1, other_bitmap, fmask, cur1, r1,
                   c->d_err));

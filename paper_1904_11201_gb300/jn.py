@@ -48,7 +48,8 @@ class Tuning(ctypes.Structure):
                 ("radix_bits1", ctypes.c_int32), ("filter_bits", ctypes.c_int32),
                 ("heavy", ctypes.c_int32), ("theta_groups", ctypes.c_int32),
                 ("nlj_tile_r", ctypes.c_int32), ("graphs", ctypes.c_int32),
-                ("part_rows", ctypes.c_int32), ("reserved", ctypes.c_int32 * 7)]
+                ("part_rows", ctypes.c_int32), ("host_io", ctypes.c_int32),
+                ("reserved", ctypes.c_int32 * 6)]
 
 
 class Join(ctypes.Structure):

@@ -128,6 +128,46 @@ def test_hash_unaligned_and_host_columns(ctx):
     got = jn.jn_hash(ctx, jn.table(r[1:].clone(), payload=rp[1:].clone()),
                      jn.table(s[3:].clone().pin_memory(), payload=sp[3:].clone()), out=out)
     assert np.array_equal(canon(got), exp)
+    # page-locked host columns read in place (off a 16-byte boundary too) and a
+    # page-locked host output written in place
+    rh, sh = r.clone().pin_memory(), s.clone().pin_memory()
+    rph, sph = rp.clone().pin_memory(), sp.clone().pin_memory()
+    outp = torch.empty((exp.shape[0] + 5, 2), dtype=torch.int32).pin_memory()
+    r2 = keys(300000, 0, 5000, 19, 0).pin_memory()
+    s2 = keys(200000, 0, 5000, 19, 1).pin_memory()
+    exp2 = canon(O.hash_join(r2.numpy(), s2.numpy()))
+    for io in (1, 2, 3):
+        ctx.set_tuning(host_io=io)
+        try:
+            got = jn.jn_hash(ctx, jn.table(rh[1:], payload=rph[1:]), jn.table(sh[3:], payload=sph[3:]), out=outp)
+            assert np.array_equal(canon(got), exp)
+            # the heavy-key path, more rows than one tile of a pass
+            ctx.set_tuning(heavy=64)
+            out2 = torch.empty((exp2.shape[0], 2), dtype=torch.int32).pin_memory()
+            got = jn.jn_hash(ctx, jn.table(r2), jn.table(s2), out=out2)
+            assert np.array_equal(canon(got), exp2)
+        finally:
+            ctx.set_tuning(heavy=-1, host_io=0)
+
+
+def test_host_mapped_outputs_band_and_nested_loop(ctx):
+    ra, rk = datagen.band_columns(3000, 12, seed=44, stream=0)
+    sa, sk = datagen.band_columns(7000, 12, seed=44, stream=1)
+    exp = canon(O.band_join_sorted(ra.numpy(), rk.numpy(), sa.numpy(), sk.numpy(), O.GT, 3))
+    R = jn.table(ra.to(DEV), rk.to(DEV))
+    S = jn.table(sa.to(DEV), sk.to(DEV))
+    out = torch.empty((exp.shape[0], 2), dtype=torch.int32).pin_memory()
+    ctx.set_tuning(host_io=2)
+    try:
+        assert np.array_equal(canon(jn.jn_theta(ctx, R, S, jn.JN_GT, 3, out=out)), exp)
+        out.zero_()
+        assert np.array_equal(canon(jn.jn_nested_loop(ctx, R, S, jn.pred(jn.JN_GT, jn.JN_ANY, 3), out=out)), exp)
+    finally:
+        ctx.set_tuning(host_io=0)
+    # pinned host columns on the paths that copy them
+    Rh = jn.table(ra.pin_memory(), rk.pin_memory())
+    Sh = jn.table(sa.pin_memory(), sk.pin_memory())
+    assert np.array_equal(canon(jn.jn_theta(ctx, Rh, Sh, jn.JN_GT, 3)), exp)
 
 
 def test_capacity_error_writes_nothing(ctx):
