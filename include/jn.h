@@ -270,10 +270,11 @@ void jn_free(jn_ctx* ctx, jn_pair* p);
  * (or decide whether it fits) first. */
 jn_status jn_batch_count(jn_ctx* ctx, int32_t count, const jn_join* joins, uint64_t* pairs, uint64_t* total);
 
-/* Autotuner: times candidate tunings on these inputs through the count pass
- * (every phase but the writing of pairs), applies the fastest to the context
- * and caches it per (algorithm, key type, size class); *best (may be NULL)
- * receives it.  The knobs tried never change a result: the hash join's
+/* Autotuner: times candidate tunings on these inputs -- the full join with a
+ * library-allocated output that is freed at once, when the exact result fits
+ * a quarter of the free device memory, else count and checksum -- applies the
+ * fastest to the context and caches it per (algorithm, key type, size class);
+ * *best (may be NULL) receives it.  The knobs tried never change a result: the hash join's
  * partition bits and pre-filter, the theta join's group count, the nested
  * loop's R tile.  It stands in for the hand sweep of the partition parameter
  * alpha in Sec. 5.1.4 and 5.2.4. */

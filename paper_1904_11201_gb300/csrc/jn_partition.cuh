@@ -15,10 +15,23 @@
 
 namespace jnx {
 
-constexpr int SC_T = 512;                // threads per scatter block
-constexpr int SC_IPT = 8;                // rows per thread per tile
+// Partition block shape (build-time knobs): threads per block, rows per
+// thread per tile, and blocks per SM the scatter is compiled for.
+#ifndef JN_SC_T
+#define JN_SC_T 512
+#endif
+#ifndef JN_SC_IPT
+#define JN_SC_IPT 8
+#endif
+#ifndef JN_SC_MINB
+#define JN_SC_MINB 2
+#endif
+constexpr int SC_T = JN_SC_T;            // threads per scatter block
+constexpr int SC_IPT = JN_SC_IPT;        // rows per thread per tile
 constexpr int SC_TILE = SC_T * SC_IPT;   // rows per tile
 constexpr int SC_FMAX = 1024;            // digits per pass
+constexpr int SC_DPT = SC_FMAX / SC_T;   // digits per thread in a tile's digit scan
+static_assert(SC_FMAX % SC_T == 0, "the digit scan gives every thread the same number of digits");
 constexpr uint32_t SC_DROP = 0xFFFFu;    // digit of a filtered row
 
 // Digit = bits of the multiplicative key hash: (khash(k) >> shift) & mask.
@@ -441,7 +454,7 @@ __device__ __forceinline__ void scatter_issue(TileDesc* d, const PartIn<K, HB>& 
 }
 
 template <typename K, bool HB, bool FILTER, typename Digit>
-__global__ void __launch_bounds__(SC_T, 2)
+__global__ void __launch_bounds__(SC_T, JN_SC_MINB)
 k_scatter(PartIn<K, HB> in, const uint64_t* __restrict__ seg_begin, const uint64_t* __restrict__ seg_count,
           const uint64_t* __restrict__ tile_prefix, int nseg, Digit dg0, int nd,
           const uint32_t* __restrict__ other, uint32_t fmask, unsigned long long* __restrict__ cursor,
@@ -549,20 +562,25 @@ k_scatter(PartIn<K, HB> in, const uint64_t* __restrict__ seg_begin, const uint64
 #pragma unroll
         for (int j = 0; j < SC_IPT; j++) rk[j] = (dd[j] != SC_DROP) ? atomicAdd(&s_cnt[dd[j]], 1u) : 0u;
         __syncthreads();
-        // exclusive scan of the digit counts; nd <= SC_FMAX = 2 * SC_T
-        uint32_t c0 = 0, c1 = 0;
-        const int i0 = 2 * threadIdx.x, i1 = i0 + 1;
-        if (i0 < nd) c0 = s_cnt[i0];
-        if (i1 < nd) c1 = s_cnt[i1];
-        uint32_t total;
-        const uint32_t pre = block_excl_scan(c0 + c1, tmp, &total);
-        if (i0 < nd) {
-            s_start[i0] = pre;
-            if (c0) s_delta[i0] = atomicAdd(&cursor[(uint64_t)d.seg * nd + i0], (unsigned long long)c0) - pre;
+        // exclusive scan of the digit counts; nd <= SC_FMAX = SC_DPT * SC_T
+        uint32_t cc[SC_DPT];
+        uint32_t csum = 0;
+        const int i0 = SC_DPT * threadIdx.x;
+#pragma unroll
+        for (int q = 0; q < SC_DPT; q++) {
+            cc[q] = i0 + q < nd ? s_cnt[i0 + q] : 0u;
+            csum += cc[q];
         }
-        if (i1 < nd) {
-            s_start[i1] = pre + c0;
-            if (c1) s_delta[i1] = atomicAdd(&cursor[(uint64_t)d.seg * nd + i1], (unsigned long long)c1) - (pre + c0);
+        uint32_t total;
+        uint32_t pre = block_excl_scan(csum, tmp, &total);
+#pragma unroll
+        for (int q = 0; q < SC_DPT; q++) {
+            const int i = i0 + q;
+            if (i < nd) {
+                s_start[i] = pre;
+                if (cc[q]) s_delta[i] = atomicAdd(&cursor[(uint64_t)d.seg * nd + i], (unsigned long long)cc[q]) - pre;
+            }
+            pre += cc[q];
         }
         __syncthreads();
 #pragma unroll

@@ -3,8 +3,8 @@
 // The knobs that shape the work without changing the result -- the hash
 // join's partition bits and pre-filter, the theta join's group count, the
 // nested loop's R tile, a batch's rows per partition -- are tried on the
-// caller's own inputs through the count pass (every phase except writing the
-// pairs), the fastest is applied to the context, and the choice is cached per
+// caller's own inputs (the full join when its pairs fit in memory, else the
+// count and checksum), the fastest is applied to the context, and the choice is cached per
 // (algorithm, key type, log2 |R|, log2 |S|) so a later call for the same size
 // class costs nothing.  This plays the part of the paper's choice of alpha
 // (Sec. 5.1.4 and 5.2.4 sweep it by hand and report the best range).
@@ -83,13 +83,48 @@ jn_status jn_autotune(jn_ctx* c, int32_t algo, const jn_table* R, const jn_table
     uint64_t cnt = 0;
     jn_status st = jn_count(c, algo, R, S, pred, &cnt);  // warm-up (and argument check)
     if (st != JN_OK) return st;
+    // Each candidate runs the call the caller will run: the join that writes
+    // its pairs when they fit a quarter of the free device memory (the knobs
+    // change what the emit pass reads as much as the count pass), otherwise
+    // count and checksum.
+    size_t free_b = 0, total_b = 0;
+    if (cudaMemGetInfo(&free_b, &total_b) != cudaSuccess) {
+        cudaGetLastError();
+        free_b = 0;
+    }
+    const bool emit = cnt > 0 && cnt * sizeof(jn_pair) <= free_b / 4;
+    jn_pred pr{JN_EQ, JN_ANY, -1};
+    if (pred) pr = *pred;
+    auto one = [&]() -> jn_status {
+        if (!emit) {
+            uint64_t chk = 0;
+            return jn_aggregate(c, algo, R, S, pred, &cnt, &chk);
+        }
+        jn_pair* out = nullptr;
+        uint64_t n = 0;
+        jn_status r = algo == JN_ALGO_HASH    ? jn_hash(c, R, S, &out, 0, &n)
+                      : algo == JN_ALGO_THETA ? jn_theta(c, R, S, pr.op_a, pr.band, &out, 0, &n)
+                                              : jn_nested_loop(c, R, S, pred, &out, 0, &n);
+        if (out) {
+            cudaStreamSynchronize(c->stream);
+            jn_free(c, out);
+        }
+        return r;
+    };
     double best_ms = 1e30;
     jn_tuning pick = base;
     for (const jn_tuning& t : cands) {
         c->tune = t;
         double ms = 1e30;
         for (int rep = 0; rep < 2; rep++) {  // the faster of two runs: host noise only adds time
-            const double x = time_call(c, [&] { return jn_count(c, algo, R, S, pred, &cnt); }, &st);
+            const double x = time_call(c, [&] {
+                const jn_status r = one();
+                if (r == JN_OK && cudaStreamSynchronize(c->stream) != cudaSuccess) {
+                    cudaGetLastError();
+                    return JN_ERR_CUDA;
+                }
+                return r;
+            }, &st);
             if (st != JN_OK) break;
             ms = std::min(ms, x);
         }
@@ -122,10 +157,31 @@ jn_status jn_autotune_batch(jn_ctx* c, int32_t count, const jn_join* joins, jn_t
         }
     }
     const jn_tuning base = c->tune;
-    std::vector<uint64_t> pairs(count);
-    auto trial = [&](jn_status* st) { *st = jn_batch_count(c, count, joins, pairs.data(), nullptr); };
-    jn_status st;
-    trial(&st);  // warm-up
+    std::vector<uint64_t> pairs(count), first(count);
+    uint64_t total = 0;
+    jn_status st = jn_batch_count(c, count, joins, pairs.data(), &total);  // warm-up (and argument check)
+    if (st != JN_OK) return st;
+    size_t free_b = 0, total_b = 0;
+    if (cudaMemGetInfo(&free_b, &total_b) != cudaSuccess) {
+        cudaGetLastError();
+        free_b = 0;
+    }
+    // the whole batch with its pairs when they fit a quarter of the free
+    // memory, otherwise its count phases
+    const bool emit = total > 0 && total * sizeof(jn_pair) <= free_b / 4;
+    auto trial = [&](jn_status* st) {
+        if (!emit) {
+            *st = jn_batch_count(c, count, joins, pairs.data(), nullptr);
+            return;
+        }
+        jn_pair* out = nullptr;
+        uint64_t n = 0;
+        *st = jn_batch(c, count, joins, &out, 0, &n, first.data(), pairs.data());
+        if (out) {
+            cudaStreamSynchronize(c->stream);
+            jn_free(c, out);
+        }
+    };
     double best_ms = 1e30;
     jn_tuning pick = base;
     for (int rows_per_part : {1024, 2048, 4096}) {
