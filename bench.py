@@ -685,6 +685,7 @@ def main():
                     help="hash workloads: 2^N rows per table over a 2^N key domain (profiling runs)")
     ap.add_argument("--prefilter", type=int, default=-1, help="-1 auto, 0 off, 1 on")
     ap.add_argument("--radix-bits", type=int, default=0)
+    ap.add_argument("--theta-groups", type=int, default=0, help="band: log2 of the key groups (0 = autotune)")
     ap.add_argument("--aggregate", action="store_true",
                     help="count + checksum without storing pairs (results too large to store)")
     ap.add_argument("--no-e2e", action="store_true")
@@ -713,8 +714,8 @@ def main():
     dev = "cuda:%d" % local
     stream = torch.cuda.current_stream(local)
     ctx = jn.Context(local, stream)
-    if args.prefilter != -1 or args.radix_bits:
-        ctx.set_tuning(prefilter=args.prefilter, radix_bits=args.radix_bits)
+    if args.prefilter != -1 or args.radix_bits or args.theta_groups:
+        ctx.set_tuning(prefilter=args.prefilter, radix_bits=args.radix_bits, theta_groups=args.theta_groups)
     if args.workload in ("batch", "serve"):
         (batch_main if args.workload == "batch" else serve_main)(args, world, rank, local, dev, stream, jn, ctx)
         ctx.close()
@@ -733,7 +734,7 @@ def main():
     nr, ns = rk.shape[0], sk.shape[0]
     ksize = rk.element_size()
     torch.cuda.synchronize()
-    if args.prefilter == -1 and not args.radix_bits and not args.no_autotune:
+    if args.prefilter == -1 and not args.radix_bits and not args.theta_groups and not args.no_autotune:
         # the library's autotuner times its candidate tunings before the warm-up
         algo = {"hash": jn.JN_ALGO_HASH, "band": jn.JN_ALGO_THETA, "nlj": jn.JN_ALGO_NLJ}[w["kind"]]
         pr = None
@@ -821,9 +822,9 @@ def main():
     # this exact workload and tuning (dram__bytes_read.sum + dram__bytes_write.sum);
     # any other configuration reports null
     if (roof and roof["kernel"] == "scatter" and args.workload == "hash" and not args.small
-            and not args.rows_log2 and args.theta == 0 and info.get("prefilter") == 0
-            and info.get("radix_bits") == 17):
-        roof["traffic"] = 4.247e9
+            and not args.rows_log2 and args.theta == 0 and info.get("prefilter") == 1
+            and info.get("radix_bits") == 16):
+        roof["traffic"] = 3.129e9
         roof["traffic_note"] = "ncu launch list, mean over the four scatter launches of a step"
     floor = None
     if w["kind"] in ("hash", "band"):
