@@ -139,6 +139,13 @@ __device__ __forceinline__ K col_a(const Row<K, BAND>& x) {
     if constexpr (BAND) return x.b; else return x.key;
 }
 
+// One staged R row of a theta work item: its grouped column k and column a.
+template <typename K>
+struct alignas(2 * sizeof(K)) KA {
+    K k;
+    K a;
+};
+
 template <typename K, int MODE, bool BAND>
 __global__ void __launch_bounds__(TH_T)
 k_theta_join(const Row<K, BAND>* __restrict__ rrows, const uint64_t* __restrict__ roff,
@@ -147,9 +154,9 @@ k_theta_join(const Row<K, BAND>* __restrict__ rrows, const uint64_t* __restrict_
              unsigned long long* __restrict__ chk, const uint64_t* __restrict__ item_off, jn_pair* __restrict__ out,
              unsigned int* __restrict__ work) {
     extern __shared__ __align__(16) unsigned char smem[];
-    K* s_k = reinterpret_cast<K*>(smem);
-    K* s_a = s_k + TH_RCAP;
-    int32_t* s_p = reinterpret_cast<int32_t*>(s_a + TH_RCAP);
+    // the staged R rows' k and a side by side, so one load gives both
+    KA<K>* s_ka = reinterpret_cast<KA<K>*>(smem);
+    int32_t* s_p = reinterpret_cast<int32_t*>(s_ka + TH_RCAP);
     uint32_t* s_off = reinterpret_cast<uint32_t*>(s_p + TH_RCAP);
     __shared__ unsigned long long tmp64[33];
     __shared__ uint32_t tmp32[33];
@@ -220,8 +227,7 @@ k_theta_join(const Row<K, BAND>* __restrict__ rrows, const uint64_t* __restrict_
                 const uint64_t u = uoff(x.key, P.lo);
                 if (u >= wlo && u <= whi) {
                     const uint32_t pos = atomicAdd(&s_off[(u - wlo) >> fs], 1u);
-                    s_k[pos] = x.key;
-                    s_a[pos] = col_a<K, BAND>(x);
+                    s_ka[pos] = KA<K>{x.key, col_a<K, BAND>(x)};
                     s_p[pos] = x.pay;
                 }
             }
@@ -229,7 +235,7 @@ k_theta_join(const Row<K, BAND>* __restrict__ rrows, const uint64_t* __restrict_
         } else {
             for (int i = threadIdx.x; i < rn; i += TH_T) {
                 const Row<K, BAND> x = rrows[rbeg + i];
-                s_a[i] = col_a<K, BAND>(x);
+                s_ka[i] = KA<K>{x.key, col_a<K, BAND>(x)};
                 s_p[i] = x.pay;
             }
             if (threadIdx.x == 0) s_rows = (uint32_t)rn;
@@ -267,8 +273,9 @@ k_theta_join(const Row<K, BAND>* __restrict__ rrows, const uint64_t* __restrict_
             uint32_t m = 0;
             unsigned long long fs_sum = 0;
             for (uint32_t e = lo; e < hi; e++) {
-                bool ok = iv_test(ia, s_a[e]);
-                if (BAND) ok = ok && iv_test(ib, s_k[e]);
+                const KA<K> t = s_ka[e];
+                bool ok = iv_test(ia, t.a);
+                if (BAND) ok = ok && iv_test(ib, t.k);
                 if (ok) {
                     m++;
                     if (MODE == MODE_AGG) fs_sum += chk_f(s_p[e]);
@@ -283,8 +290,9 @@ k_theta_join(const Row<K, BAND>* __restrict__ rrows, const uint64_t* __restrict_
                 if (m) {
                     uint64_t o = item_off[it] + base + (incl - m);
                     for (uint32_t e = lo; e < hi; e++) {
-                        bool ok = iv_test(ia, s_a[e]);
-                        if (BAND) ok = ok && iv_test(ib, s_k[e]);
+                        const KA<K> t = s_ka[e];
+                        bool ok = iv_test(ia, t.a);
+                        if (BAND) ok = ok && iv_test(ib, t.k);
                         if (ok) {
                             jn_pair q;
                             q.r = s_p[e];
