@@ -89,8 +89,60 @@ static jn_status check_table(jn_ctx* c, const jn_table* t, const char* name, boo
 
 static bool valid_op(int op) { return op >= JN_EQ && op <= JN_ANY; }
 
+// Host columns of one run: device scratch for each, filled on the copy
+// stream (key columns first, then second columns and payloads), with one
+// event when the keys have landed and one when everything has.
+struct HostCopies {
+    jn_ctx* c;
+    struct Job {
+        void* dst;
+        const void* src;
+        size_t bytes;
+        bool key;
+    };
+    std::vector<Job> jobs;
+    explicit HostCopies(jn_ctx* ctx) : c(ctx) {}
+    ~HostCopies() {
+        // the run's stream-ordered frees of the scratch come after every copy
+        if (c->copied_all) cudaStreamWaitEvent(c->stream, c->copied_all, 0);
+        if (c->copied_keys) cudaEventDestroy(c->copied_keys);
+        if (c->copied_all) cudaEventDestroy(c->copied_all);
+        c->copied_keys = c->copied_all = nullptr;
+    }
+    // a device column as it is, or scratch that a later copy fills
+    jn_status column(Scratch& s, const void* p, size_t bytes, bool key, const void** dp) {
+        if (p == nullptr || bytes == 0 || is_device_pointer(p)) {
+            *dp = p;
+            return JN_OK;
+        }
+        uint8_t* d = nullptr;
+        JN_TRY(s.get(&d, bytes));
+        jobs.push_back(Job{d, p, bytes, key});
+        *dp = d;
+        return JN_OK;
+    }
+    jn_status start() {
+        if (jobs.empty()) return JN_OK;
+        if (!c->copy_stream) JN_CUDA(c, cudaStreamCreateWithFlags(&c->copy_stream, cudaStreamNonBlocking));
+        cudaEvent_t ready;  // the scratch allocations (stream-ordered on the run's stream) come first
+        JN_CUDA(c, cudaEventCreateWithFlags(&ready, cudaEventDisableTiming));
+        cudaEventRecord(ready, c->stream);
+        cudaStreamWaitEvent(c->copy_stream, ready, 0);
+        cudaEventDestroy(ready);
+        JN_CUDA(c, cudaEventCreateWithFlags(&c->copied_keys, cudaEventDisableTiming));
+        JN_CUDA(c, cudaEventCreateWithFlags(&c->copied_all, cudaEventDisableTiming));
+        for (int pass = 0; pass < 2; pass++) {
+            for (const Job& j : jobs)
+                if (j.key == (pass == 0))
+                    JN_CUDA(c, cudaMemcpyAsync(j.dst, j.src, j.bytes, cudaMemcpyHostToDevice, c->copy_stream));
+            JN_CUDA(c, cudaEventRecord(pass == 0 ? c->copied_keys : c->copied_all, c->copy_stream));
+        }
+        return JN_OK;
+    }
+};
+
 template <typename K>
-static jn_status stage(jn_ctx* c, Scratch& s, const jn_table* t, bool use_key2, Cols<K>* out,
+static jn_status stage(jn_ctx* c, Scratch& s, HostCopies& hc, const jn_table* t, bool use_key2, Cols<K>* out,
                        bool in_place = false) {
     const size_t kb = (size_t)t->n * sizeof(K);
     const void *k = nullptr, *k2 = nullptr, *p = nullptr;
@@ -103,9 +155,9 @@ static jn_status stage(jn_ctx* c, Scratch& s, const jn_table* t, bool use_key2, 
         k = mk;
         p = mp;
     } else {
-        JN_TRY(device_column(c, s, t->key, kb, &k));
-        if (use_key2 && t->key2) JN_TRY(device_column(c, s, t->key2, kb, &k2));
-        if (t->payload) JN_TRY(device_column(c, s, t->payload, (size_t)t->n * 4, &p));
+        JN_TRY(hc.column(s, t->key, kb, true, &k));
+        if (use_key2 && t->key2) JN_TRY(hc.column(s, t->key2, kb, false, &k2));
+        if (t->payload) JN_TRY(hc.column(s, t->payload, (size_t)t->n * 4, false, &p));
     }
     out->key = static_cast<const K*>(k);
     out->key2 = static_cast<const K*>(k2);
@@ -118,12 +170,15 @@ template <typename K>
 static jn_status dispatch(jn_ctx* c, int algo, const jn_table* R, const jn_table* S, const jn_pred& pr,
                           int mode, OutPlan* plan, RunResult* res) {
     Scratch s(c);
+    HostCopies hc(c);
     Cols<K> r, q;
     const bool use2 = algo != JN_ALGO_HASH;
     // the hash join samples a column, then reads it in two streaming passes
     const bool in_place = algo == JN_ALGO_HASH && (c->tune.host_io & 1);
-    JN_TRY(stage<K>(c, s, R, use2, &r, in_place));
-    JN_TRY(stage<K>(c, s, S, use2, &q, in_place));
+    JN_TRY(stage<K>(c, s, hc, R, use2, &r, in_place));
+    JN_TRY(stage<K>(c, s, hc, S, use2, &q, in_place));
+    JN_TRY(hc.start());
+    if (algo != JN_ALGO_HASH) JN_TRY(wait_copies(c, true));  // the hash join waits per phase
     switch (algo) {
         case JN_ALGO_HASH: return run_hash<K>(c, r, q, mode, plan, res);
         case JN_ALGO_NLJ: return run_nlj<K>(c, r, q, pr, mode, plan, res);
@@ -181,16 +236,19 @@ static jn_status batch_typed(jn_ctx* c, int count, const jn_join* joins, jn_pair
     std::vector<Cols<K>> ER(eq.size()), ES(eq.size()), BR(bd.size()), BS(bd.size());
     std::vector<int> bops(bd.size());
     std::vector<int64_t> bbands(bd.size());
+    HostCopies hc(c);
     for (size_t j = 0; j < eq.size(); j++) {
-        JN_TRY(stage<K>(c, s, &joins[eq[j]].R, false, &ER[j]));
-        JN_TRY(stage<K>(c, s, &joins[eq[j]].S, false, &ES[j]));
+        JN_TRY(stage<K>(c, s, hc, &joins[eq[j]].R, false, &ER[j]));
+        JN_TRY(stage<K>(c, s, hc, &joins[eq[j]].S, false, &ES[j]));
     }
     for (size_t j = 0; j < bd.size(); j++) {
-        JN_TRY(stage<K>(c, s, &joins[bd[j]].R, true, &BR[j]));
-        JN_TRY(stage<K>(c, s, &joins[bd[j]].S, true, &BS[j]));
+        JN_TRY(stage<K>(c, s, hc, &joins[bd[j]].R, true, &BR[j]));
+        JN_TRY(stage<K>(c, s, hc, &joins[bd[j]].S, true, &BS[j]));
         bops[j] = joins[bd[j]].op;
         bbands[j] = joins[bd[j]].band;
     }
+    JN_TRY(hc.start());
+    JN_TRY(wait_copies(c, true));
     // every join is counted before the single output allocation
     std::unique_ptr<BatchRun> he, be;
     if (!eq.empty()) JN_TRY(batch_hash_prepare<K>(c, (int)eq.size(), ER.data(), ES.data(), &he));

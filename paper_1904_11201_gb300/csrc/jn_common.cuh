@@ -71,6 +71,9 @@ struct jn_ctx {
     uint64_t launches_at_call = 0;
     std::string err;
     jn_run_info info{};
+    cudaStream_t copy_stream = nullptr;  // private stream for host-column copies
+    cudaEvent_t copied_keys = nullptr;   // this run's host key columns have landed (or NULL)
+    cudaEvent_t copied_all = nullptr;    // every host column of this run has landed (or NULL)
     uint64_t scratch_bytes = 0;  // bytes held by live Scratch sets
     uint64_t mem_limit = 0;      // admission: output + scratch bound (0 = none)
     jn_admit_fn admit = nullptr;
@@ -168,6 +171,10 @@ jn_status device_column(jn_ctx* c, Scratch& s, const void* p, size_t bytes, cons
 // Device address of page-locked host memory the kernels may read and write
 // in place (over the CPU-GPU link), or NULL for any other pointer.
 const void* host_mapped(const void* p);
+// Host columns are copied on the context's copy stream, key columns first;
+// a run waits for the keys before its first key read and for the rest before
+// it needs them (so the first passes overlap the remaining copies).
+jn_status wait_copies(jn_ctx* c, bool all);
 bool is_device_pointer(const void* p);
 
 // ------------------------------------------------------------- helpers --

@@ -111,6 +111,12 @@ const void* host_mapped(const void* p) {
     return a.type == cudaMemoryTypeHost ? a.devicePointer : nullptr;
 }
 
+jn_status wait_copies(jn_ctx* c, bool all) {
+    cudaEvent_t e = all ? c->copied_all : c->copied_keys;
+    if (e) JN_CUDA(c, cudaStreamWaitEvent(c->stream, e, 0));
+    return JN_OK;
+}
+
 jn_status device_column(jn_ctx* c, Scratch& s, const void* p, size_t bytes, const void** dp) {
     if (p == nullptr || bytes == 0 || is_device_pointer(p)) {
         *dp = p;
@@ -338,6 +344,10 @@ void jn_destroy(jn_ctx* c) {
     if (c->h_small) cudaFreeHost(c->h_small);
     if (c->d_err) cudaFree(c->d_err);
     if (c->capture_stream) cudaStreamDestroy(c->capture_stream);
+    if (c->copy_stream) {
+        cudaStreamSynchronize(c->copy_stream);
+        cudaStreamDestroy(c->copy_stream);
+    }
     cudaGetLastError();
     delete c;
 }

@@ -632,6 +632,7 @@ jn_status run_hash(jn_ctx* c, const Cols<K>& R, const Cols<K>& S, int mode, OutP
     using RW = Row<K, false>;
     const uint64_t nr = (uint64_t)R.n, ns = (uint64_t)S.n;
     jn_run_info& info = c->info;
+    JN_TRY(wait_copies(c, false));  // key columns (payloads may still be on their way)
     if (nr == 0 || ns == 0) {
         res->count = 0;
         res->checksum = 0;
@@ -744,6 +745,7 @@ jn_status run_hash(jn_ctx* c, const Cols<K>& R, const Cols<K>& S, int mode, OutP
         JN_TRY(launch(c, K_PRESENCE, kp, dim3(g), dim3(512), smp, R.key, R.n, bmR, fmask, d1, nd1, h1R));
         JN_TRY(launch(c, K_PRESENCE, kp, dim3(g), dim3(512), smp, S.key, S.n, bmS, fmask, d1, nd1, h1S));
         // ---- 2-3. two partition passes per table (filtered by the other's bitmap) ----
+        JN_TRY(wait_copies(c, true));
         JN_TRY((partition_table<K, D1>(c, s, R, b1, b2, d1, heavy ? &hs : nullptr, bmS, fmask, h1R, &PR,
                                        d_small + 0)));
         JN_TRY((partition_table<K, D1>(c, s, S, b1, b2, d1, heavy ? &hs : nullptr, bmR, fmask, h1S, &PS,
