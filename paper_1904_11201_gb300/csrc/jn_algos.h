@@ -29,6 +29,7 @@ struct OutPlan {
     bool host_copy = false;      // caller buffer is host memory, filled by a copy
     bool lib_alloc = false;      // library allocated the result
     bool mapped = false;         // caller buffer is page-locked host memory written in place
+    bool copied = false;         // the run already copied the pairs to the caller's host buffer
 };
 
 // Sizes the output for `m` pairs (allocating or checking the caller buffer).

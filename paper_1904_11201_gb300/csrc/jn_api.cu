@@ -65,8 +65,9 @@ jn_status out_prepare(jn_ctx* c, Scratch& s, uint64_t m, OutPlan& plan) {
 jn_status out_finish(jn_ctx* c, uint64_t m, OutPlan& plan) {
     if (plan.mapped && m > 0) JN_CUDA(c, cudaStreamSynchronize(c->stream));  // pairs visible to the host
     if (plan.host_copy && m > 0) {
-        JN_CUDA(c, cudaMemcpyAsync(*plan.user_out, plan.dev, m * sizeof(jn_pair), cudaMemcpyDeviceToHost,
-                                   c->stream));
+        if (!plan.copied)
+            JN_CUDA(c, cudaMemcpyAsync(*plan.user_out, plan.dev, m * sizeof(jn_pair), cudaMemcpyDeviceToHost,
+                                       c->stream));
         JN_CUDA(c, cudaStreamSynchronize(c->stream));
     }
     if (plan.lib_alloc) *plan.user_out = plan.dev;

@@ -43,6 +43,9 @@ constexpr int HJ_T = JN_HJ_T;        // threads per join block
 constexpr int HJ_CAP = JN_HJ_CAP;    // R rows per shared-memory table (int32 keys)
 constexpr int HJ_SCH = JN_HJ_SCH;    // S rows per staged chunk
 
+#ifndef JN_SLICE_PAIRS
+#define JN_SLICE_PAIRS (1ull << 24)  // host outputs of at least this many pairs are copied back in slices
+#endif
 constexpr int HJ_PAD = 16;         // rows of slack for 16-byte widened copies
 constexpr uint64_t CE_PAIRS = 1u << 16;  // cross-product pairs per work chunk
 
@@ -158,7 +161,8 @@ k_hash_join(const Row<K, false>* __restrict__ rrows, const Row<K, false>* __rest
             const Item* __restrict__ items, const uint64_t* __restrict__ nitems_p, int bits,
             unsigned long long* __restrict__ item_val,
             unsigned long long* __restrict__ chk, const uint64_t* __restrict__ item_off,
-            jn_pair* __restrict__ out, unsigned int* __restrict__ err) {
+            jn_pair* __restrict__ out, unsigned int* __restrict__ err, uint64_t item_lo = 0,
+            uint64_t item_hi = ~0ull) {
     using R = Row<K, false>;
     using L = JoinSmem<K, MODE>;
     constexpr int CAP = L::CAP;
@@ -184,8 +188,9 @@ k_hash_join(const Row<K, false>* __restrict__ rrows, const Row<K, false>* __rest
     const K KMIN = key_sentinel<K>();
 
     const int lane = threadIdx.x & 31;
-    const uint64_t nitems = *nitems_p;
-    uint64_t it = blockIdx.x;
+    // items [item_lo, min(*nitems_p, item_hi)) of the queue
+    const uint64_t nitems = min(*nitems_p, item_hi);
+    uint64_t it = item_lo + blockIdx.x;
     if (it >= nitems) return;
     Item d = items[it];
     // S-chunk stream: chunk q of this block sits in buffer q & 1; thread 0
@@ -673,8 +678,8 @@ jn_status run_hash(jn_ctx* c, const Cols<K>& R, const Cols<K>& S, int mode, OutP
 
     Scratch s(c);
     uint64_t* d_small;  // [0] R survivors, [1] S survivors, [2] items, [3] count, [4] checksum, [5] heavy
-    JN_TRY(s.get(&d_small, 8));
-    JN_TRY(zero(c, d_small, 64));
+    JN_TRY(s.get(&d_small, 16));  // [8 ..] output offsets of emit slices
+    JN_TRY(zero(c, d_small, 128));
     uint32_t *bmR = nullptr, *bmS = nullptr;
     unsigned long long *h1R, *h1S;
     JN_TRY(s.get(&h1R, nd1));
@@ -805,7 +810,7 @@ jn_status run_hash(jn_ctx* c, const Cols<K>& R, const Cols<K>& S, int mode, OutP
         const int gj = (int)min((uint64_t)persistent_grid(c, (const void*)kc, HJ_T, smc), nitems);
         JN_TRY(launch(c, K_HASH_COUNT, kc, dim3(gj), dim3(HJ_T), smc, (const RW*)PR.rows, (const RW*)PS.rows,
                       (const Item*)idesc, (const uint64_t*)(iprefix + P), b, ival, chk, (const uint64_t*)nullptr,
-                      (jn_pair*)nullptr, c->d_err));
+                      (jn_pair*)nullptr, c->d_err, (uint64_t)0, ~0ull));
     }
     JN_TRY(scan_u64(c, reinterpret_cast<const uint64_t*>(ival), ioff, (int64_t)nitems));
     // ---- heavy keys: c_R(h) * c_S(h) pairs each ----
@@ -847,19 +852,57 @@ jn_status run_hash(jn_ctx* c, const Cols<K>& R, const Cols<K>& S, int mode, OutP
     if (mode != MODE_EMIT) return JN_OK;
     // ---- 5. exact allocation and the emit pass ----
     JN_TRY(out_prepare(c, s, total, *plan));
+    // A host output is copied back slice by slice (on the copy stream) while
+    // the later slices of the work queue emit: slice k's pairs are the
+    // contiguous range [ioff[ib[k]], ioff[ib[k + 1]]).
+    const int nsl = (plan->host_copy && normal >= (uint64_t)JN_SLICE_PAIRS && nitems >= 64) ? 4 : 1;
+    uint64_t ib[5], ob[5] = {0, 0, 0, 0, 0};
+    for (int k = 0; k <= nsl; k++) ib[k] = nitems * (uint64_t)k / (uint64_t)nsl;
+    if (nsl > 1) {
+        for (int k = 0; k <= nsl; k++)
+            JN_CUDA(c, cudaMemcpyAsync(d_small + 8 + k, ioff + ib[k], 8, cudaMemcpyDeviceToDevice, c->stream));
+        JN_TRY(read_back(c, d_small + 8, ob, nsl + 1));
+        if (!c->copy_stream) JN_CUDA(c, cudaStreamCreateWithFlags(&c->copy_stream, cudaStreamNonBlocking));
+    }
+    auto copy_back = [&](uint64_t lo, uint64_t hi) -> jn_status {  // pairs [lo, hi) to the caller's buffer
+        if (hi <= lo) return JN_OK;
+        cudaEvent_t e;
+        JN_CUDA(c, cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
+        cudaEventRecord(e, c->stream);
+        cudaStreamWaitEvent(c->copy_stream, e, 0);
+        cudaEventDestroy(e);
+        JN_CUDA(c, cudaMemcpyAsync(*plan->user_out + lo, plan->dev + lo, (hi - lo) * sizeof(jn_pair),
+                                   cudaMemcpyDeviceToHost, c->copy_stream));
+        return JN_OK;
+    };
     if (normal > 0) {
         auto ke = skewed ? k_hash_join<K, MODE_EMIT, true> : k_hash_join<K, MODE_EMIT, false>;
         const size_t sme = hash_smem<K>(MODE_EMIT);
-        const int ge = (int)min((uint64_t)persistent_grid(c, (const void*)ke, HJ_T, sme), nitems);
-        JN_TRY(launch(c, K_HASH_EMIT, ke, dim3(ge), dim3(HJ_T), sme, (const RW*)PR.rows, (const RW*)PS.rows,
-                      (const Item*)idesc, (const uint64_t*)(iprefix + P), b, (unsigned long long*)nullptr,
-                      (unsigned long long*)nullptr, (const uint64_t*)ioff, plan->dev, c->d_err));
+        const uint64_t pg = (uint64_t)persistent_grid(c, (const void*)ke, HJ_T, sme);
+        for (int k = 0; k < nsl; k++) {
+            if (ib[k + 1] == ib[k]) continue;
+            const int ge = (int)min(pg, ib[k + 1] - ib[k]);
+            JN_TRY(launch(c, K_HASH_EMIT, ke, dim3(ge), dim3(HJ_T), sme, (const RW*)PR.rows, (const RW*)PS.rows,
+                          (const Item*)idesc, (const uint64_t*)(iprefix + P), b, (unsigned long long*)nullptr,
+                          (unsigned long long*)nullptr, (const uint64_t*)ioff, plan->dev, c->d_err, ib[k],
+                          ib[k + 1]));
+            if (nsl > 1) JN_TRY(copy_back(ob[k], ob[k + 1]));
+        }
     }
     if (heavy_pairs > 0) {
         JN_TRY(launch(c, K_CROSS_EMIT, k_cartesian<RW>, dim3(8 * c->num_sms), dim3(256), 0, (const RW*)PR.hrows,
                       (const uint64_t*)PR.hoff, (const RW*)PS.hrows, (const uint64_t*)PS.hoff,
                       (const uint64_t*)hpoff, (const uint64_t*)hchp, HV_MAX, (uint64_t)CE_PAIRS, normal,
                       plan->dev));
+    }
+    if (nsl > 1) {
+        JN_TRY(copy_back(normal, total));
+        cudaEvent_t e;  // the run ends when its last copy has landed
+        JN_CUDA(c, cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
+        cudaEventRecord(e, c->copy_stream);
+        cudaStreamWaitEvent(c->stream, e, 0);
+        cudaEventDestroy(e);
+        plan->copied = true;
     }
     JN_TRY(out_finish(c, total, *plan));
     return JN_OK;
@@ -1003,7 +1046,7 @@ struct HashBatchRun : BatchRun {
             if ((st = launch(c, K_HASH_COUNT, kc, dim3(persistent_grid(c, (const void*)kc, HJ_T, smc)), dim3(HJ_T),
                              smc, (const RW*)prow, (const RW*)prow, (const Item*)idesc,
                              (const uint64_t*)(iprefix + P), 10, ival, chk, (const uint64_t*)nullptr,
-                             (jn_pair*)nullptr, c->d_err)) != JN_OK)
+                             (jn_pair*)nullptr, c->d_err, (uint64_t)0, ~0ull)) != JN_OK)
                 break;
             // items past the real count keep zero counts: scan the whole bound
             if ((st = scan_u64(c, reinterpret_cast<const uint64_t*>(ival), ioff, (int64_t)item_bound)) != JN_OK) break;
@@ -1034,7 +1077,7 @@ struct HashBatchRun : BatchRun {
         jn_status st = launch(c, K_HASH_EMIT, ke, dim3(persistent_grid(c, (const void*)ke, HJ_T, sme)), dim3(HJ_T),
                               sme, (const RW*)prow, (const RW*)prow, (const Item*)idesc, (const uint64_t*)(iprefix + P),
                               10, (unsigned long long*)nullptr, (unsigned long long*)nullptr, (const uint64_t*)ioff,
-                              out, c->d_err);
+                              out, c->d_err, (uint64_t)0, ~0ull);
         if (st != JN_OK) {
             gp.abort();
             return st;

@@ -415,3 +415,24 @@ def test_heavy_keys_are_the_most_frequent(ctx):
         assert info["heavy_pairs"] >= 5000 * 5000
     finally:
         ctx.set_tuning(heavy=-1)
+
+
+def test_host_output_copied_back_in_slices(ctx):
+    # more than 2^24 pairs into a host buffer: the emit pass runs in slices and
+    # each slice's pairs are copied back while the next one emits
+    r = keys(4_500_000, 0, 1 << 20, 51, 0)
+    s = keys(4_500_000, 0, 1 << 20, 51, 1)
+    cnt, chk = O.equi_count_checksum(r.numpy(), s.numpy())
+    assert cnt >= 1 << 24
+    R, S = jn.table(r.to(DEV)), jn.table(s.to(DEV))
+    for pin in (False, True):
+        out = torch.full((cnt + 3, 2), -1, dtype=torch.int32)
+        if pin:
+            out = out.pin_memory()
+        got = jn.jn_hash(ctx, R, S, out=out)
+        assert got.shape[0] == cnt
+        assert O.checksum_pairs(got.numpy()) == chk
+        assert bool((out[cnt:] == -1).all())
+        # every pair joins equal keys
+        g = got.long()
+        assert torch.equal(r[g[:, 0]], s[g[:, 1]])
