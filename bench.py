@@ -207,6 +207,51 @@ class ClockSampler:
                 "samples": len(mhz)}
 
 
+class PinnedHost:
+    """Page-locked host buffers for the end-to-end leg.  "thp": anonymous
+    memory advised for transparent huge pages, touched, then registered with
+    CUDA (few large pages keep the device's DMA fast even when host memory is
+    fragmented); "pin": torch's pin_memory."""
+
+    def __init__(self, kind):
+        self.kind = kind
+        self.maps = []
+        self.regs = []
+
+    def empty(self, shape, dtype):
+        if self.kind == "pin":
+            return torch.empty(shape, dtype=dtype).pin_memory()
+        import mmap
+        import numpy as np
+        n = 1
+        for d in shape:
+            n *= d
+        nbytes = max(n * torch.empty((), dtype=dtype).element_size(), 1)
+        size = (nbytes + (2 << 20) - 1) & ~((2 << 20) - 1)
+        mm = mmap.mmap(-1, size, flags=mmap.MAP_PRIVATE | mmap.MAP_ANONYMOUS)
+        if hasattr(mm, "madvise") and hasattr(mmap, "MADV_HUGEPAGE"):
+            mm.madvise(mmap.MADV_HUGEPAGE)
+        arr = np.frombuffer(mm, dtype=np.uint8, count=size)
+        arr[::4096] = 0  # touch every page before it is locked
+        t = torch.from_numpy(arr[:nbytes]).view(dtype).view(shape)
+        rc = torch.cuda.cudart().cudaHostRegister(t.data_ptr(), size, 0)
+        if int(rc) != 0:
+            raise RuntimeError("cudaHostRegister failed: %s" % rc)
+        self.maps.append((mm, arr))
+        self.regs.append(t.data_ptr())
+        return t
+
+    def copy_of(self, t):
+        h = self.empty(tuple(t.shape), t.dtype)
+        h.copy_(t)
+        return h
+
+    def close(self):
+        for p in self.regs:
+            torch.cuda.cudart().cudaHostUnregister(p)
+        self.regs = []
+
+
 # ------------------------------------------------------------ cpu baseline --
 
 def cpu_baseline(kind, budget_s=12.0):
@@ -691,6 +736,8 @@ def main():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-autotune", action="store_true", help="keep the library's default tuning")
+    ap.add_argument("--host-alloc", default="pin", choices=("thp", "pin"),
+                    help="e2e host buffers: huge-page-advised memory registered with CUDA, or torch pin_memory")
     ap.add_argument("--host-io", type=int, default=0,
                     help="e2e: 0 copy host buffers, 1 read inputs in place, 2 write pairs in place, 3 both")
     ap.add_argument("--batch-count", type=int, default=4096, help="batch workload: number of joins")
@@ -834,25 +881,34 @@ def main():
     # ---- end to end: host columns in, host pairs out, through the C ABI ----
     e2e = None
     if not args.no_e2e:
-        hr = tuple(None if t is None else t.cpu().pin_memory() for t in w["R"])
-        hs = tuple(None if t is None else t.cpu().pin_memory() for t in w["S"])
+        host = PinnedHost(args.host_alloc)
+        hr = tuple(None if t is None else host.copy_of(t) for t in w["R"])
+        hs = tuple(None if t is None else host.copy_of(t) for t in w["S"])
         HR, HS = jn.table(*hr), jn.table(*hs)
-        hout = torch.empty((m, 2), dtype=torch.int32).pin_memory()
+        hout = host.empty((m, 2), torch.int32)
         if args.host_io:
             ctx.set_tuning(host_io=args.host_io)
         run_step(jn, ctx, w, HR, HS, out=hout)  # warm-up of the staging path
         torch.cuda.synchronize()
         barrier(world)
-        t0 = time.perf_counter()
-        for _ in range(max(1, min(args.steps, 3))):
+        # each step timed on its own (the call returns once the pairs are in
+        # host memory); the median damps the host link's sharing with other
+        # jobs on the machine, every sample is reported
+        samples = []
+        for _ in range(max(1, min(args.steps, 5))):
+            t0 = time.perf_counter()
             got = run_step(jn, ctx, w, HR, HS, out=hout)
-        torch.cuda.synchronize()
-        te = (time.perf_counter() - t0) / max(1, min(args.steps, 3))
+            torch.cuda.synchronize()
+            samples.append(time.perf_counter() - t0)
+        te = sorted(samples)[len(samples) // 2]
         te = max_over_ranks(te, world, dev)
         hb = sum(t.numel() * t.element_size() for t in hr + hs if t is not None)
         e2e = {"value": world * units / te, "unit": "tuples/s", "h2d_bytes_per_step": hb,
-               "d2h_bytes_per_step": 8 * m, "ms_per_step": te * 1e3, "host_io": args.host_io}
-        del got, hout, hr, hs
+               "d2h_bytes_per_step": 8 * m, "ms_per_step": te * 1e3, "stat": "median of %d steps" % len(samples),
+               "samples_ms": [round(x * 1e3, 2) for x in samples], "host_io": args.host_io,
+               "host_alloc": args.host_alloc}
+        del got, hout, hr, hs, HR, HS
+        host.close()
 
     cb = cb_all = None
     if rank == 0 and world == 1 and not args.no_cpu:

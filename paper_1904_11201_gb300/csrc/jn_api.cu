@@ -100,15 +100,18 @@ struct HostCopies {
         const void* src;
         size_t bytes;
         bool key;
+        bool first;  // a column of the first table staged
     };
     std::vector<Job> jobs;
+    bool first_table = true;  // stage() calls of the first table come first
     explicit HostCopies(jn_ctx* ctx) : c(ctx) {}
     ~HostCopies() {
         // the run's stream-ordered frees of the scratch come after every copy
         if (c->copied_all) cudaStreamWaitEvent(c->stream, c->copied_all, 0);
         if (c->copied_keys) cudaEventDestroy(c->copied_keys);
+        if (c->copied_r) cudaEventDestroy(c->copied_r);
         if (c->copied_all) cudaEventDestroy(c->copied_all);
-        c->copied_keys = c->copied_all = nullptr;
+        c->copied_keys = c->copied_r = c->copied_all = nullptr;
     }
     // a device column as it is, or scratch that a later copy fills
     jn_status column(Scratch& s, const void* p, size_t bytes, bool key, const void** dp) {
@@ -118,7 +121,7 @@ struct HostCopies {
         }
         uint8_t* d = nullptr;
         JN_TRY(s.get(&d, bytes));
-        jobs.push_back(Job{d, p, bytes, key});
+        jobs.push_back(Job{d, p, bytes, key, first_table});
         *dp = d;
         return JN_OK;
     }
@@ -131,12 +134,15 @@ struct HostCopies {
         cudaStreamWaitEvent(c->copy_stream, ready, 0);
         cudaEventDestroy(ready);
         JN_CUDA(c, cudaEventCreateWithFlags(&c->copied_keys, cudaEventDisableTiming));
+        JN_CUDA(c, cudaEventCreateWithFlags(&c->copied_r, cudaEventDisableTiming));
         JN_CUDA(c, cudaEventCreateWithFlags(&c->copied_all, cudaEventDisableTiming));
-        for (int pass = 0; pass < 2; pass++) {
+        // keys of both tables, then the rest of the first table, then the rest
+        cudaEvent_t marks[3] = {c->copied_keys, c->copied_r, c->copied_all};
+        for (int pass = 0; pass < 3; pass++) {
             for (const Job& j : jobs)
-                if (j.key == (pass == 0))
+                if (pass == 0 ? j.key : (!j.key && j.first == (pass == 1)))
                     JN_CUDA(c, cudaMemcpyAsync(j.dst, j.src, j.bytes, cudaMemcpyHostToDevice, c->copy_stream));
-            JN_CUDA(c, cudaEventRecord(pass == 0 ? c->copied_keys : c->copied_all, c->copy_stream));
+            JN_CUDA(c, cudaEventRecord(marks[pass], c->copy_stream));
         }
         return JN_OK;
     }
@@ -177,6 +183,7 @@ static jn_status dispatch(jn_ctx* c, int algo, const jn_table* R, const jn_table
     // the hash join samples a column, then reads it in two streaming passes
     const bool in_place = algo == JN_ALGO_HASH && (c->tune.host_io & 1);
     JN_TRY(stage<K>(c, s, hc, R, use2, &r, in_place));
+    hc.first_table = false;
     JN_TRY(stage<K>(c, s, hc, S, use2, &q, in_place));
     JN_TRY(hc.start());
     if (algo != JN_ALGO_HASH) JN_TRY(wait_copies(c, true));  // the hash join waits per phase

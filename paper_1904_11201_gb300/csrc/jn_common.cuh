@@ -73,6 +73,7 @@ struct jn_ctx {
     jn_run_info info{};
     cudaStream_t copy_stream = nullptr;  // private stream for host-column copies
     cudaEvent_t copied_keys = nullptr;   // this run's host key columns have landed (or NULL)
+    cudaEvent_t copied_r = nullptr;      // ... and every column of its first table (or NULL)
     cudaEvent_t copied_all = nullptr;    // every host column of this run has landed (or NULL)
     uint64_t scratch_bytes = 0;  // bytes held by live Scratch sets
     uint64_t mem_limit = 0;      // admission: output + scratch bound (0 = none)
@@ -175,6 +176,7 @@ const void* host_mapped(const void* p);
 // a run waits for the keys before its first key read and for the rest before
 // it needs them (so the first passes overlap the remaining copies).
 jn_status wait_copies(jn_ctx* c, bool all);
+jn_status wait_copies_r(jn_ctx* c);  // the keys and the first table's other columns
 bool is_device_pointer(const void* p);
 
 // ------------------------------------------------------------- helpers --

@@ -117,6 +117,11 @@ jn_status wait_copies(jn_ctx* c, bool all) {
     return JN_OK;
 }
 
+jn_status wait_copies_r(jn_ctx* c) {
+    if (c->copied_r) JN_CUDA(c, cudaStreamWaitEvent(c->stream, c->copied_r, 0));
+    return JN_OK;
+}
+
 jn_status device_column(jn_ctx* c, Scratch& s, const void* p, size_t bytes, const void** dp) {
     if (p == nullptr || bytes == 0 || is_device_pointer(p)) {
         *dp = p;

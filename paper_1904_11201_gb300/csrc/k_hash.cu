@@ -750,9 +750,10 @@ jn_status run_hash(jn_ctx* c, const Cols<K>& R, const Cols<K>& S, int mode, OutP
         JN_TRY(launch(c, K_PRESENCE, kp, dim3(g), dim3(512), smp, R.key, R.n, bmR, fmask, d1, nd1, h1R));
         JN_TRY(launch(c, K_PRESENCE, kp, dim3(g), dim3(512), smp, S.key, S.n, bmS, fmask, d1, nd1, h1S));
         // ---- 2-3. two partition passes per table (filtered by the other's bitmap) ----
-        JN_TRY(wait_copies(c, true));
+        JN_TRY(wait_copies_r(c));
         JN_TRY((partition_table<K, D1>(c, s, R, b1, b2, d1, heavy ? &hs : nullptr, bmS, fmask, h1R, &PR,
                                        d_small + 0)));
+        JN_TRY(wait_copies(c, true));
         JN_TRY((partition_table<K, D1>(c, s, S, b1, b2, d1, heavy ? &hs : nullptr, bmR, fmask, h1S, &PS,
                                        d_small + 1)));
         return JN_OK;
