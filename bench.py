@@ -605,7 +605,7 @@ def serve_main(args, world, rank, local, dev, stream, jn, ctx):
                 "saturation": sat, "poisson": rates, "server_stats": st,
                 "roofline": None, "cpu_baseline": None, "e2e": None,
                 "e2e_note": "requests name device-resident columns; latency is submit to pairs ready",
-                "clocks": clocks, "gpu_launches": None}
+                "clocks": clocks, "gpu_launches": st["kernel_launches"]}
         print(json.dumps(line), flush=True)
 
 

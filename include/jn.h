@@ -329,6 +329,7 @@ typedef struct {
 typedef struct {
     uint64_t submitted, completed, failed, batches, queued;
     uint64_t held_bytes, peak_bytes, resident_bytes;
+    uint64_t kernel_launches;  /* kernels the workers launched (graph replays count their kernels) */
 } jn_server_stats;
 
 jn_status jn_server_create(jn_server** s, int device, const jn_server_config* cfg);

@@ -146,6 +146,7 @@ void unreserve(jn_server* s, uint64_t bytes) {
 // count pass of its own.
 struct Admit {
     jn_server* s = nullptr;
+    jn_ctx* ctx = nullptr;  // the worker's context (its launch counter)
     uint64_t granted = 0;  // output bytes the hook reserved for the current run
     uint64_t prepaid = 0;  // output bytes reserved before a second run
     uint64_t wanted = 0;   // output bytes the last hook call asked for
@@ -186,6 +187,18 @@ jn_status admit_hook(void* user, uint64_t out_bytes, uint64_t scratch_bytes) {
 // output bytes of a successful run.
 template <typename Call>
 jn_status admitted_run(jn_server* s, Admit* a, cudaStream_t stream, uint64_t scratch, Call call) {
+    const uint64_t l0 = a->ctx ? jn_launch_count(a->ctx) : 0;
+    struct Count {  // kernels of this run (and of a second one) go to the server's stats
+        jn_server* s;
+        Admit* a;
+        uint64_t l0;
+        ~Count() {
+            if (!a->ctx) return;
+            const uint64_t n = jn_launch_count(a->ctx) - l0;
+            std::lock_guard<std::mutex> g(s->mu);
+            s->stats.kernel_launches += n;
+        }
+    } count{s, a, l0};
     a->reset();
     if (!reserve(s, scratch)) return JN_ERR_OOM;
     jn_status st = call();
@@ -301,6 +314,7 @@ void worker_main(jn_server* s, int slot) {
     jn_set_tuning(ctx, &t);
     Admit adm;
     adm.s = s;
+    adm.ctx = ctx;
     jn_set_admission(ctx, admit_hook, &adm);
     (void)slot;
     while (true) {

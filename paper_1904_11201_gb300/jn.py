@@ -75,7 +75,8 @@ class Result(ctypes.Structure):
 
 class ServerStats(ctypes.Structure):
     _fields_ = [(n, ctypes.c_uint64) for n in ("submitted", "completed", "failed", "batches", "queued",
-                                               "held_bytes", "peak_bytes", "resident_bytes")]
+                                               "held_bytes", "peak_bytes", "resident_bytes",
+                                               "kernel_launches")]
 
 
 class KernelStat(ctypes.Structure):
