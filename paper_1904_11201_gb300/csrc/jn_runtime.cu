@@ -4,6 +4,7 @@
 
 #include <algorithm>
 #include <mutex>
+#include <map>
 #include <set>
 
 #include "jn_common.cuh"
@@ -66,14 +67,20 @@ cudaEvent_t take_event(jn_ctx* c) {
     return e;
 }
 
+// Raises a kernel's dynamic shared-memory limit to at least `smem`; never
+// lowers it (a lower limit would refuse later, larger launches of the kernel).
 void ensure_smem(const void* fn, size_t smem) {
     static std::mutex mu;
-    static std::set<std::pair<const void*, size_t>> done;
+    static std::map<const void*, size_t> limit;
     std::lock_guard<std::mutex> g(mu);
-    auto key = std::make_pair(fn, smem);
-    if (done.count(key)) return;
-    cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    done.insert(key);
+    auto it = limit.find(fn);
+    if (it != limit.end() && it->second >= smem) return;
+    if (smem <= 48 * 1024 && it == limit.end()) return;  // within the default limit
+    if (cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess) {
+        cudaGetLastError();
+        return;  // the launch reports the error
+    }
+    limit[fn] = smem;
 }
 
 jn_status read_back(jn_ctx* c, const uint64_t* dsrc, uint64_t* hdst, int n) {
