@@ -336,7 +336,7 @@ def batch_main(args, world, rank, local, dev, stream, jn, ctx):
     rows = sum(x["R"][0].shape[0] + x["S"][0].shape[0] for x in inst)
     eq_rows = sum(x["R"][0].shape[0] + x["S"][0].shape[0] for x in inst if x["band"] < 0)
     torch.cuda.synchronize()
-    tune = jn.jn_autotune_batch(ctx, joins)
+    tune = ctx.tuning() if args.no_autotune else jn.jn_autotune_batch(ctx, joins)
     counts = jn.jn_batch_count(ctx, joins)
     m = sum(counts)
     m_eq = sum(c for c, x in zip(counts, inst) if x["band"] < 0)
@@ -365,7 +365,7 @@ def batch_main(args, world, rank, local, dev, stream, jn, ctx):
     ms = max_over_ranks(e0.elapsed_time(e1) / args.steps, world, dev)
 
     # one at a time: the same joins, each its own library call
-    reps = max(1, min(args.steps, 3))
+    reps = 0 if args.no_compare else max(1, min(args.steps, 3))
     one_counts = []
     torch.cuda.synchronize()
     o0 = torch.cuda.Event(enable_timing=True)
@@ -379,7 +379,7 @@ def batch_main(args, world, rank, local, dev, stream, jn, ctx):
             del res
     o1.record(stream)
     torch.cuda.synchronize()
-    ms_one = o0.elapsed_time(o1) / reps
+    ms_one = o0.elapsed_time(o1) / reps if reps else float("nan")
 
     # kernel breakdown from profiled steps (per-launch events; graphs off)
     ctx.reset_stats()
@@ -410,8 +410,9 @@ def batch_main(args, world, rank, local, dev, stream, jn, ctx):
                            else "inputs fit in L2",
                            "parallelism": "replicas" if world > 1 else "1 GPU",
                            "algo": "jn_batch: one partition pass, one count and one emit launch per phase"},
-                "one_at_a_time": {"ms_per_step": ms_one, "value": world * units / (ms_one * 1e-3),
-                                  "counts_match": one_counts == counts, "speedup_of_batch": ms_one / ms},
+                "one_at_a_time": None if not reps else
+                {"ms_per_step": ms_one, "value": world * units / (ms_one * 1e-3),
+                 "counts_match": one_counts == counts, "speedup_of_batch": ms_one / ms},
                 "roofline": roof, "cpu_baseline": None,
                 "e2e": None, "e2e_note": "batched inputs and outputs stay in device memory",
                 "clocks": clocks, "gpu_launches": launches, "kernels": kern}
@@ -736,6 +737,7 @@ def main():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-autotune", action="store_true", help="keep the library's default tuning")
+    ap.add_argument("--no-compare", action="store_true", help="batch: skip the one-at-a-time comparison")
     ap.add_argument("--host-alloc", default="pin", choices=("thp", "pin"),
                     help="e2e host buffers: huge-page-advised memory registered with CUDA, or torch pin_memory")
     ap.add_argument("--host-io", type=int, default=0,

@@ -25,11 +25,11 @@ using Key = std::tuple<int, int, int, int>;
 std::mutex g_mu;
 std::map<Key, jn_tuning> g_cache;
 
-double time_call(jn_ctx* c, const std::function<jn_status()>& f, jn_status* st) {
+// Host time of one call that synchronises before it returns.
+double time_call(const std::function<jn_status()>& f, jn_status* st) {
     const auto t0 = std::chrono::steady_clock::now();
     *st = f();
     const auto t1 = std::chrono::steady_clock::now();
-    (void)c;
     return std::chrono::duration<double, std::milli>(t1 - t0).count();
 }
 
@@ -117,7 +117,7 @@ jn_status jn_autotune(jn_ctx* c, int32_t algo, const jn_table* R, const jn_table
         c->tune = t;
         double ms = 1e30;
         for (int rep = 0; rep < 2; rep++) {  // the faster of two runs: host noise only adds time
-            const double x = time_call(c, [&] {
+            const double x = time_call([&] {
                 const jn_status r = one();
                 if (r == JN_OK && cudaStreamSynchronize(c->stream) != cudaSuccess) {
                     cudaGetLastError();
@@ -190,7 +190,7 @@ jn_status jn_autotune_batch(jn_ctx* c, int32_t count, const jn_join* joins, jn_t
             t.part_rows = rows_per_part;
             t.graphs = graphs;
             c->tune = t;
-            const double ms = time_call(c, [&] { trial(&st); return st; }, &st);
+            const double ms = time_call([&] { trial(&st); return st; }, &st);
             if (st == JN_OK && ms < best_ms) {
                 best_ms = ms;
                 pick = t;
