@@ -729,7 +729,8 @@ def main():
     ap.add_argument("--small", action="store_true", help="small inputs (profiling runs)")
     ap.add_argument("--rows-log2", type=int, default=0,
                     help="hash workloads: 2^N rows per table over a 2^N key domain (profiling runs)")
-    ap.add_argument("--prefilter", type=int, default=-1, help="-1 auto, 0 off, 1 on")
+    ap.add_argument("--prefilter", type=int, default=-1,
+                    help="-1 auto, 0 off, 1 both tables, 2 only S, 3 only R")
     ap.add_argument("--radix-bits", type=int, default=0)
     ap.add_argument("--theta-groups", type=int, default=0, help="band: log2 of the key groups (0 = autotune)")
     ap.add_argument("--aggregate", action="store_true",

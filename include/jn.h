@@ -89,7 +89,8 @@ typedef struct {
 /* Tuning knobs; 0 (or -1 where noted) lets the library choose.  The result
  * never depends on them. */
 typedef struct {
-    int32_t prefilter;     /* -1 auto, 0 off, 1 on: Algorithm 1's common-key filter     */
+    int32_t prefilter;     /* Algorithm 1's common-key filter: -1 auto, 0 off, 1 both
+                              tables, 2 only S (by R's keys), 3 only R (by S's keys)    */
     int32_t radix_bits;    /* total partition bits of the hash join (0 = auto, <= 20)   */
     int32_t radix_bits1;   /* bits of the first partition pass (0 = auto)               */
     int32_t filter_bits;   /* log2 of the key-presence bitmap size (0 = auto, <= 30)    */
@@ -121,7 +122,8 @@ typedef struct {
     uint64_t work_items;        /* count/emit work items                            */
     uint64_t heavy_keys;        /* keys routed to the cross-product path            */
     uint64_t kernel_launches;   /* kernels launched by the call                     */
-    int32_t prefilter;          /* 1 if the pre-filter ran                          */
+    int32_t prefilter;          /* tables the pre-filter thinned: 0 none, 1 both,
+                                   2 only S, 3 only R                                */
     int32_t radix_bits;
     int32_t radix_bits1;
     int32_t filter_bits;
@@ -368,6 +370,19 @@ jn_status jn_reset_stats(jn_ctx* ctx);
 jn_status jn_last_run_info(const jn_ctx* ctx, jn_run_info* info);
 uint64_t jn_launch_count(const jn_ctx* ctx);           /* kernels launched since creation */
 int32_t jn_pointer_is_device(const void* p);            /* 1 if p is device (or managed) memory */
+
+/* Diagnostic of the bounded device-side wait that every TMA staging pipeline
+ * uses (not part of the join method).  One block on ctx's stream
+ * initialises an mbarrier that expects one arrival and waits on its first
+ * phase for at most `polls` polls (1 <= polls <= 2^20).  With arrive = 1 the
+ * block arrives first and the wait completes: JN_OK.  With arrive = 0
+ * nothing arrives, the wait runs out, the kernel records JN_ERR_TIMEOUT in
+ * the context's device error word and returns, and the call returns
+ * JN_ERR_TIMEOUT through the same read-back the joins use; the context
+ * stays usable.  *elapsed_ns (may be NULL) receives the device time of the
+ * wait.  Synchronises ctx's stream.  Errors: JN_ERR_INVALID (polls out of
+ * range or no context), JN_ERR_CUDA. */
+jn_status jn_selftest_wait(jn_ctx* ctx, uint32_t polls, int32_t arrive, uint64_t* elapsed_ns);
 
 #ifdef __cplusplus
 }

@@ -8,9 +8,12 @@
 
 namespace jnx {
 
-// Iterations of mbarrier.try_wait before a wait is declared failed (each
-// try_wait suspends for a short, hardware-chosen time).
-constexpr uint32_t MBAR_SPIN_LIMIT = 1u << 24;
+// Iterations of mbarrier.try_wait before a wait is declared failed.  Each
+// try_wait on an incomplete phase suspends for a hardware-chosen time,
+// measured at about 3.8 us on GB300, so the limit is about 2 s: far above
+// any bulk copy of a staging buffer, short enough that a lost copy frees
+// the GPU quickly.
+constexpr uint32_t MBAR_SPIN_LIMIT = 1u << 19;
 
 __device__ __forceinline__ uint32_t smem_addr(const void* p) {
     return (uint32_t)__cvta_generic_to_shared(p);
@@ -37,12 +40,22 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
     return ok != 0;
 }
 
-// Waits for phase `parity` of `bar`; false (and *err set) after the limit.
-__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, unsigned int* err) {
-    for (uint32_t i = 0; i < MBAR_SPIN_LIMIT; i++)
+// Waits for phase `parity` of `bar` for at most `polls` polls; false (and
+// *err set to JN_ERR_TIMEOUT) when the phase has not completed by then.
+__device__ __forceinline__ bool mbar_wait_polls(uint64_t* bar, uint32_t parity, unsigned int* err, uint32_t polls) {
+    for (uint32_t i = 0; i < polls; i++)
         if (mbar_try_wait(bar, parity)) return true;
     if (err) atomicExch(err, (unsigned int)JN_ERR_TIMEOUT);
     return false;
+}
+
+// The wait every pipeline uses: MBAR_SPIN_LIMIT polls.
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, unsigned int* err) {
+    return mbar_wait_polls(bar, parity, err, MBAR_SPIN_LIMIT);
+}
+
+__device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_addr(bar)) : "memory");
 }
 
 // Orders this thread's earlier generic-proxy shared-memory accesses before

@@ -201,8 +201,8 @@ __global__ void k_heavy_bits(HeavySet<K> hs, uint32_t* __restrict__ a, uint32_t*
     const int h = *hs.count;
     for (int i = threadIdx.x; i < h; i += blockDim.x) {
         const uint32_t x = fbits(hs.keys[i]) & fmask;
-        atomicOr(&a[x >> 5], 1u << (x & 31));
-        atomicOr(&b[x >> 5], 1u << (x & 31));
+        if (a) atomicOr(&a[x >> 5], 1u << (x & 31));
+        if (b) atomicOr(&b[x >> 5], 1u << (x & 31));
     }
 }
 

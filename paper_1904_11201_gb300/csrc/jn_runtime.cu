@@ -7,6 +7,7 @@
 #include <map>
 #include <set>
 
+#include "jn_async.cuh"
 #include "jn_common.cuh"
 
 namespace jnx {
@@ -280,6 +281,22 @@ static void resolve_pending(jn_ctx* c) {
 
 using namespace jnx;
 
+// One block waits on the first phase of an mbarrier that expects one
+// arrival; with `arrive` set, thread 0 arrives before the wait.  Writes the
+// wait's device time to *ns.
+__global__ void k_wait_selftest(unsigned int* err, uint32_t polls, int32_t arrive, uint64_t* ns) {
+    __shared__ __align__(8) uint64_t bar;
+    if (threadIdx.x == 0) mbar_init(&bar, 1);
+    __syncthreads();
+    if (threadIdx.x == 0 && arrive) mbar_arrive(&bar);
+    uint64_t t0 = 0, t1 = 0;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t0));
+    mbar_wait_polls(&bar, 0, err, polls);
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t1));
+    __syncthreads();
+    if (threadIdx.x == 0) *ns = t1 - t0;
+}
+
 extern "C" {
 
 const char* jn_version(void) { return "jn 0.1 (sm_103a)"; }
@@ -376,7 +393,7 @@ jn_status jn_set_tuning(jn_ctx* c, const jn_tuning* t) {
         default_tuning(&c->tune);
         return JN_OK;
     }
-    if (t->radix_bits < 0 || t->radix_bits > 20 || t->radix_bits1 < 0 || t->radix_bits1 > 10 ||
+    if (t->prefilter < -1 || t->prefilter > 3 || t->radix_bits < 0 || t->radix_bits > 20 || t->radix_bits1 < 0 || t->radix_bits1 > 10 ||
         t->filter_bits < 0 || t->filter_bits > 30 || t->theta_groups < 0 || t->theta_groups > 10 ||
         t->nlj_tile_r < 0 || (t->nlj_tile_r % 256) != 0 || t->nlj_tile_r > 4096 || t->part_rows < 0 ||
         t->host_io < 0 || t->host_io > 3)
@@ -448,5 +465,20 @@ jn_status jn_last_run_info(const jn_ctx* c, jn_run_info* info) {
 uint64_t jn_launch_count(const jn_ctx* c) { return c ? c->launches_total : 0; }
 
 int32_t jn_pointer_is_device(const void* p) { return p && is_device_pointer(p) ? 1 : 0; }
+
+jn_status jn_selftest_wait(jn_ctx* c, uint32_t polls, int32_t arrive, uint64_t* elapsed_ns) {
+    if (!c || polls < 1 || polls > (1u << 20) || (arrive != 0 && arrive != 1)) return JN_ERR_INVALID;
+    c->err.clear();
+    Scratch s(c);
+    uint64_t* d_ns = nullptr;
+    jn_status st = s.get(&d_ns, 1);
+    if (st != JN_OK) return st;
+    st = launch(c, K_MISC, k_wait_selftest, dim3(1), dim3(32), 0, c->d_err, polls, arrive, d_ns);
+    if (st != JN_OK) return st;
+    uint64_t ns = 0;
+    st = read_back(c, d_ns, &ns, 1);
+    if (elapsed_ns) *elapsed_ns = ns;
+    return st;
+}
 
 }  // extern "C"

@@ -54,8 +54,8 @@ jn_status jn_autotune(jn_ctx* c, int32_t algo, const jn_table* R, const jn_table
     std::vector<jn_tuning> cands;
     if (algo == JN_ALGO_HASH) {
         const int cap = jnx::hash_cap(R->key_type);
-        for (int pre : {0, 1}) {
-            const uint64_t target = pre ? cap : cap / 2;
+        for (int pre : {0, 1, 2, 3}) {  // off, both tables, only S, only R
+            const uint64_t target = (pre == 1 || pre == 3) ? cap : cap / 2;  // R rows per partition
             int b = jnx::ceil_log2(jnx::ceil_div((uint64_t)R->n + 1, target));
             for (int d = -1; d <= 1; d++) {
                 jn_tuning t = base;

@@ -652,12 +652,20 @@ jn_status run_hash(jn_ctx* c, const Cols<K>& R, const Cols<K>& S, int mode, OutP
     // ---- parameters ----
     bool heavy = tu.heavy >= 1 || (tu.heavy == -1 && nr + ns >= (1u << 20));
     const int64_t heavy_rows = tu.heavy >= 2 ? tu.heavy : cap_of<K>() / 4;  // rows that make a key heavy
-    bool pre = tu.prefilter == 1 || (tu.prefilter == -1 && nr + ns >= (1u << 22));
+    // which tables the pre-filter thins: bit 0 S (by R's keys), bit 1 R (by S's keys)
+    int fside = 0;
+    if (tu.prefilter == 1 || (tu.prefilter == -1 && nr + ns >= (1u << 22)))
+        fside = 3;
+    else if (tu.prefilter == 2)
+        fside = 1;
+    else if (tu.prefilter == 3)
+        fside = 2;
+    const bool pre = fside != 0;
     int b = tu.radix_bits;
     if (b == 0) {
         // expected R rows per partition: the table capacity when the filter
-        // will thin the rows out, half of it otherwise
-        uint64_t target = pre ? cap_of<K>() : cap_of<K>() / 2;
+        // will thin R's rows out, half of it otherwise
+        uint64_t target = (fside & 2) ? cap_of<K>() : cap_of<K>() / 2;
         b = ceil_log2((nr + target - 1) / target);
         if (b > 20) b = 20;
     }
@@ -686,10 +694,12 @@ jn_status run_hash(jn_ctx* c, const Cols<K>& R, const Cols<K>& S, int mode, OutP
     JN_TRY(s.get(&h1S, nd1));
     JN_TRY(zero(c, h1R, sizeof(unsigned long long) * nd1));
     JN_TRY(zero(c, h1S, sizeof(unsigned long long) * nd1));
-    if (pre) {
+    if (fside & 1) {  // R's keys, filtering S
         JN_TRY(s.get(&bmR, fwords));
-        JN_TRY(s.get(&bmS, fwords));
         JN_TRY(zero(c, bmR, fwords * 4));
+    }
+    if (fside & 2) {  // S's keys, filtering R
+        JN_TRY(s.get(&bmS, fwords));
         JN_TRY(zero(c, bmS, fwords * 4));
     }
     // ---- 0. heavy keys from a strided sample of both key columns ----
@@ -784,7 +794,7 @@ jn_status run_hash(jn_ctx* c, const Cols<K>& R, const Cols<K>& S, int mode, OutP
     info.s_survivors = h[1];
     info.partitions = (uint64_t)P;
     info.work_items = nitems;
-    info.prefilter = pre ? 1 : 0;
+    info.prefilter = fside == 3 ? 1 : fside == 1 ? 2 : fside == 2 ? 3 : 0;
     info.radix_bits = b;
     info.radix_bits1 = b1;
     info.filter_bits = pre ? fb : 0;

@@ -153,6 +153,7 @@ _SIGS = {
     "jn_last_run_info": (ctypes.c_int, [_P, ctypes.POINTER(RunInfo)]),
     "jn_launch_count": (ctypes.c_uint64, [_P]),
     "jn_pointer_is_device": (ctypes.c_int32, [_P]),
+    "jn_selftest_wait": (ctypes.c_int, [_P, ctypes.c_uint32, ctypes.c_int32, ctypes.POINTER(ctypes.c_uint64)]),
 }
 
 
@@ -520,3 +521,10 @@ def jn_batch_count(ctx: Context, joins) -> list:
     cnt = (ctypes.c_uint64 * max(n, 1))()
     _check(ctx, load().jn_batch_count(ctx.handle, n, arr, cnt, None))
     return [int(cnt[i]) for i in range(n)]
+
+
+def jn_selftest_wait(ctx: Context, polls: int, arrive: bool):
+    """Runs the bounded-wait diagnostic; returns (status, elapsed_ns) without raising."""
+    ns = ctypes.c_uint64(0)
+    st = load().jn_selftest_wait(ctx.handle, polls, 1 if arrive else 0, ctypes.byref(ns))
+    return int(st), int(ns.value)

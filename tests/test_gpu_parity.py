@@ -81,7 +81,7 @@ HASH_CASES = [
 
 
 @pytest.mark.parametrize("case", HASH_CASES)
-@pytest.mark.parametrize("pre", [0, 1])
+@pytest.mark.parametrize("pre", [0, 1, 2, 3])  # off, both tables, only S, only R
 def test_hash_cases(ctx, case, pre):
     nr, ns, lo, hi, dt = case
     r = keys(nr, lo, hi, 3, 0, dt)
@@ -94,6 +94,8 @@ def test_hash_cases(ctx, case, pre):
     ctx.set_tuning(prefilter=pre)
     try:
         got = jn.jn_hash(ctx, jn.table(r.to(DEV)), jn.table(s.to(DEV)))
+        if nr and ns:
+            assert ctx.run_info()["prefilter"] == pre
     finally:
         ctx.set_tuning(prefilter=-1)
     assert np.array_equal(canon(got), exp)
@@ -304,8 +306,8 @@ def test_hash_heavy_keys(ctx, theta, dt):
     cnt, chk = O.equi_count_checksum(r.numpy(), s.numpy(), rp.numpy(), sp.numpy())
     R = jn.table(r.to(DEV), payload=rp.to(DEV))
     S = jn.table(s.to(DEV), payload=sp.to(DEV))
-    for heavy in (64, 0):
-        ctx.set_tuning(heavy=heavy, prefilter=1)
+    for heavy, pre in ((64, 1), (0, 1), (64, 2), (64, 3)):
+        ctx.set_tuning(heavy=heavy, prefilter=pre)
         try:
             assert jn.jn_aggregate(ctx, jn.JN_ALGO_HASH, R, S) == (cnt, chk)
             info = ctx.run_info()

@@ -33,7 +33,7 @@ def test_autotune_hash_then_join_equals_oracle(ctx):
     s = datagen.uniform_keys(500000, 0, 1 << 20, 201, 1)
     R, S = jn.table(r.to(DEV)), jn.table(s.to(DEV))
     t = jn.jn_autotune(ctx, jn.JN_ALGO_HASH, R, S)
-    assert t["prefilter"] in (0, 1) and 1 <= t["radix_bits"] <= 20
+    assert t["prefilter"] in (0, 1, 2, 3) and 1 <= t["radix_bits"] <= 20
     assert ctx.tuning()["radix_bits"] == t["radix_bits"]
     assert np.array_equal(canon(jn.jn_hash(ctx, R, S)), canon(O.hash_join(r.numpy(), s.numpy())))
     # the same size class reuses the cached choice
