@@ -45,7 +45,7 @@ def peaks():
 
 # ------------------------------------------------------------- workloads --
 
-def make_workload(name, theta, device, small=False, rows_log2=0):
+def make_workload(name, theta, device, small=False, rows_log2=0, r_rows_log2=0):
     from paper_1904_11201_gb300 import datagen as D
     if name in ("hash", "hash_int64"):
         i64 = name == "hash_int64"
@@ -56,16 +56,17 @@ def make_workload(name, theta, device, small=False, rows_log2=0):
         if rows_log2:
             n, dbits = 1 << rows_log2, rows_log2
         dt = torch.int64 if i64 else torch.int32
+        nr = (1 << r_rows_log2) if r_rows_log2 else n
         cdf = None
         if theta != 0:
             cdf = D.zipf_cdf(theta, 1 << dbits, device)
-        r = D.zipf_keys(n, theta, dbits, seed=0, stream=0, device=device, dtype=dt, cdf=cdf)
+        r = D.zipf_keys(nr, theta, dbits, seed=0, stream=0, device=device, dtype=dt, cdf=cdf)
         s = D.zipf_keys(n, theta, dbits, seed=0, stream=1, device=device, dtype=dt, cdf=cdf)
         del cdf
-        return {"kind": "hash", "R": (r, None, D.row_ids(n, device)), "S": (s, None, D.row_ids(n, device)),
+        return {"kind": "hash", "R": (r, None, D.row_ids(nr, device)), "S": (s, None, D.row_ids(n, device)),
                 "config": {"workload": "equi hash join %dM x %dM %s keys, Zipf theta=%g over 2^%d"
-                           % (n >> 20, n >> 20, "int64" if i64 else "int32", theta, dbits),
-                           "R_rows": n, "S_rows": n, "key": "int64" if i64 else "int32",
+                           % (nr >> 20, n >> 20, "int64" if i64 else "int32", theta, dbits),
+                           "R_rows": nr, "S_rows": n, "key": "int64" if i64 else "int32",
                            "zipf_theta": theta, "key_domain": 1 << dbits, "payload": "int32 row id",
                            "algo": "jn_hash (pre-filter, 2-pass radix partition, count, emit)"}}
     if name == "band":
@@ -729,6 +730,8 @@ def main():
     ap.add_argument("--small", action="store_true", help="small inputs (profiling runs)")
     ap.add_argument("--rows-log2", type=int, default=0,
                     help="hash workloads: 2^N rows per table over a 2^N key domain (profiling runs)")
+    ap.add_argument("--r-rows-log2", type=int, default=0,
+                    help="hash workloads: 2^N rows in R only, S and the key domain unchanged")
     ap.add_argument("--prefilter", type=int, default=-1,
                     help="-1 auto, 0 off, 1 both tables, 2 only S, 3 only R")
     ap.add_argument("--radix-bits", type=int, default=0)
@@ -751,7 +754,7 @@ def main():
     if args.impl == "reference":
         reference_arm(args, world, rank)
         return
-    profiling_run = args.small or args.rows_log2 > 0
+    profiling_run = args.small or args.rows_log2 > 0 or args.r_rows_log2 > 0
     if not profiling_run:
         args.warmup = max(args.warmup, 3)
 
@@ -773,7 +776,7 @@ def main():
             import torch.distributed as dist
             dist.destroy_process_group()
         return
-    w = make_workload(args.workload, args.theta, dev, args.small, args.rows_log2)
+    w = make_workload(args.workload, args.theta, dev, args.small, args.rows_log2, args.r_rows_log2)
     if args.aggregate:
         w["aggregate"] = True
         w["config"]["mode"] = "count + separable checksum (pairs not stored)"
@@ -872,7 +875,7 @@ def main():
     # this exact workload and tuning (dram__bytes_read.sum + dram__bytes_write.sum);
     # any other configuration reports null
     if (roof and roof["kernel"] == "scatter" and args.workload == "hash" and not args.small
-            and not args.rows_log2 and args.theta == 0 and info.get("prefilter") == 1
+            and not args.rows_log2 and not args.r_rows_log2 and args.theta == 0 and info.get("prefilter") == 1
             and info.get("radix_bits") == 16):
         roof["traffic"] = 3.129e9
         roof["traffic_note"] = "ncu launch list, mean over the four scatter launches of a step"
@@ -914,7 +917,7 @@ def main():
         host.close()
 
     cb = cb_all = None
-    if rank == 0 and world == 1 and not args.no_cpu:
+    if rank == 0 and world == 1 and not args.no_cpu and not profiling_run:
         cb = cpu_baseline(w["kind"])
         if w["kind"] == "hash":
             try:

@@ -654,7 +654,12 @@ jn_status run_hash(jn_ctx* c, const Cols<K>& R, const Cols<K>& S, int mode, OutP
     const int64_t heavy_rows = tu.heavy >= 2 ? tu.heavy : cap_of<K>() / 4;  // rows that make a key heavy
     // which tables the pre-filter thins: bit 0 S (by R's keys), bit 1 R (by S's keys)
     int fside = 0;
-    if (tu.prefilter == 1 || (tu.prefilter == -1 && nr + ns >= (1u << 22)))
+    if (tu.prefilter == -1 && nr + ns >= (1u << 22))
+        // with one table twice the other or larger, only the large one is
+        // filtered: building the large table's bitmap costs more than thinning
+        // the small table saves
+        fside = 2 * nr <= ns ? 1 : 2 * ns <= nr ? 2 : 3;
+    else if (tu.prefilter == 1)
         fside = 3;
     else if (tu.prefilter == 2)
         fside = 1;

@@ -101,6 +101,20 @@ def test_hash_cases(ctx, case, pre):
     assert np.array_equal(canon(got), exp)
 
 
+@pytest.mark.parametrize("sizes", [(1 << 20, (1 << 22) + 3, 2), ((1 << 22) + 5, 1 << 20, 3),
+                                   ((1 << 21) + 7, (1 << 21) + 1, 1)])
+def test_hash_auto_prefilter_sides(ctx, sizes):
+    # the automatic choice filters only the larger table when one is 2x the other
+    nr, ns, side = sizes
+    r = keys(nr, 0, 1 << 23, 41, 0)
+    s = keys(ns, 0, 1 << 23, 41, 1)
+    exp = canon(O.hash_join(r.numpy(), s.numpy()))
+    ctx.set_tuning(prefilter=-1)
+    got = jn.jn_hash(ctx, jn.table(r.to(DEV)), jn.table(s.to(DEV)))
+    assert ctx.run_info()["prefilter"] == side
+    assert np.array_equal(canon(got), exp)
+
+
 @pytest.mark.parametrize("bits", [(1, 1), (3, 2), (5, 0), (12, 6), (16, 8)])
 def test_hash_result_independent_of_partitioning(ctx, bits):
     b, b1 = bits
