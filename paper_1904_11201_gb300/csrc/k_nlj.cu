@@ -18,8 +18,18 @@
 namespace jnx {
 
 constexpr int NLJ_T = 256;
-constexpr int NLJ_SPT = 4;
+#ifndef JN_NLJ_SPT
+#define JN_NLJ_SPT 4
+#endif
+constexpr int NLJ_SPT = JN_NLJ_SPT;  // S rows per thread
 constexpr int NLJ_STILE = NLJ_T * NLJ_SPT;
+
+// An R row's two predicate columns, adjacent in shared memory so that one
+// load fetches both.
+template <typename K>
+struct __align__(2 * sizeof(K)) KPair {
+    K a, b;
+};
 
 template <typename K, bool HAS2, int MODE>
 __global__ void __launch_bounds__(NLJ_T)
@@ -29,9 +39,10 @@ k_nlj(const K* __restrict__ rk, const K* __restrict__ rk2, const int32_t* __rest
       unsigned long long* __restrict__ chk, const uint64_t* __restrict__ tile_off,
       jn_pair* __restrict__ out) {
     extern __shared__ __align__(16) unsigned char smem[];
+    // R tile: (a, b) pairs with a second column, else the a column alone
     K* s_a = reinterpret_cast<K*>(smem);
-    K* s_b = s_a + tr;
-    int32_t* s_p = reinterpret_cast<int32_t*>(s_b + (HAS2 ? tr : 0));
+    KPair<K>* s_ab = reinterpret_cast<KPair<K>*>(smem);
+    int32_t* s_p = reinterpret_cast<int32_t*>(s_a + (HAS2 ? 2 : 1) * tr);
     __shared__ unsigned long long tmp64[33];
     __shared__ uint32_t s_cur;
 
@@ -43,8 +54,10 @@ k_nlj(const K* __restrict__ rk, const K* __restrict__ rk2, const int32_t* __rest
     const int64_t r0 = (int64_t)blockIdx.y * tr;
     const int rn = (int)min((int64_t)tr, nr - r0);
     for (int i = threadIdx.x; i < rn; i += NLJ_T) {
-        s_a[i] = rk[r0 + i];
-        if (HAS2) s_b[i] = rk2[r0 + i];
+        if (HAS2)
+            s_ab[i] = KPair<K>{rk[r0 + i], rk2[r0 + i]};
+        else
+            s_a[i] = rk[r0 + i];
         s_p[i] = rp ? rp[r0 + i] : (int32_t)(r0 + i);
     }
     if (threadIdx.x == 0) s_cur = 0;
@@ -70,31 +83,56 @@ k_nlj(const K* __restrict__ rk, const K* __restrict__ rk2, const int32_t* __rest
         }
         spay[j] = valid[j] ? (sp ? sp[s] : (int32_t)s) : 0;
     }
+    // Inverted intervals (!=, and the empty sets of invalid rows and of
+    // "< min" / "> max") take the general test; a warp whose rows have none
+    // runs the plain interval test, which needs no inversion step per pair.
+    bool inv = false;
+#pragma unroll
+    for (int j = 0; j < NLJ_SPT; j++) inv |= ia[j].inv || (HAS2 && ib[j].inv);
+    const bool plain = !__any_sync(0xffffffffu, inv);
     __syncthreads();
 
     unsigned long long acc = 0, csum = 0;
-    for (int i = 0; i < rn; i++) {
-        const K a = s_a[i];
-        K b = 0;
-        if (HAS2) b = s_b[i];
-#pragma unroll
-        for (int j = 0; j < NLJ_SPT; j++) {
-            bool m = iv_test(ia[j], a);
-            if (HAS2) m = m && iv_test(ib[j], b);
-            if (MODE == MODE_EMIT) {
-                if (m) {
-                    const uint32_t slot = atomicAdd(&s_cur, 1u);
-                    jn_pair q;
-                    q.r = s_p[i];
-                    q.s = spay[j];
-                    out[tile_off[tile] + slot] = q;
-                }
+    auto visit = [&](auto test) {
+        for (int i = 0; i < rn; i++) {
+            K a, b = 0;
+            if (HAS2) {
+                const KPair<K> ab = s_ab[i];
+                a = ab.a;
+                b = ab.b;
             } else {
-                acc += m;
-                if (MODE == MODE_AGG && m) csum += chk_f(s_p[i]) * chk_g(spay[j]);
+                a = s_a[i];
+            }
+#pragma unroll
+            for (int j = 0; j < NLJ_SPT; j++) {
+                const bool m = test(j, a, b);
+                if (MODE == MODE_EMIT) {
+                    if (m) {
+                        const uint32_t slot = atomicAdd(&s_cur, 1u);
+                        jn_pair q;
+                        q.r = s_p[i];
+                        q.s = spay[j];
+                        out[tile_off[tile] + slot] = q;
+                    }
+                } else {
+                    acc += m;
+                    if (MODE == MODE_AGG && m) csum += chk_f(s_p[i]) * chk_g(spay[j]);
+                }
             }
         }
-    }
+    };
+    if (plain)
+        visit([&](int j, K a, K b) {
+            bool m = in_range(a, ia[j].lo, ia[j].span);
+            if (HAS2) m &= in_range(b, ib[j].lo, ib[j].span);
+            return m;
+        });
+    else
+        visit([&](int j, K a, K b) {
+            bool m = iv_test(ia[j], a);
+            if (HAS2) m &= iv_test(ib[j], b);
+            return m;
+        });
     if (MODE != MODE_EMIT) {
         const unsigned long long t = block_sum(acc, tmp64);
         if (MODE == MODE_AGG) {
