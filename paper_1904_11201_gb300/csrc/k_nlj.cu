@@ -103,18 +103,27 @@ k_nlj(const K* __restrict__ rk, const K* __restrict__ rk2, const int32_t* __rest
             } else {
                 a = s_a[i];
             }
+            if (MODE == MODE_EMIT) {
+                // one branch per R row: matches are rare, the tests are not
+                uint32_t mask = 0;
 #pragma unroll
-            for (int j = 0; j < NLJ_SPT; j++) {
-                const bool m = test(j, a, b);
-                if (MODE == MODE_EMIT) {
-                    if (m) {
-                        const uint32_t slot = atomicAdd(&s_cur, 1u);
-                        jn_pair q;
-                        q.r = s_p[i];
-                        q.s = spay[j];
-                        out[tile_off[tile] + slot] = q;
+                for (int j = 0; j < NLJ_SPT; j++) mask |= (uint32_t)test(j, a, b) << j;
+                if (mask) {
+#pragma unroll
+                    for (int j = 0; j < NLJ_SPT; j++) {
+                        if ((mask >> j) & 1u) {
+                            const uint32_t slot = atomicAdd(&s_cur, 1u);
+                            jn_pair q;
+                            q.r = s_p[i];
+                            q.s = spay[j];
+                            out[tile_off[tile] + slot] = q;
+                        }
                     }
-                } else {
+                }
+            } else {
+#pragma unroll
+                for (int j = 0; j < NLJ_SPT; j++) {
+                    const bool m = test(j, a, b);
                     acc += m;
                     if (MODE == MODE_AGG && m) csum += chk_f(s_p[i]) * chk_g(spay[j]);
                 }
