@@ -611,6 +611,43 @@ def serve_main(args, world, rank, local, dev, stream, jn, ctx):
         print(json.dumps(line), flush=True)
 
 
+def sweep_main(args, world, rank, stream, jn, ctx, w, R, S):
+    """The partition fan-out sweep (the paper's alpha, Sec. 5.1.4 and 5.2.4): the
+    same join timed at every partition-bit count (hash) or group count (band),
+    the rest of the tuning as chosen before; one JSON line with every point."""
+    if w["kind"] == "hash":
+        knob, values = "radix_bits", list(range(10, 21))
+    elif w["kind"] == "band":
+        knob, values = "theta_groups", list(range(2, 11))
+    else:
+        raise SystemExit("--sweep: hash and band workloads only")
+    base = ctx.tuning()
+    points = []
+    for v in values:
+        ctx.set_tuning(**{knob: v})
+        for _ in range(2):
+            del_out = run_step(jn, ctx, w, R, S)
+            del del_out
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(args.steps):
+            out = run_step(jn, ctx, w, R, S)
+            m = out.shape[0]
+            del out
+        e1.record(stream)
+        torch.cuda.synchronize()
+        info = ctx.run_info()
+        points.append({knob: v, "ms_per_step": e0.elapsed_time(e1) / args.steps, "pairs": m,
+                       "partitions": int(info["partitions"]), "work_items": int(info["work_items"]),
+                       "eq_rsize_bound_pairs": int(info["cartesian_bound"])})
+    ctx.set_tuning(**{knob: base[knob]})
+    if rank == 0:
+        print(json.dumps({"metric": "fan-out sweep", "knob": knob, "steps": args.steps,
+                          "config": w["config"], "points": points}), flush=True)
+
+
 def pool_hi(small):
     return (1 << 20) if small else (64 << 20)
 
@@ -747,6 +784,8 @@ def main():
     ap.add_argument("--host-io", type=int, default=0,
                     help="e2e: 0 copy host buffers, 1 read inputs in place, 2 write pairs in place, 3 both")
     ap.add_argument("--batch-count", type=int, default=4096, help="batch workload: number of joins")
+    ap.add_argument("--sweep", action="store_true",
+                    help="time the join at every partition-bit (hash) or group (band) count; one JSON line")
     ap.add_argument("--serve-requests", type=int, default=10000, help="serve workload: requests per stream")
     ap.add_argument("--serve-slots", type=int, default=4, help="serve workload: server worker slots")
     args = ap.parse_args()
@@ -797,6 +836,10 @@ def main():
             pr = jn.pred(*w["pred"])
         w["config"]["tuning"] = jn.jn_autotune(ctx, algo, R, S, pr)
         w["config"]["autotuned"] = True
+    if args.sweep:
+        sweep_main(args, world, rank, stream, jn, ctx, w, R, S)
+        ctx.close()
+        return
 
     clk = ClockSampler(local)
     clk.start()
@@ -936,6 +979,11 @@ def main():
                 "output_tuples_per_s": world * m / (ms * 1e-3),
                 "result_pairs": m, "join_floor": floor, "roofline": roof, "cpu_baseline": cb,
                 "cpu_baseline_all_cores": cb_all,
+                # what sizing the output by Eq. (rsize) would have allocated for the
+                # same decomposition, against the exact count the library allocates
+                "eq_rsize_bound": {"pairs": int(info.get("cartesian_bound", 0)),
+                                   "bytes": 8 * int(info.get("cartesian_bound", 0)),
+                                   "over_exact": int(info.get("cartesian_bound", 0)) / m if m else None},
                 "e2e": e2e, "clocks": clocks, "gpu_launches": launches,
                 "run_info": {k: int(v) for k, v in info.items()}, "kernels": kern}
         print(json.dumps(line), flush=True)

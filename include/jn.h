@@ -129,7 +129,13 @@ typedef struct {
     int32_t filter_bits;
     uint64_t scratch_peak;      /* most scratch bytes the call held at once         */
     uint64_t heavy_pairs;       /* pairs emitted by the cross-product path          */
-    uint64_t reserved[4];
+    uint64_t cartesian_bound;   /* what Eq. (rsize) would allocate for this run's
+                                   decomposition: sum of |R_i| * |S_i| over the hash
+                                   partitions (plus the frequent keys' exact cross
+                                   products), over the theta join's compared and
+                                   cross regions, or |R| * |S| for the nested loop;
+                                   always >= result                                 */
+    uint64_t reserved[3];
 } jn_run_info;
 
 typedef struct jn_ctx jn_ctx;

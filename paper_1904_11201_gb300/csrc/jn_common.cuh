@@ -140,7 +140,7 @@ template <typename Kern, typename... Args>
 jn_status launch(jn_ctx* c, int kid, Kern kern, dim3 grid, dim3 block, size_t smem,
                  Args... args) {
     if (grid.x == 0 || grid.y == 0 || grid.z == 0) return JN_OK;
-    if (smem > 48 * 1024) ensure_smem(reinterpret_cast<const void*>(kern), smem);
+    if (smem > 0) ensure_smem(reinterpret_cast<const void*>(kern), smem);
     cudaEvent_t e0 = nullptr, e1 = nullptr;
     if (c->profiling) {
         e0 = take_event(c);
@@ -262,6 +262,13 @@ __device__ __forceinline__ T block_sum(T v, T* tmp) {
     T t;
     block_excl_scan(v, tmp, &t);
     return t;
+}
+
+// Adds the warp's total of v to *dst (one atomic per warp; every lane calls).
+__device__ __forceinline__ void warp_add_to(unsigned long long* dst, unsigned long long v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    if ((threadIdx.x & 31) == 0 && v) atomicAdd(dst, v);
 }
 
 // Membership of x in [lo, hi] for signed integers, by one unsigned compare:

@@ -70,13 +70,24 @@ cudaEvent_t take_event(jn_ctx* c) {
 
 // Raises a kernel's dynamic shared-memory limit to at least `smem`; never
 // lowers it (a lower limit would refuse later, larger launches of the kernel).
+// Without the attribute, static and dynamic shared memory together may not
+// pass 48 KB; the first call for a kernel records how much dynamic memory
+// that default leaves it.
 void ensure_smem(const void* fn, size_t smem) {
     static std::mutex mu;
-    static std::map<const void*, size_t> limit;
+    static std::map<const void*, size_t> limit;  // dynamic bytes a launch may use now
     std::lock_guard<std::mutex> g(mu);
     auto it = limit.find(fn);
-    if (it != limit.end() && it->second >= smem) return;
-    if (smem <= 48 * 1024 && it == limit.end()) return;  // within the default limit
+    if (it == limit.end()) {
+        cudaFuncAttributes fa;
+        size_t dflt = 0;
+        if (cudaFuncGetAttributes(&fa, fn) == cudaSuccess && fa.sharedSizeBytes < 48 * 1024)
+            dflt = 48 * 1024 - fa.sharedSizeBytes;
+        else
+            cudaGetLastError();
+        it = limit.emplace(fn, dflt).first;
+    }
+    if (it->second >= smem) return;
     if (cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess) {
         cudaGetLastError();
         return;  // the launch reports the error

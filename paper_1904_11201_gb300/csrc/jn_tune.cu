@@ -72,7 +72,7 @@ jn_status jn_autotune(jn_ctx* c, int32_t algo, const jn_table* R, const jn_table
             cands.push_back(t);
         }
     } else if (algo == JN_ALGO_NLJ) {
-        for (int tr : {512, 1024, 2048}) {
+        for (int tr : {512, 1024, 2048, 4096}) {
             jn_tuning t = base;
             t.nlj_tile_r = tr;
             cands.push_back(t);

@@ -50,13 +50,18 @@ constexpr int HJ_PAD = 16;         // rows of slack for 16-byte widened copies
 constexpr uint64_t CE_PAIRS = 1u << 16;  // cross-product pairs per work chunk
 
 // Items of partition p: one per chunk of HJ_CAP R rows; each item probes
-// every S row of the partition, HJ_SCH rows at a time.
+// every S row of the partition, HJ_SCH rows at a time.  With `bound`, adds
+// sum_p |R_p| * |S_p| to it: Eq. (rsize)'s allocation for these partitions.
 __global__ void k_items(const uint64_t* __restrict__ roff, const uint64_t* __restrict__ soff, int P, int cap,
-                        uint64_t* __restrict__ items) {
-    int p = blockIdx.x * blockDim.x + threadIdx.x;
-    if (p >= P) return;
-    uint64_t nr = roff[p + 1] - roff[p], ns = soff[p + 1] - soff[p];
-    items[p] = (nr && ns) ? (nr + cap - 1) / cap : 0;
+                        uint64_t* __restrict__ items, unsigned long long* __restrict__ bound) {
+    const int p = blockIdx.x * blockDim.x + threadIdx.x;
+    uint64_t nr = 0, ns = 0;
+    if (p < P) {
+        nr = roff[p + 1] - roff[p];
+        ns = soff[p + 1] - soff[p];
+        items[p] = (nr && ns) ? (nr + cap - 1) / cap : 0;
+    }
+    if (bound) warp_add_to(bound, nr * ns);  // < |R| * |S| < 2^62: no overflow
 }
 
 // R rows per shared-memory table: 4096 for int32 keys, 2048 for int64.
@@ -519,7 +524,7 @@ static size_t hash_smem(int mode) {
 
 static int persistent_grid(jn_ctx* c, const void* fn, int threads, size_t smem) {
     int per = 0;
-    if (smem > 48 * 1024) ensure_smem(fn, smem);
+    if (smem > 0) ensure_smem(fn, smem);
     if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, fn, threads, smem) != cudaSuccess) {
         cudaGetLastError();
         per = 1;
@@ -785,13 +790,13 @@ jn_status run_hash(jn_ctx* c, const Cols<K>& R, const Cols<K>& S, int mode, OutP
     JN_TRY(s.get(&items, P));
     JN_TRY(s.get(&iprefix, P + 1));
     JN_TRY(launch(c, K_ITEMS, k_items, dim3((P + 255) / 256), dim3(256), 0, (const uint64_t*)PR.off,
-                  (const uint64_t*)PS.off, P, cap_of<K>(), items));
+                  (const uint64_t*)PS.off, P, cap_of<K>(), items, (unsigned long long*)(d_small + 15)));
     JN_TRY(scan_u64(c, items, iprefix, P));
-    uint64_t h[8];
+    uint64_t h[16];
     JN_TRY(launch(c, K_MISC, k_copy_words, dim3(1), dim3(32), 0, (const uint64_t*)(iprefix + P),
                   d_small + 2, 1));
     if (heavy) JN_CUDA(c, cudaMemcpyAsync(d_small + 7, d_hcount, 4, cudaMemcpyDeviceToDevice, c->stream));
-    JN_TRY(read_back(c, d_small, h, 8));
+    JN_TRY(read_back(c, d_small, h, 16));
     // many frequent keys in the sample: expect duplicate-heavy partitions too
     const bool skewed = heavy && (h[7] & 0xffffffffu) >= 64;
     const uint64_t nitems = h[2];
@@ -865,6 +870,7 @@ jn_status run_hash(jn_ctx* c, const Cols<K>& R, const Cols<K>& S, int mode, OutP
     info.result = total;
     info.heavy_keys = heavy ? (hc[3] & 0xffffffffu) : 0;
     info.heavy_pairs = heavy_pairs;
+    info.cartesian_bound = h[15] + heavy_pairs;  // the frequent keys' cross products are exact
     if (mode != MODE_EMIT) return JN_OK;
     // ---- 5. exact allocation and the emit pass ----
     JN_TRY(out_prepare(c, s, total, *plan));
@@ -1051,7 +1057,7 @@ struct HashBatchRun : BatchRun {
             const uint64_t* roff = start;
             const uint64_t* soff = start + P;
             if ((st = launch(c, K_ITEMS, k_items, dim3((unsigned)ceil_div(P, 256)), dim3(256), 0, roff, soff, (int)P,
-                             cap, items)) != JN_OK)
+                             cap, items, (unsigned long long*)nullptr)) != JN_OK)
                 break;
             if ((st = scan_u64(c, items, iprefix, (int64_t)P)) != JN_OK) break;
             if ((st = launch(c, K_ITEMS, k_item_desc, dim3((unsigned)ceil_div(item_bound, 256)), dim3(256), 0, roff,

@@ -216,6 +216,7 @@ jn_status run_nlj(jn_ctx* c, const Cols<K>& R, const Cols<K>& S, const jn_pred& 
     info.r_survivors = (uint64_t)R.n;
     info.s_survivors = (uint64_t)S.n;
     info.prefilter = 0;
+    info.cartesian_bound = (uint64_t)R.n * (uint64_t)S.n;  // every pair is compared
     if (mode != MODE_EMIT) return JN_OK;
     JN_TRY(out_prepare(c, s, h[0], *plan));
     if (h[0] > 0) {

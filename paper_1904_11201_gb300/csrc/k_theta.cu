@@ -113,21 +113,24 @@ __global__ void k_set_theta_one(long long* band, int* op, int* groups, long long
 }
 
 // items[p] = R chunks of the window of group y of its join x S chunks of y.
+// With `bound`, adds sum_y |window of y| * |S_y| to it: the pairs the
+// compared regions hold (Eq. (rsize)'s allocation for them).
 __global__ void k_theta_items(const uint64_t* __restrict__ roff, const uint64_t* __restrict__ soff, ThetaSet ts,
-                              int P, uint64_t* __restrict__ items) {
+                              int P, uint64_t* __restrict__ items, unsigned long long* __restrict__ bound) {
     const int p = blockIdx.x * blockDim.x + threadIdx.x;
-    if (p >= P) return;
-    const int inst = p >> ts.lg, y = p & ((1 << ts.lg) - 1), G = ts.groups[inst];
-    if (y >= G) {
-        items[p] = 0;
-        return;
+    uint64_t nrw = 0, ns = 0;
+    if (p < P) {
+        const int inst = p >> ts.lg, y = p & ((1 << ts.lg) - 1), G = ts.groups[inst];
+        if (y < G) {
+            const int dg = band_groups(ts.prm[inst], ts.band[inst], G);
+            const int base = inst << ts.lg;
+            const int x0 = base + max(0, y - dg), x1 = base + min(G - 1, y + dg);
+            nrw = roff[x1 + 1] - roff[x0];
+            ns = soff[p + 1] - soff[p];
+        }
+        items[p] = (nrw && ns) ? ((nrw + TH_RCAP - 1) / TH_RCAP) * ((ns + TH_SCH - 1) / TH_SCH) : 0;
     }
-    const int dg = band_groups(ts.prm[inst], ts.band[inst], G);
-    const int base = inst << ts.lg;
-    const int x0 = base + max(0, y - dg), x1 = base + min(G - 1, y + dg);
-    const uint64_t nrw = roff[x1 + 1] - roff[x0];
-    const uint64_t ns = soff[p + 1] - soff[p];
-    items[p] = (nrw && ns) ? ((nrw + TH_RCAP - 1) / TH_RCAP) * ((ns + TH_SCH - 1) / TH_SCH) : 0;
+    if (bound) warp_add_to(bound, nrw * ns);  // < |R| * |S| < 2^62: no overflow
 }
 
 // BAND: window + fine buckets; !BAND: diagonal group, every pair compared.
@@ -494,6 +497,7 @@ static jn_status run_theta_t(jn_ctx* c, const Cols<K>& R, const Cols<K>& S, int 
     JN_TRY(s.get(&mm, 2));
     JN_TRY(s.get(&prm, 1));
     JN_TRY(s.get(&d_small, 4));
+    JN_TRY(zero(c, d_small, 4 * sizeof(uint64_t)));
     const K* rg = B ? R.key2 : R.key;
     const K* sg = B ? S.key2 : S.key;
     JN_TRY(launch(c, K_MINMAX, k_mm_init, dim3(1), dim3(1), 0, mm));
@@ -517,7 +521,7 @@ static jn_status run_theta_t(jn_ctx* c, const Cols<K>& R, const Cols<K>& S, int 
     JN_TRY(s.get(&items, G));
     JN_TRY(s.get(&ipre, G + 1));
     JN_TRY(launch(c, K_ITEMS, k_theta_items, dim3((G + 255) / 256), dim3(256), 0, (const uint64_t*)roff,
-                  (const uint64_t*)soff, ts, G, items));
+                  (const uint64_t*)soff, ts, G, items, (unsigned long long*)(d_small + 3)));
     JN_TRY(scan_u64(c, items, ipre, G));
     // ---- cross regions (one-column predicate only) ----
     uint64_t *cross = nullptr, *coff = nullptr, *chunks = nullptr, *cpre = nullptr;
@@ -533,8 +537,9 @@ static jn_status run_theta_t(jn_ctx* c, const Cols<K>& R, const Cols<K>& S, int 
         JN_TRY(scan_u64(c, chunks, cpre, G));
     }
     JN_CUDA(c, cudaMemcpyAsync(d_small, ipre + G, 8, cudaMemcpyDeviceToDevice, c->stream));
-    uint64_t nitems = 0;
-    JN_TRY(read_back(c, d_small, &nitems, 1));
+    uint64_t h0[4];
+    JN_TRY(read_back(c, d_small, h0, 4));
+    const uint64_t nitems = h0[0], compared = h0[3];
     unsigned long long *ival, *chk;
     uint64_t* ioff;
     JN_TRY(s.get(&ival, nitems + 1));
@@ -587,6 +592,7 @@ static jn_status run_theta_t(jn_ctx* c, const Cols<K>& R, const Cols<K>& S, int 
     info.r_survivors = (uint64_t)R.n;
     info.s_survivors = (uint64_t)S.n;
     info.prefilter = 0;
+    info.cartesian_bound = compared + crossn;  // cross regions are written whole
     if (mode != MODE_EMIT) return JN_OK;
     JN_TRY(out_prepare(c, s, total, *plan));
     if (diag) {
@@ -850,7 +856,8 @@ struct BandBatchRun : BatchRun {
                                  SC_FMAX, (const uint32_t*)nullptr, 0u, cur, prow, c->d_err)) != JN_OK)
                     break;
                 if ((st = launch(c, K_ITEMS, k_theta_items, dim3((unsigned)ceil_div(P, 256)), dim3(256), 0,
-                                 (const uint64_t*)start, (const uint64_t*)(start + P), ts, (int)P, items)) != JN_OK)
+                                 (const uint64_t*)start, (const uint64_t*)(start + P), ts, (int)P, items,
+                                 (unsigned long long*)nullptr)) != JN_OK)
                     break;
                 if ((st = scan_u64(c, items, ipre, (int64_t)P)) != JN_OK) break;
             } while (0);

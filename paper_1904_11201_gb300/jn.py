@@ -90,7 +90,8 @@ class RunInfo(ctypes.Structure):
                 ("kernel_launches", ctypes.c_uint64), ("prefilter", ctypes.c_int32),
                 ("radix_bits", ctypes.c_int32), ("radix_bits1", ctypes.c_int32),
                 ("filter_bits", ctypes.c_int32), ("scratch_peak", ctypes.c_uint64),
-                ("heavy_pairs", ctypes.c_uint64), ("reserved", ctypes.c_uint64 * 4)]
+                ("heavy_pairs", ctypes.c_uint64), ("cartesian_bound", ctypes.c_uint64),
+                ("reserved", ctypes.c_uint64 * 3)]
 
 
 ADMIT_FN = ctypes.CFUNCTYPE(ctypes.c_int, ctypes.c_void_p, ctypes.c_uint64, ctypes.c_uint64)

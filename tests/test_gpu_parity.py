@@ -242,14 +242,21 @@ def test_nested_loop_all_predicates(ctx, dt):
         assert c == exp.shape[0] and h == O.checksum_pairs(exp)
 
 
-def test_nested_loop_conjunctive_band_64k_scaled(ctx):
+@pytest.mark.parametrize("tile_r", [0, 512, 4096])
+def test_nested_loop_conjunctive_band_64k_scaled(ctx, tile_r):
     # the two-column band predicate of the 64K x 1M tiled workload, at 8K x 64K
-    nr, ns, w = 8192, 65536, 24414 // 16
+    # (plus ragged tails), for the default and the smallest and largest R tiles
+    nr, ns, w = 8192 + 77, 65536 + 1001, 24414 // 16
     ra, rk = datagen.band_columns(nr, 24, seed=4, stream=0)
     sa, sk = datagen.band_columns(ns, 24, seed=4, stream=1)
     exp = canon(O.band_join_sorted(ra.numpy(), rk.numpy(), sa.numpy(), sk.numpy(), O.LT, w))
-    got = jn.jn_nested_loop(ctx, jn.table(ra.to(DEV), rk.to(DEV)), jn.table(sa.to(DEV), sk.to(DEV)),
-                            jn.pred(jn.JN_LT, jn.JN_ANY, w))
+    ctx.set_tuning(nlj_tile_r=tile_r)
+    try:
+        R, S = jn.table(ra.to(DEV), rk.to(DEV)), jn.table(sa.to(DEV), sk.to(DEV))
+        got = jn.jn_nested_loop(ctx, R, S, jn.pred(jn.JN_LT, jn.JN_ANY, w))
+        assert jn.jn_count(ctx, jn.JN_ALGO_NLJ, R, S, jn.pred(jn.JN_LT, jn.JN_ANY, w)) == exp.shape[0]
+    finally:
+        ctx.set_tuning(nlj_tile_r=0)
     assert np.array_equal(canon(got), exp)
 
 
@@ -452,3 +459,52 @@ def test_host_output_copied_back_in_slices(ctx):
         # every pair joins equal keys
         g = got.long()
         assert torch.equal(r[g[:, 0]], s[g[:, 1]])
+
+
+# ------------------------------------------------ Eq. (rsize) bound report --
+
+def test_cartesian_bound_reports(ctx):
+    # the bound the paper would allocate, against the exact count the joins use
+    r = keys(30000, 0, 5000, 61, 0)
+    s = keys(50000, 0, 5000, 61, 1)
+    R, S = jn.table(r.to(DEV)), jn.table(s.to(DEV))
+    n = O.hash_join(r.numpy(), s.numpy(), count_only=True)
+    for pre, bits in ((0, 4), (1, 4), (0, 1)):
+        ctx.set_tuning(prefilter=pre, radix_bits=bits)
+        try:
+            assert jn.jn_count(ctx, jn.JN_ALGO_HASH, R, S) == n
+            info = ctx.run_info()
+        finally:
+            ctx.set_tuning(prefilter=-1, radix_bits=0)
+        assert n <= info["cartesian_bound"] <= 30000 * 50000
+    # one key on both sides: one partition (or the cross-product path) holds it all
+    one_r, one_s = torch.full((3000,), 7, dtype=torch.int32), torch.full((2000,), 7, dtype=torch.int32)
+    for heavy in (0, 64):
+        ctx.set_tuning(heavy=heavy)
+        try:
+            assert jn.jn_count(ctx, jn.JN_ALGO_HASH, jn.table(one_r.to(DEV)), jn.table(one_s.to(DEV))) == 6_000_000
+            assert ctx.run_info()["cartesian_bound"] == 6_000_000
+        finally:
+            ctx.set_tuning(heavy=-1)
+    # disjoint keys, both tables filtered: nothing survives, nothing is allocated
+    ctx.set_tuning(prefilter=1)
+    try:
+        assert jn.jn_count(ctx, jn.JN_ALGO_HASH, jn.table(keys(9000, 0, 100, 62, 0).to(DEV)),
+                           jn.table(keys(9000, 200, 300, 62, 1).to(DEV))) == 0
+        assert ctx.run_info()["cartesian_bound"] == 0
+    finally:
+        ctx.set_tuning(prefilter=-1)
+    # the nested loop compares every pair; the theta join its regions
+    ra, rk = datagen.band_columns(4000, 16, seed=63, stream=0)
+    sa, sk = datagen.band_columns(9000, 16, seed=63, stream=1)
+    RB, SB = jn.table(ra.to(DEV), rk.to(DEV)), jn.table(sa.to(DEV), sk.to(DEV))
+    pr = jn.pred(jn.JN_LT, jn.JN_ANY, 30)
+    exp = O.band_join_sorted(ra.numpy(), rk.numpy(), sa.numpy(), sk.numpy(), O.LT, 30, count_only=True)
+    assert jn.jn_count(ctx, jn.JN_ALGO_NLJ, RB, SB, pr) == exp
+    assert ctx.run_info()["cartesian_bound"] == 4000 * 9000
+    assert jn.jn_count(ctx, jn.JN_ALGO_THETA, RB, SB, pr) == exp
+    assert exp <= ctx.run_info()["cartesian_bound"] < 4000 * 9000
+    one = jn.pred(jn.JN_LT)
+    exp1 = O.nested_loop(ra.numpy(), sa.numpy(), op_a=O.LT, count_only=True)
+    assert jn.jn_count(ctx, jn.JN_ALGO_THETA, RB, SB, one) == exp1
+    assert exp1 <= ctx.run_info()["cartesian_bound"] <= 4000 * 9000
