@@ -90,7 +90,9 @@ typedef struct {
  * never depends on them. */
 typedef struct {
     int32_t prefilter;     /* Algorithm 1's common-key filter: -1 auto, 0 off, 1 both
-                              tables, 2 only S (by R's keys), 3 only R (by S's keys)    */
+                              tables, 2 only S (by R's keys), 3 only R (by S's keys).
+                              Auto: off below 2^22 rows in all; else only the larger
+                              table when it has twice the other's rows, else both     */
     int32_t radix_bits;    /* total partition bits of the hash join (0 = auto, <= 20)   */
     int32_t radix_bits1;   /* bits of the first partition pass (0 = auto)               */
     int32_t filter_bits;   /* log2 of the key-presence bitmap size (0 = auto, <= 30)    */
