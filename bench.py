@@ -47,7 +47,7 @@ def peaks():
 
 def make_workload(name, theta, device, small=False, rows_log2=0, r_rows_log2=0):
     from paper_1904_11201_gb300 import datagen as D
-    if name in ("hash", "hash_int64"):
+    if name in ("hash", "hash_int64", "sortmerge"):
         i64 = name == "hash_int64"
         n = (1 << 27) if i64 else (1 << 28)
         dbits = 28
@@ -63,12 +63,15 @@ def make_workload(name, theta, device, small=False, rows_log2=0, r_rows_log2=0):
         r = D.zipf_keys(nr, theta, dbits, seed=0, stream=0, device=device, dtype=dt, cdf=cdf)
         s = D.zipf_keys(n, theta, dbits, seed=0, stream=1, device=device, dtype=dt, cdf=cdf)
         del cdf
-        return {"kind": "hash", "R": (r, None, D.row_ids(nr, device)), "S": (s, None, D.row_ids(n, device)),
-                "config": {"workload": "equi hash join %dM x %dM %s keys, Zipf theta=%g over 2^%d"
-                           % (nr >> 20, n >> 20, "int64" if i64 else "int32", theta, dbits),
+        sm = name == "sortmerge"
+        return {"kind": "hash", "sort": sm, "R": (r, None, D.row_ids(nr, device)), "S": (s, None, D.row_ids(n, device)),
+                "config": {"workload": "equi %s join %dM x %dM %s keys, Zipf theta=%g over 2^%d"
+                           % ("sort-merge" if sm else "hash", nr >> 20, n >> 20, "int64" if i64 else "int32", theta,
+                              dbits),
                            "R_rows": nr, "S_rows": n, "key": "int64" if i64 else "int32",
                            "zipf_theta": theta, "key_domain": 1 << dbits, "payload": "int32 row id",
-                           "algo": "jn_hash (pre-filter, 2-pass radix partition, count, emit)"}}
+                           "algo": ("jn_sort_merge" if sm else "jn_hash")
+                           + " (pre-filter, 2-pass radix partition, count, emit)"}}
     if name == "band":
         nr, ns = (1 << 20, 1 << 24) if not small else (1 << 16, 1 << 20)
         ra, rk = D.band_columns(nr, 24, seed=0, stream=0, device=device)
@@ -107,13 +110,14 @@ class Counted:
 
 def run_step(jn, ctx, w, R, S, out=None):
     if w.get("aggregate"):
-        algo = {"hash": jn.JN_ALGO_HASH, "band": jn.JN_ALGO_THETA, "nlj": jn.JN_ALGO_NLJ}[w["kind"]]
+        algo = {"hash": jn.JN_ALGO_SORT if w.get("sort") else jn.JN_ALGO_HASH, "band": jn.JN_ALGO_THETA,
+                "nlj": jn.JN_ALGO_NLJ}[w["kind"]]
         pr = jn.pred(w["op"], jn.JN_ANY, w["band"]) if w["kind"] == "band" else None
         if "pred" in w:
             pr = jn.pred(*w["pred"])
         return Counted(*jn.jn_aggregate(ctx, algo, R, S, pr))
     if w["kind"] == "hash":
-        return jn.jn_hash(ctx, R, S, out=out)
+        return (jn.jn_sort_merge if w.get("sort") else jn.jn_hash)(ctx, R, S, out=out)
     if w["kind"] == "band":
         return jn.jn_theta(ctx, R, S, w["op"], w["band"], out=out)
     pr = jn.pred(*w["pred"]) if "pred" in w else None
@@ -123,7 +127,7 @@ def run_step(jn, ctx, w, R, S, out=None):
 # ------------------------------------------------------------ roofline --
 
 def algorithmic_bytes(kind, info, nr, ns, m, ksize):
-    """Algorithmic bytes per kernel for one step (measurement)."""
+    """Algorithmic bytes per kernel for one step: what each kernel must read and write at least."""
     sr, ss = info["r_survivors"], info["s_survivors"]
     surv = sr + ss
     row = ksize + 4
@@ -134,6 +138,9 @@ def algorithmic_bytes(kind, info, nr, ns, m, ksize):
             "histogram": ksize * surv,
             "hash_count": row * surv,
             "hash_emit": row * surv + 8 * (m - info.get("heavy_pairs", 0)),
+            "sort_chunks": 2 * row * sr,
+            "sort_count": row * surv,
+            "sort_emit": row * surv + 8 * (m - info.get("heavy_pairs", 0)),
             "cross_emit": 8 * info.get("heavy_pairs", 0),
         }
     if kind == "band":
@@ -828,7 +835,8 @@ def main():
     torch.cuda.synchronize()
     if args.prefilter == -1 and not args.radix_bits and not args.theta_groups and not args.no_autotune:
         # the library's autotuner times its candidate tunings before the warm-up
-        algo = {"hash": jn.JN_ALGO_HASH, "band": jn.JN_ALGO_THETA, "nlj": jn.JN_ALGO_NLJ}[w["kind"]]
+        algo = {"hash": jn.JN_ALGO_SORT if w.get("sort") else jn.JN_ALGO_HASH, "band": jn.JN_ALGO_THETA,
+                "nlj": jn.JN_ALGO_NLJ}[w["kind"]]
         pr = None
         if w["kind"] == "band":
             pr = jn.pred(w["op"], jn.JN_ANY, w["band"])

@@ -56,7 +56,7 @@ typedef enum {
     JN_EQ = 0, JN_NE = 1, JN_LT = 2, JN_LE = 3, JN_GT = 4, JN_GE = 5, JN_ANY = 6
 } jn_op;
 
-typedef enum { JN_ALGO_NLJ = 0, JN_ALGO_HASH = 1, JN_ALGO_THETA = 2 } jn_algo;
+typedef enum { JN_ALGO_NLJ = 0, JN_ALGO_HASH = 1, JN_ALGO_THETA = 2, JN_ALGO_SORT = 3 } jn_algo;
 
 /* One table as column buffers (Sec. 3.2.2).  Signed integers; all key columns
  * of one call share key_type. */
@@ -204,6 +204,15 @@ jn_status jn_nested_loop(jn_ctx* ctx, const jn_table* R, const jn_table* S, cons
 jn_status jn_hash(jn_ctx* ctx, const jn_table* R, const jn_table* S,
                   jn_pair** out, uint64_t capacity, uint64_t* n_out);
 
+/* Equi sort-merge join: the sort-based category that Sec. 2.3 names beside
+ * the nested-loop and hash joins (Sec. 6 leaves it for future work).  The
+ * pre-filter, partitioning, frequent-key path, count pass and exact
+ * allocation are those of jn_hash; within a partition each chunk of R rows
+ * is sorted by key in shared memory and every S row finds its run of equal
+ * keys by binary search.  Same arguments, result and errors as jn_hash. */
+jn_status jn_sort_merge(jn_ctx* ctx, const jn_table* R, const jn_table* S,
+                        jn_pair** out, uint64_t capacity, uint64_t* n_out);
+
 /* Theta join (Sec. 4.2, Algorithm 3).
  *   band < 0 : predicate R.key op S.key.  Both tables are cut into ranges with
  *              shared boundaries; off-diagonal regions whose ranges already
@@ -284,7 +293,7 @@ jn_status jn_batch_count(jn_ctx* ctx, int32_t count, const jn_join* joins, uint6
  * library-allocated output that is freed at once, when the exact result fits
  * a quarter of the free device memory, else count and checksum -- applies the
  * fastest to the context and caches it per (algorithm, key type, size class);
- * *best (may be NULL) receives it.  The knobs tried never change a result: the hash join's
+ * *best (may be NULL) receives it.  The knobs tried never change a result: the hash and sort-merge joins'
  * partition bits and pre-filter, the theta join's group count, the nested
  * loop's R tile.  It stands in for the hand sweep of the partition parameter
  * alpha in Sec. 5.1.4 and 5.2.4. */

@@ -47,7 +47,7 @@ int hash_cap(int32_t key_type);
 
 template <typename K>
 jn_status run_hash(jn_ctx* c, const Cols<K>& R, const Cols<K>& S, int mode, OutPlan* plan,
-                   RunResult* res);
+                   RunResult* res, bool sort_merge = false);
 
 // A batch of joins run as one: prepare() (all passes up to the exact
 // counts) fills total and the per-join offsets; emit() writes the pairs to

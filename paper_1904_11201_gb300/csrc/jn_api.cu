@@ -179,16 +179,18 @@ static jn_status dispatch(jn_ctx* c, int algo, const jn_table* R, const jn_table
     Scratch s(c);
     HostCopies hc(c);
     Cols<K> r, q;
-    const bool use2 = algo != JN_ALGO_HASH;
-    // the hash join samples a column, then reads it in two streaming passes
-    const bool in_place = algo == JN_ALGO_HASH && (c->tune.host_io & 1);
+    const bool equi = algo == JN_ALGO_HASH || algo == JN_ALGO_SORT;
+    const bool use2 = !equi;
+    // the equi joins sample a column, then read it in two streaming passes
+    const bool in_place = equi && (c->tune.host_io & 1);
     JN_TRY(stage<K>(c, s, hc, R, use2, &r, in_place));
     hc.first_table = false;
     JN_TRY(stage<K>(c, s, hc, S, use2, &q, in_place));
     JN_TRY(hc.start());
-    if (algo != JN_ALGO_HASH) JN_TRY(wait_copies(c, true));  // the hash join waits per phase
+    if (!equi) JN_TRY(wait_copies(c, true));  // the equi joins wait per phase
     switch (algo) {
         case JN_ALGO_HASH: return run_hash<K>(c, r, q, mode, plan, res);
+        case JN_ALGO_SORT: return run_hash<K>(c, r, q, mode, plan, res, true);
         case JN_ALGO_NLJ: return run_nlj<K>(c, r, q, pr, mode, plan, res);
         case JN_ALGO_THETA: return run_theta<K>(c, r, q, pr.op_a, pr.band, mode, plan, res);
     }
@@ -206,10 +208,10 @@ static jn_status run(jn_ctx* c, int algo, const jn_table* R, const jn_table* S, 
     pr.band = -1;
     if (pred) pr = *pred;
     if (!valid_op(pr.op_a) || !valid_op(pr.op_k)) return fail(c, JN_ERR_INVALID, "unknown predicate op");
-    if (algo == JN_ALGO_HASH) {
+    if (algo == JN_ALGO_HASH || algo == JN_ALGO_SORT) {
         const bool second = pred && (pr.band >= 0 || pr.op_k != JN_ANY);
         if (pr.op_a != JN_EQ || second)
-            return fail(c, JN_ERR_UNSUPPORTED, "the hash join takes the equality predicate only");
+            return fail(c, JN_ERR_UNSUPPORTED, "the hash and sort-merge joins take the equality predicate only");
     }
     const bool need2 = algo == JN_ALGO_THETA && pr.band >= 0;
     JN_TRY(check_table(c, R, "R", need2));
@@ -319,6 +321,11 @@ jn_status jn_nested_loop(jn_ctx* ctx, const jn_table* R, const jn_table* S, cons
 jn_status jn_hash(jn_ctx* ctx, const jn_table* R, const jn_table* S, jn_pair** out, uint64_t capacity,
                   uint64_t* n_out) {
     return run(ctx, JN_ALGO_HASH, R, S, nullptr, MODE_EMIT, out, capacity, n_out, nullptr, nullptr);
+}
+
+jn_status jn_sort_merge(jn_ctx* ctx, const jn_table* R, const jn_table* S, jn_pair** out, uint64_t capacity,
+                        uint64_t* n_out) {
+    return run(ctx, JN_ALGO_SORT, R, S, nullptr, MODE_EMIT, out, capacity, n_out, nullptr, nullptr);
 }
 
 static jn_status batch_entry(jn_ctx* ctx, int32_t count, const jn_join* joins, jn_pair** out, uint64_t capacity,

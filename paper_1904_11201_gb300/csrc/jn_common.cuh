@@ -36,6 +36,9 @@ enum KernelId {
     K_GATHER,
     K_BATCH,
     K_MISC,
+    K_SORT_COUNT,
+    K_SORT_EMIT,
+    K_SORT_CHUNKS,
     K_COUNT_IDS
 };
 

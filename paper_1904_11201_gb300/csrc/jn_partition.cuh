@@ -85,6 +85,13 @@ struct RangeDigit {
     }
 };
 
+// One join work item: rows [rbeg, rbeg + rn) of R against all rows
+// [sbeg, sbeg + sn) of S of the same partition.
+struct Item {
+    unsigned long long rbeg, sbeg;
+    int rn, sn;
+};
+
 // ---------------------------------------------------------------- rows --
 // Partitioned intermediates are stored as rows (array of structs): the key,
 // an optional second column and the payload of one tuple sit together, so a

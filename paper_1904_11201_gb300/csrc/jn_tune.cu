@@ -52,7 +52,7 @@ jn_status jn_autotune(jn_ctx* c, int32_t algo, const jn_table* R, const jn_table
     }
     const jn_tuning base = c->tune;
     std::vector<jn_tuning> cands;
-    if (algo == JN_ALGO_HASH) {
+    if (algo == JN_ALGO_HASH || algo == JN_ALGO_SORT) {
         const int cap = jnx::hash_cap(R->key_type);
         for (int pre : {0, 1, 2, 3}) {  // off, both tables, only S, only R
             const uint64_t target = (pre == 1 || pre == 3) ? cap : cap / 2;  // R rows per partition
@@ -103,6 +103,7 @@ jn_status jn_autotune(jn_ctx* c, int32_t algo, const jn_table* R, const jn_table
         jn_pair* out = nullptr;
         uint64_t n = 0;
         jn_status r = algo == JN_ALGO_HASH    ? jn_hash(c, R, S, &out, 0, &n)
+                      : algo == JN_ALGO_SORT  ? jn_sort_merge(c, R, S, &out, 0, &n)
                       : algo == JN_ALGO_THETA ? jn_theta(c, R, S, pr.op_a, pr.band, &out, 0, &n)
                                               : jn_nested_loop(c, R, S, pred, &out, 0, &n);
         if (out) {

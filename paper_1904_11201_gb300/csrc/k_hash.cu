@@ -22,6 +22,7 @@
 #include "jn_algos.h"
 #include "jn_heavy.cuh"
 #include "jn_partition.cuh"
+#include "jn_sortjoin.cuh"
 
 namespace jnx {
 
@@ -70,12 +71,6 @@ __host__ __device__ constexpr int cap_of() {
     return sizeof(K) == 4 ? HJ_CAP : HJ_CAP / 2;
 }
 
-// One work item: rows [rbeg, rbeg + rn) of R against all rows
-// [sbeg, sbeg + sn) of S of the same partition.
-struct Item {
-    unsigned long long rbeg, sbeg;
-    int rn, sn;
-};
 
 // items[it] for every item: its partition is the last p with item_prefix[p] <= it.
 __global__ void k_item_desc(const uint64_t* __restrict__ roff, const uint64_t* __restrict__ soff,
@@ -170,7 +165,6 @@ k_hash_join(const Row<K, false>* __restrict__ rrows, const Row<K, false>* __rest
             uint64_t item_hi = ~0ull) {
     using R = Row<K, false>;
     using L = JoinSmem<K, MODE>;
-    constexpr int CAP = L::CAP;
     constexpr int TS = L::TS;
     extern __shared__ __align__(128) unsigned char smem[];
     unsigned char* g_r = smem;
@@ -638,7 +632,7 @@ static jn_status partition_table(jn_ctx* c, Scratch& s, const Cols<K>& T, int b1
 
 template <typename K>
 jn_status run_hash(jn_ctx* c, const Cols<K>& R, const Cols<K>& S, int mode, OutPlan* plan,
-                   RunResult* res) {
+                   RunResult* res, bool sort_merge) {
     using RW = Row<K, false>;
     const uint64_t nr = (uint64_t)R.n, ns = (uint64_t)S.n;
     jn_run_info& info = c->info;
@@ -817,6 +811,7 @@ jn_status run_hash(jn_ctx* c, const Cols<K>& R, const Cols<K>& S, int mode, OutP
     uint64_t* ioff;
     JN_TRY(s.get(&idesc, nitems + 1));
     JN_TRY(s.get(&ival, nitems + 1));
+    RW* rsorted = nullptr;  // sort-merge: the R chunks sorted by key
     JN_TRY(s.get(&ioff, nitems + 1));
     JN_TRY(s.get(&chk, 1));
     JN_TRY(zero(c, chk, 8));
@@ -825,13 +820,30 @@ jn_status run_hash(jn_ctx* c, const Cols<K>& R, const Cols<K>& S, int mode, OutP
                       (const uint64_t*)PR.off, (const uint64_t*)PS.off, (const uint64_t*)iprefix, P, cap_of<K>(),
                       idesc));
         const int cm = mode == MODE_AGG ? MODE_AGG : MODE_COUNT;
-        const size_t smc = hash_smem<K>(cm);
-        auto kc = (cm == MODE_AGG) ? (skewed ? k_hash_join<K, MODE_AGG, true> : k_hash_join<K, MODE_AGG, false>)
-                                   : (skewed ? k_hash_join<K, MODE_COUNT, true> : k_hash_join<K, MODE_COUNT, false>);
-        const int gj = (int)min((uint64_t)persistent_grid(c, (const void*)kc, HJ_T, smc), nitems);
-        JN_TRY(launch(c, K_HASH_COUNT, kc, dim3(gj), dim3(HJ_T), smc, (const RW*)PR.rows, (const RW*)PS.rows,
-                      (const Item*)idesc, (const uint64_t*)(iprefix + P), b, ival, chk, (const uint64_t*)nullptr,
-                      (jn_pair*)nullptr, c->d_err, (uint64_t)0, ~0ull));
+        if (sort_merge) {
+            // every R chunk sorted by key once, into a copy the count and emit passes read
+            JN_TRY(s.get(&rsorted, (size_t)R.n + HJ_PAD));
+            auto kso = k_sort_chunks<K>;
+            const size_t sms = SortJoinSmem<K>::sort_bytes(cap_of<K>());
+            const int gs = (int)min((uint64_t)persistent_grid(c, (const void*)kso, SJ_T, sms), nitems);
+            JN_TRY(launch(c, K_SORT_CHUNKS, kso, dim3(gs), dim3(SJ_T), sms, (const RW*)PR.rows, rsorted,
+                          (const Item*)idesc, (const uint64_t*)(iprefix + P), cap_of<K>()));
+            auto kc = cm == MODE_AGG ? k_sort_join<K, MODE_AGG> : k_sort_join<K, MODE_COUNT>;
+            const size_t smc = SortJoinSmem<K>::bytes(cap_of<K>(), cm);
+            const int gj = (int)min((uint64_t)persistent_grid(c, (const void*)kc, SJ_T, smc), nitems);
+            JN_TRY(launch(c, K_SORT_COUNT, kc, dim3(gj), dim3(SJ_T), smc, (const RW*)rsorted, (const RW*)PS.rows,
+                          (const Item*)idesc, (const uint64_t*)(iprefix + P), cap_of<K>(), ival, chk,
+                          (const uint64_t*)nullptr, (jn_pair*)nullptr, (uint64_t)0, ~0ull));
+        } else {
+            const size_t smc = hash_smem<K>(cm);
+            auto kc = (cm == MODE_AGG)
+                          ? (skewed ? k_hash_join<K, MODE_AGG, true> : k_hash_join<K, MODE_AGG, false>)
+                          : (skewed ? k_hash_join<K, MODE_COUNT, true> : k_hash_join<K, MODE_COUNT, false>);
+            const int gj = (int)min((uint64_t)persistent_grid(c, (const void*)kc, HJ_T, smc), nitems);
+            JN_TRY(launch(c, K_HASH_COUNT, kc, dim3(gj), dim3(HJ_T), smc, (const RW*)PR.rows, (const RW*)PS.rows,
+                          (const Item*)idesc, (const uint64_t*)(iprefix + P), b, ival, chk,
+                          (const uint64_t*)nullptr, (jn_pair*)nullptr, c->d_err, (uint64_t)0, ~0ull));
+        }
     }
     JN_TRY(scan_u64(c, reinterpret_cast<const uint64_t*>(ival), ioff, (int64_t)nitems));
     // ---- heavy keys: c_R(h) * c_S(h) pairs each ----
@@ -899,15 +911,23 @@ jn_status run_hash(jn_ctx* c, const Cols<K>& R, const Cols<K>& S, int mode, OutP
     };
     if (normal > 0) {
         auto ke = skewed ? k_hash_join<K, MODE_EMIT, true> : k_hash_join<K, MODE_EMIT, false>;
-        const size_t sme = hash_smem<K>(MODE_EMIT);
-        const uint64_t pg = (uint64_t)persistent_grid(c, (const void*)ke, HJ_T, sme);
+        auto kse = k_sort_join<K, MODE_EMIT>;
+        const size_t sme = sort_merge ? SortJoinSmem<K>::bytes(cap_of<K>(), MODE_EMIT) : hash_smem<K>(MODE_EMIT);
+        const uint64_t pg = sort_merge ? (uint64_t)persistent_grid(c, (const void*)kse, SJ_T, sme)
+                                       : (uint64_t)persistent_grid(c, (const void*)ke, HJ_T, sme);
         for (int k = 0; k < nsl; k++) {
             if (ib[k + 1] == ib[k]) continue;
             const int ge = (int)min(pg, ib[k + 1] - ib[k]);
-            JN_TRY(launch(c, K_HASH_EMIT, ke, dim3(ge), dim3(HJ_T), sme, (const RW*)PR.rows, (const RW*)PS.rows,
-                          (const Item*)idesc, (const uint64_t*)(iprefix + P), b, (unsigned long long*)nullptr,
-                          (unsigned long long*)nullptr, (const uint64_t*)ioff, plan->dev, c->d_err, ib[k],
-                          ib[k + 1]));
+            if (sort_merge)
+                JN_TRY(launch(c, K_SORT_EMIT, kse, dim3(ge), dim3(SJ_T), sme, (const RW*)rsorted,
+                              (const RW*)PS.rows, (const Item*)idesc, (const uint64_t*)(iprefix + P), cap_of<K>(),
+                              (unsigned long long*)nullptr, (unsigned long long*)nullptr, (const uint64_t*)ioff,
+                              plan->dev, ib[k], ib[k + 1]));
+            else
+                JN_TRY(launch(c, K_HASH_EMIT, ke, dim3(ge), dim3(HJ_T), sme, (const RW*)PR.rows,
+                              (const RW*)PS.rows, (const Item*)idesc, (const uint64_t*)(iprefix + P), b,
+                              (unsigned long long*)nullptr, (unsigned long long*)nullptr, (const uint64_t*)ioff,
+                              plan->dev, c->d_err, ib[k], ib[k + 1]));
             if (nsl > 1) JN_TRY(copy_back(ob[k], ob[k + 1]));
         }
     }
@@ -1128,8 +1148,8 @@ template jn_status batch_hash_prepare<int64_t>(jn_ctx*, int, const Cols<int64_t>
 int hash_cap(int32_t key_type) { return key_type == JN_KEY_I32 ? cap_of<int32_t>() : cap_of<int64_t>(); }
 
 template jn_status run_hash<int32_t>(jn_ctx*, const Cols<int32_t>&, const Cols<int32_t>&, int,
-                                     OutPlan*, RunResult*);
+                                     OutPlan*, RunResult*, bool);
 template jn_status run_hash<int64_t>(jn_ctx*, const Cols<int64_t>&, const Cols<int64_t>&, int,
-                                     OutPlan*, RunResult*);
+                                     OutPlan*, RunResult*, bool);
 
 }  // namespace jnx

@@ -23,7 +23,7 @@ JN_OK, JN_ERR_INVALID, JN_ERR_OOM, JN_ERR_CAPACITY, JN_ERR_CUDA, JN_ERR_TIMEOUT,
     JN_ERR_UNSUPPORTED = range(7)
 JN_KEY_I32, JN_KEY_I64 = 4, 8
 JN_EQ, JN_NE, JN_LT, JN_LE, JN_GT, JN_GE, JN_ANY = range(7)
-JN_ALGO_NLJ, JN_ALGO_HASH, JN_ALGO_THETA = range(3)
+JN_ALGO_NLJ, JN_ALGO_HASH, JN_ALGO_THETA, JN_ALGO_SORT = range(4)
 OPS = {"=": JN_EQ, "!=": JN_NE, "<": JN_LT, "<=": JN_LE, ">": JN_GT, ">=": JN_GE, "any": JN_ANY}
 
 
@@ -124,6 +124,8 @@ _SIGS = {
                                       ctypes.POINTER(ctypes.c_uint64)]),
     "jn_hash": (ctypes.c_int, [_P, ctypes.POINTER(Table), ctypes.POINTER(Table), ctypes.POINTER(_P),
                                ctypes.c_uint64, ctypes.POINTER(ctypes.c_uint64)]),
+    "jn_sort_merge": (ctypes.c_int, [_P, ctypes.POINTER(Table), ctypes.POINTER(Table), ctypes.POINTER(_P),
+                                     ctypes.c_uint64, ctypes.POINTER(ctypes.c_uint64)]),
     "jn_theta": (ctypes.c_int, [_P, ctypes.POINTER(Table), ctypes.POINTER(Table), ctypes.c_int32,
                                 ctypes.c_int64, ctypes.POINTER(_P), ctypes.c_uint64,
                                 ctypes.POINTER(ctypes.c_uint64)]),
@@ -357,6 +359,10 @@ def jn_nested_loop(ctx: Context, R: TableRef, S: TableRef, pr: Pred = None, out=
 
 def jn_hash(ctx: Context, R: TableRef, S: TableRef, out=None):
     return _emit(ctx, load().jn_hash, (ctypes.byref(R.t), ctypes.byref(S.t)), out)
+
+
+def jn_sort_merge(ctx: Context, R: TableRef, S: TableRef, out=None):
+    return _emit(ctx, load().jn_sort_merge, (ctypes.byref(R.t), ctypes.byref(S.t)), out)
 
 
 def jn_theta(ctx: Context, R: TableRef, S: TableRef, op: int, band: int = -1, out=None):

@@ -508,3 +508,66 @@ def test_cartesian_bound_reports(ctx):
     exp1 = O.nested_loop(ra.numpy(), sa.numpy(), op_a=O.LT, count_only=True)
     assert jn.jn_count(ctx, jn.JN_ALGO_THETA, RB, SB, one) == exp1
     assert exp1 <= ctx.run_info()["cartesian_bound"] <= 4000 * 9000
+
+
+# ------------------------------------------------------ sort-merge join --
+
+@pytest.mark.parametrize("case", HASH_CASES)
+@pytest.mark.parametrize("pre", [0, 1])
+def test_sort_merge_cases(ctx, case, pre):
+    nr, ns, lo, hi, dt = case
+    r = keys(nr, lo, hi, 13, 0, dt)
+    s = keys(ns, lo, hi, 13, 1, dt)
+    if dt == torch.int32:
+        r, s = with_edges(r, [I32_MIN, I32_MAX], 15), with_edges(s, [I32_MAX, I32_MIN], 16)
+    else:
+        r, s = with_edges(r, [I64_MIN, I64_MAX], 15), with_edges(s, [I64_MAX, I64_MIN], 16)
+    exp = canon(O.hash_join(r.numpy(), s.numpy()))
+    ctx.set_tuning(prefilter=pre)
+    try:
+        R, S = jn.table(r.to(DEV)), jn.table(s.to(DEV))
+        got = jn.jn_sort_merge(ctx, R, S)
+        assert jn.jn_count(ctx, jn.JN_ALGO_SORT, R, S) == exp.shape[0]
+    finally:
+        ctx.set_tuning(prefilter=-1)
+    assert np.array_equal(canon(got), exp)
+
+
+@pytest.mark.parametrize("dt", [torch.int32, torch.int64])
+def test_sort_merge_full_chunks_and_extreme_keys(ctx, dt):
+    # one radix bit: partitions hold many full R chunks (4096 / 2048 rows), so
+    # the in-chunk sort runs at its full length; the largest key equals the
+    # padding's sort key and must still sort before the padding
+    top = I32_MAX if dt == torch.int32 else I64_MAX
+    bot = I32_MIN if dt == torch.int32 else I64_MIN
+    r = torch.cat([torch.full((5000,), top, dtype=dt), keys(20000, -40, 40, 17, 0, dt),
+                   torch.full((300,), bot, dtype=dt)])
+    s = torch.cat([keys(7000, -40, 40, 17, 1, dt), torch.full((3,), top, dtype=dt),
+                   torch.full((2,), bot, dtype=dt)])
+    r = r[datagen.uniform_int(r.numel(), 0, 1 << 30, 18, 0, dtype=torch.int64).argsort()]
+    rp = datagen.uniform_int(r.numel(), I32_MIN, I32_MAX, 18, 1)
+    sp = datagen.uniform_int(s.numel(), I32_MIN, I32_MAX, 18, 2)
+    exp = canon(O.hash_join(r.numpy(), s.numpy(), rp.numpy(), sp.numpy()))
+    cnt, chk = O.equi_count_checksum(r.numpy(), s.numpy(), rp.numpy(), sp.numpy())
+    R = jn.table(r.to(DEV), payload=rp.to(DEV))
+    S = jn.table(s.to(DEV), payload=sp.to(DEV))
+    for heavy in (0, 64):
+        ctx.set_tuning(radix_bits=1, radix_bits1=1, prefilter=0, heavy=heavy)
+        try:
+            got = jn.jn_sort_merge(ctx, R, S)
+            assert jn.jn_aggregate(ctx, jn.JN_ALGO_SORT, R, S) == (cnt, chk)
+        finally:
+            ctx.set_tuning(radix_bits=0, radix_bits1=0, prefilter=-1, heavy=-1)
+        assert np.array_equal(canon(got), exp)
+
+
+def test_sort_merge_equals_hash_join_zipf(ctx):
+    r = skewed(200000, 1 << 16, 0.8, 19, 0, torch.int32)
+    s = skewed(300000, 1 << 16, 0.8, 19, 1, torch.int32)
+    R, S = jn.table(r.to(DEV)), jn.table(s.to(DEV))
+    a = canon(jn.jn_hash(ctx, R, S))
+    b = canon(jn.jn_sort_merge(ctx, R, S))
+    assert np.array_equal(a, b)
+    assert a.shape[0] == O.hash_join(r.numpy(), s.numpy(), count_only=True)
+    with pytest.raises(jn.JoinError):
+        jn.jn_count(ctx, jn.JN_ALGO_SORT, R, S, jn.pred(jn.JN_LT))
