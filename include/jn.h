@@ -204,12 +204,13 @@ jn_status jn_nested_loop(jn_ctx* ctx, const jn_table* R, const jn_table* S, cons
 jn_status jn_hash(jn_ctx* ctx, const jn_table* R, const jn_table* S,
                   jn_pair** out, uint64_t capacity, uint64_t* n_out);
 
-/* Equi sort-merge join: the sort-based category that Sec. 2.3 names beside
- * the nested-loop and hash joins (Sec. 6 leaves it for future work).  The
- * pre-filter, partitioning, frequent-key path, count pass and exact
- * allocation are those of jn_hash; within a partition each chunk of R rows
- * is sorted by key in shared memory and every S row finds its run of equal
- * keys by binary search.  Same arguments, result and errors as jn_hash. */
+/* Equi sort-merge join: the third category of join algorithms in Sec. 2.3
+ * (sort, then walk the tables in order), beside the nested-loop and hash
+ * joins the paper builds.  The pre-filter, partitioning, frequent-key path,
+ * count pass and exact allocation are those of jn_hash; within a partition
+ * each chunk of R rows is sorted by key in shared memory and every S row
+ * finds its run of equal keys by binary search.  Same arguments, result and
+ * errors as jn_hash. */
 jn_status jn_sort_merge(jn_ctx* ctx, const jn_table* R, const jn_table* S,
                         jn_pair** out, uint64_t capacity, uint64_t* n_out);
 

@@ -1,6 +1,6 @@
-// Sort-merge equi join of one hash partition pair (the sort-merge category
-// of join algorithms the paper names beside nested-loop and hash joins,
-// Sec. 2.3, and leaves for future work, Sec. 6).
+// Sort-merge equi join of one hash partition pair: the third category of
+// join algorithms in Sec. 2.3 (sort both tables, then walk them in order),
+// beside the nested-loop and hash joins the paper builds.
 //
 // It takes the same work items as the hash join kernel: a chunk of at most
 // cap R rows of one partition against every S row of that partition.
