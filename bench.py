@@ -12,7 +12,8 @@ tuples/s ("join tuples/s in+out"), with the inputs already in device memory.
 copies the host columns in and the pairs out inside the timed region.
 
 Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
-                       [--workload hash|hash_int64|band|nlj] [--theta T]
+                       [--workload hash|hash_int64|sortmerge|band|nlj|nlj_band|batch|serve]
+                       [--theta T] [--sweep]
 Under torchrun (N > 1) every rank runs its own replica of the workload
 (the join does not shard without a collective); value sums all ranks.
 """
