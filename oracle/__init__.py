@@ -49,6 +49,8 @@ def _load():
         lib.or_nested_loop.argtypes = [P, P, P, I64, P, P, P, I64, I, I, I, I64, P, U64]
         lib.or_hash_join.restype = U64
         lib.or_hash_join.argtypes = [P, P, I64, P, P, I64, I, P, U64]
+        lib.or_sort_merge_join.restype = U64
+        lib.or_sort_merge_join.argtypes = [P, P, I64, P, P, I64, I, P, U64]
         lib.or_checksum_pairs.restype = U64
         lib.or_checksum_pairs.argtypes = [P, U64]
         lib.or_f.restype = U64
@@ -134,6 +136,18 @@ def hash_join(rkey, skey, rpay=None, spay=None, count_only=False):
     if count_only:
         return int(lib.or_hash_join(*args, None, 0))
     return _two_call(lib.or_hash_join, *args)
+
+
+def sort_merge_join(rkey, skey, rpay=None, spay=None, count_only=False):
+    """O5: sort-merge equi join (sort both tables, walk them in key order)."""
+    lib = _load()
+    rkey, skey = _keys(rkey), _keys(skey)
+    ks = _ksize(rkey, skey)
+    rp, sp = _pay(rpay, len(rkey)), _pay(spay, len(skey))
+    args = (_ptr(rkey), _ptr(rp), len(rkey), _ptr(skey), _ptr(sp), len(skey), ks)
+    if count_only:
+        return int(lib.or_sort_merge_join(*args, None, 0))
+    return _two_call(lib.or_sort_merge_join, *args)
 
 
 def band_join_sorted(rkey, rkey2, skey, skey2, op_a, band, rpay=None, spay=None,

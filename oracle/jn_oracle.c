@@ -203,6 +203,46 @@ static int64_t* sorted_order(const void* keys, int ksize, int64_t n, int64_t** v
 }
 
 /* ------------------------------------------------------------------------ *
+ * O5: sort-merge equi join, the third join category of Sec. 2.3: sort both
+ * tables on the key, then walk the two sorted sequences together; a run of
+ * equal keys in R meets the run of the same key in S as their cross product.
+ * Same conventions and return value as or_hash_join.
+ * ------------------------------------------------------------------------ */
+uint64_t or_sort_merge_join(const void* rkey, const int32_t* rpay, int64_t nr,
+                            const void* skey, const int32_t* spay, int64_t ns,
+                            int ksize, or_pair* out, uint64_t cap) {
+    int64_t *rv, *sv;
+    int64_t* ri = sorted_order(rkey, ksize, nr, &rv);
+    int64_t* si = sorted_order(skey, ksize, ns, &sv);
+    uint64_t cnt = 0;
+    int64_t i = 0, j = 0;
+    while (i < nr && j < ns) {
+        const int64_t a = rv[ri[i]], b = sv[si[j]];
+        if (a < b) {
+            i++;
+        } else if (b < a) {
+            j++;
+        } else {
+            int64_t i1 = i, j1 = j;  /* the two runs of key a */
+            while (i1 < nr && rv[ri[i1]] == a) i1++;
+            while (j1 < ns && sv[si[j1]] == a) j1++;
+            for (int64_t x = i; x < i1; x++)
+                for (int64_t y = j; y < j1; y++) {
+                    put(out, cap, cnt, pay_at(rpay, ri[x]), pay_at(spay, si[y]));
+                    cnt++;
+                }
+            i = i1;
+            j = j1;
+        }
+    }
+    free(ri);
+    free(si);
+    free(rv);
+    free(sv);
+    return cnt;
+}
+
+/* ------------------------------------------------------------------------ *
  * The separable checksum used to compare result sets too large to store
  * (Sec. 5.3 runs large theta joins "without storing the results").  For a
  * result multiset M of pairs (r, s):

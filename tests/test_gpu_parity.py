@@ -522,7 +522,7 @@ def test_sort_merge_cases(ctx, case, pre):
         r, s = with_edges(r, [I32_MIN, I32_MAX], 15), with_edges(s, [I32_MAX, I32_MIN], 16)
     else:
         r, s = with_edges(r, [I64_MIN, I64_MAX], 15), with_edges(s, [I64_MAX, I64_MIN], 16)
-    exp = canon(O.hash_join(r.numpy(), s.numpy()))
+    exp = canon(O.sort_merge_join(r.numpy(), s.numpy()))
     ctx.set_tuning(prefilter=pre)
     try:
         R, S = jn.table(r.to(DEV)), jn.table(s.to(DEV))
@@ -547,7 +547,7 @@ def test_sort_merge_full_chunks_and_extreme_keys(ctx, dt):
     r = r[datagen.uniform_int(r.numel(), 0, 1 << 30, 18, 0, dtype=torch.int64).argsort()]
     rp = datagen.uniform_int(r.numel(), I32_MIN, I32_MAX, 18, 1)
     sp = datagen.uniform_int(s.numel(), I32_MIN, I32_MAX, 18, 2)
-    exp = canon(O.hash_join(r.numpy(), s.numpy(), rp.numpy(), sp.numpy()))
+    exp = canon(O.sort_merge_join(r.numpy(), s.numpy(), rp.numpy(), sp.numpy()))
     cnt, chk = O.equi_count_checksum(r.numpy(), s.numpy(), rp.numpy(), sp.numpy())
     R = jn.table(r.to(DEV), payload=rp.to(DEV))
     S = jn.table(s.to(DEV), payload=sp.to(DEV))

@@ -80,6 +80,7 @@ def test_golden_equi_and_theta():
     assert len(pairs) == cnt
     assert as_list(O.nested_loop(r, s, op_a=O.EQ)) == sorted(pairs)
     assert as_list(O.hash_join(r, s)) == sorted(pairs)
+    assert as_list(O.sort_merge_join(r, s)) == sorted(pairs)
     c, _ = O.equi_count_checksum(r, s)
     assert c == cnt
     cnt, pairs = blocks[("<",)]
@@ -149,6 +150,25 @@ def test_band_extreme_values_no_overflow():
 
 
 @pytest.mark.parametrize("dtype", [np.int32, np.int64])
+def test_sort_merge_join_equals_brute_force(dtype):
+    # O5 against the pure-Python definition, with both extremes of the type
+    # (where a careless order key or sentinel would merge the wrong runs)
+    lo, hi = (I32_MIN, I32_MAX) if dtype == np.int32 else (I64_MIN, I64_MAX)
+    rng = np.random.default_rng(9)
+    for trial in range(25):
+        nr, ns = int(rng.integers(0, 60)), int(rng.integers(0, 80))
+        ra = rng.integers(-3, 4, nr).astype(dtype)
+        sa = rng.integers(-3, 4, ns).astype(dtype)
+        if nr > 2:
+            ra[0], ra[1] = lo, hi
+        if ns > 2:
+            sa[-1], sa[-2] = hi, lo
+        assert as_list(O.sort_merge_join(ra, sa)) == brute(ra, sa, O.EQ)
+        assert O.sort_merge_join(ra, sa, count_only=True) == len(brute(ra, sa, O.EQ))
+    assert as_list(O.sort_merge_join(np.array([], dtype=dtype), np.array([1], dtype=dtype))) == []
+
+
+@pytest.mark.parametrize("dtype", [np.int32, np.int64])
 def test_hash_join_equals_nested_loop(dtype):
     rng = np.random.default_rng(5)
     for trial in range(30):
@@ -161,6 +181,7 @@ def test_hash_join_equals_nested_loop(dtype):
         a = O.sort_pairs(O.nested_loop(ra, sa, rpay=rp, spay=sp))
         b = O.sort_pairs(O.hash_join(ra, sa, rp, sp))
         assert np.array_equal(a, b)
+        assert np.array_equal(a, O.sort_pairs(O.sort_merge_join(ra, sa, rp, sp)))
 
 
 # ---------------------------------------------------------- closed form --
