@@ -48,6 +48,9 @@ constexpr int HJ_SCH = JN_HJ_SCH;    // S rows per staged chunk
 #define JN_SLICE_PAIRS (1ull << 24)  // host outputs of at least this many pairs are copied back in slices
 #endif
 constexpr int HJ_PAD = 16;         // rows of slack for 16-byte widened copies
+// the sort-merge kernels hold a chunk as 8 words per thread and index its
+// rows in 15 bits
+static_assert(HJ_CAP <= 8 * SJ_T && HJ_CAP < 0x8000, "R chunk larger than the sort-merge kernels hold");
 constexpr uint64_t CE_PAIRS = 1u << 16;  // cross-product pairs per work chunk
 
 // Items of partition p: one per chunk of HJ_CAP R rows; each item probes
