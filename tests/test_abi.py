@@ -44,6 +44,9 @@ def test_library_loads_and_answers_without_gpu(lib_path):
     # NULL context arguments are rejected without touching a device
     assert lib.jn_set_profiling(None, 1) == jn.JN_ERR_INVALID
     assert lib.jn_count(None, 0, None, None, None, None) == jn.JN_ERR_INVALID
+    assert lib.jn_sort_merge(None, None, None, None, 0, None) == jn.JN_ERR_INVALID
+    assert lib.jn_selftest_wait(None, 1, 0, None) == jn.JN_ERR_INVALID
+    assert lib.jn_autotune(None, jn.JN_ALGO_SORT, None, None, None, None) == jn.JN_ERR_INVALID
     h = ctypes.c_void_p()
     st = lib.jn_create(ctypes.byref(h), 0, None)
     # no GPU in this container: creation must fail cleanly, not crash
@@ -54,3 +57,12 @@ def test_library_loads_and_answers_without_gpu(lib_path):
 
 def test_build_targets_sm103a_only():
     assert B.ARCH == ["-gencode", "arch=compute_103a,code=sm_103a"]
+
+
+def test_missing_library_fails_loudly():
+    # the product path has no fallback: without libjn.so the binding raises
+    code = ("from paper_1904_11201_gb300 import jn\n"
+            "try:\n    jn.load('/nonexistent/libjn.so')\nexcept RuntimeError as e:\n"
+            "    print('raised', 'not found' in str(e))\n")
+    out = subprocess.run(["python", "-c", code], capture_output=True, text=True, cwd=ROOT).stdout
+    assert out.strip() == "raised True"
