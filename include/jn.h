@@ -105,7 +105,16 @@ typedef struct {
     int32_t host_io;       /* page-locked host buffers: bit 0 = the hash join reads its
                               input columns in place, bit 1 = emitted pairs are written in
                               place; otherwise copied (0 = copy both)                  */
-    int32_t reserved[6];
+    int32_t hash_path;     /* partitioning of the hash and sort-merge joins: 0 auto, 1 two
+                              radix passes over both tables (pre-filter on both sides by
+                              global presence bitmaps), 2 regions: one radix pass, then
+                              one block per region splits it further and keeps the
+                              pre-filter's bitmap slice of that region in shared memory,
+                              thinning one table (the one `prefilter` names; the larger,
+                              S on a tie, when both are named).  Auto = 2 unless the
+                              columns are read in place from host memory or more than
+                              18 partition bits are needed                              */
+    int32_t reserved[5];
 } jn_tuning;
 
 /* Per-kernel launch statistics (profiling mode). */
@@ -137,7 +146,9 @@ typedef struct {
                                    products), over the theta join's compared and
                                    cross regions, or |R| * |S| for the nested loop;
                                    always >= result                                 */
-    uint64_t reserved[3];
+    uint64_t hash_path;         /* partition path taken by the hash / sort-merge join:
+                                   1 two radix passes, 2 regions (see jn_tuning)     */
+    uint64_t reserved[2];
 } jn_run_info;
 
 typedef struct jn_ctx jn_ctx;

@@ -39,6 +39,9 @@ enum KernelId {
     K_SORT_COUNT,
     K_SORT_EMIT,
     K_SORT_CHUNKS,
+    K_CHUNK_HIST,
+    K_REGION1,
+    K_REGION2,
     K_COUNT_IDS
 };
 

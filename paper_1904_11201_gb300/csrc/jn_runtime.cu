@@ -17,7 +17,8 @@ static const char* kKernelNames[K_COUNT_IDS] = {
     "work_items",   "hash_count",   "hash_emit",   "heavy_sample", "heavy_select",
     "cross_emit",   "scan_reduce",  "scan_top",    "scan_down",   "nlj_count",
     "nlj_emit",     "minmax",       "theta_count", "theta_emit",  "gather",
-    "batch",        "misc",         "sort_count",  "sort_emit",   "sort_chunks"};
+    "batch",        "misc",         "sort_count",  "sort_emit",   "sort_chunks",
+    "chunk_hist",   "region1",      "region2"};
 
 const char* kernel_name(int kid) {
     return (kid >= 0 && kid < K_COUNT_IDS) ? kKernelNames[kid] : "?";

@@ -22,6 +22,7 @@
 #include "jn_algos.h"
 #include "jn_heavy.cuh"
 #include "jn_partition.cuh"
+#include "jn_region.cuh"
 #include "jn_sortjoin.cuh"
 
 namespace jnx {
@@ -53,16 +54,26 @@ constexpr int HJ_PAD = 16;         // rows of slack for 16-byte widened copies
 static_assert(HJ_CAP <= 8 * SJ_T && HJ_CAP < 0x8000, "R chunk larger than the sort-merge kernels hold");
 constexpr uint64_t CE_PAIRS = 1u << 16;  // cross-product pairs per work chunk
 
+// The partitions of one table: either P + 1 offsets (partition p = rows
+// [off[p], off[p + 1])) or a first row and a row count per partition.
+struct PartView {
+    const uint64_t* off;
+    const uint32_t* beg;
+    const uint32_t* cnt;
+    __device__ __forceinline__ uint64_t first(int p) const { return off ? off[p] : (uint64_t)beg[p]; }
+    __device__ __forceinline__ uint64_t rows(int p) const { return off ? off[p + 1] - off[p] : (uint64_t)cnt[p]; }
+};
+
 // Items of partition p: one per chunk of HJ_CAP R rows; each item probes
 // every S row of the partition, HJ_SCH rows at a time.  With `bound`, adds
 // sum_p |R_p| * |S_p| to it: Eq. (rsize)'s allocation for these partitions.
-__global__ void k_items(const uint64_t* __restrict__ roff, const uint64_t* __restrict__ soff, int P, int cap,
-                        uint64_t* __restrict__ items, unsigned long long* __restrict__ bound) {
+__global__ void k_items(PartView rv, PartView sv, int P, int cap, uint64_t* __restrict__ items,
+                        unsigned long long* __restrict__ bound) {
     const int p = blockIdx.x * blockDim.x + threadIdx.x;
     uint64_t nr = 0, ns = 0;
     if (p < P) {
-        nr = roff[p + 1] - roff[p];
-        ns = soff[p + 1] - soff[p];
+        nr = rv.rows(p);
+        ns = sv.rows(p);
         items[p] = (nr && ns) ? (nr + cap - 1) / cap : 0;
     }
     if (bound) warp_add_to(bound, nr * ns);  // < |R| * |S| < 2^62: no overflow
@@ -76,18 +87,18 @@ __host__ __device__ constexpr int cap_of() {
 
 
 // items[it] for every item: its partition is the last p with item_prefix[p] <= it.
-__global__ void k_item_desc(const uint64_t* __restrict__ roff, const uint64_t* __restrict__ soff,
-                            const uint64_t* __restrict__ item_prefix, int P, int cap, Item* __restrict__ items) {
+__global__ void k_item_desc(PartView rv, PartView sv, const uint64_t* __restrict__ item_prefix, int P, int cap,
+                            Item* __restrict__ items) {
     const uint64_t it = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (it >= item_prefix[P]) return;
     const int p = find_segment(item_prefix, P, it);
     const uint64_t rc = it - item_prefix[p];
-    const uint64_t nr = roff[p + 1] - roff[p];
+    const uint64_t nr = rv.rows(p);
     Item d;
-    d.rbeg = roff[p] + rc * cap;
+    d.rbeg = rv.first(p) + rc * cap;
     d.rn = (int)min((uint64_t)cap, nr - rc * cap);
-    d.sbeg = soff[p];
-    d.sn = (int)(soff[p + 1] - soff[p]);
+    d.sbeg = sv.first(p);
+    d.sn = (int)sv.rows(p);
     items[it] = d;
 }
 
@@ -240,13 +251,17 @@ k_hash_join(const Row<K, false>* __restrict__ rrows, const Row<K, false>* __rest
         Item dn;
         if (has_next) dn = items[itn];  // its R rows load once this item's R staging is free
         const int rn = d.rn;
+        // slots this item uses: twice its R rows (at most the table) -- a slot
+        // is picked by multiply-shift, so any count works; the skewed variant
+        // keeps the whole table
+        const int ts = (MERGE || MODE == MODE_EMIT) ? TS : min(TS, max(64, 2 * rn));
         if (MODE == MODE_EMIT) {
             for (int i = threadIdx.x; i <= TS; i += HJ_T) {
                 e_tab[i].key = KMIN;
                 e_tab[i].packed = 0;
             }
         } else {
-            for (int i = threadIdx.x; i < TS; i += HJ_T) {
+            for (int i = threadIdx.x; i < ts; i += HJ_T) {
                 o_key[i] = KMIN;
                 o_cnt[i] = 0;
                 if (MODE == MODE_AGG) o_f[i] = 0;
@@ -378,8 +393,8 @@ k_hash_join(const Row<K, false>* __restrict__ rrows, const Row<K, false>* __rest
                     if (MODE == MODE_AGG) atomicAdd(&s_minf, fv);
                     continue;
                 }
-                uint32_t h = oa_slot(khash(x.key), bits, TS);
-                for (int probe = 0; probe < TS; probe++) {
+                uint32_t h = oa_slot(khash(x.key), bits, ts);
+                for (int probe = 0; probe < ts; probe++) {
                     K old;
                     if (sizeof(K) == 4)
                         old = (K)atomicCAS(reinterpret_cast<int*>(o_key) + h, (int)KMIN, (int)x.key);
@@ -391,7 +406,7 @@ k_hash_join(const Row<K, false>* __restrict__ rrows, const Row<K, false>* __rest
                         if (MODE == MODE_AGG) atomicAdd(&o_f[h], fv);
                         break;
                     }
-                    h = (h + 1 == (uint32_t)TS) ? 0u : h + 1;
+                    h = (h + 1 == (uint32_t)ts) ? 0u : h + 1;
                 }
             }
         }
@@ -444,8 +459,8 @@ k_hash_join(const Row<K, false>* __restrict__ rrows, const Row<K, false>* __rest
                         m = s_mincnt;
                         if (MODE == MODE_AGG) fs = s_minf;
                     } else {
-                        uint32_t h = oa_slot(khash(x.key), bits, TS);
-                        for (int probe = 0; probe < TS; probe++) {
+                        uint32_t h = oa_slot(khash(x.key), bits, ts);
+                        for (int probe = 0; probe < ts; probe++) {
                             const K kk = o_key[h];
                             if (kk == x.key) {
                                 m = o_cnt[h];
@@ -453,7 +468,7 @@ k_hash_join(const Row<K, false>* __restrict__ rrows, const Row<K, false>* __rest
                                 break;
                             }
                             if (kk == KMIN) break;
-                            h = (h + 1 == (uint32_t)TS) ? 0u : h + 1;
+                            h = (h + 1 == (uint32_t)ts) ? 0u : h + 1;
                         }
                     }
                 }
@@ -536,9 +551,12 @@ static int persistent_grid(jn_ctx* c, const void* fn, int threads, size_t smem) 
 template <typename K>
 struct Partitioned {
     Row<K, false>* rows = nullptr;
-    uint64_t* off = nullptr;        // P + 1 exact offsets
+    uint64_t* off = nullptr;        // P + 1 exact offsets (two radix passes), or
+    uint32_t* pbeg = nullptr;       // first row and row count per partition (region path)
+    uint32_t* pcnt = nullptr;
     Row<K, false>* hrows = nullptr; // heavy rows grouped by heavy key
     uint64_t* hoff = nullptr;       // HV_MAX + 1 offsets
+    PartView view() const { return off ? PartView{off, nullptr, nullptr} : PartView{nullptr, pbeg, pcnt}; }
 };
 
 template <typename K, typename D1>
@@ -633,6 +651,118 @@ static jn_status partition_table(jn_ctx* c, Scratch& s, const Cols<K>& T, int b1
     return JN_OK;
 }
 
+// Heavy rows of a table (rows [seg[0], seg[1]) of `rows`) grouped by heavy
+// key: rows and HV_MAX + 1 offsets.
+template <typename K>
+static jn_status group_heavy(jn_ctx* c, Scratch& s, const Row<K, false>* rows, uint64_t rows_ok, const uint64_t* seg,
+                             const HeavySet<K>& hs, Partitioned<K>* outp) {
+    using R = Row<K, false>;
+    uint64_t *hseg_c, *htp, *hstart;
+    unsigned long long *hhist, *hcur;
+    R* hr;
+    JN_TRY(s.get(&hseg_c, 2));
+    JN_TRY(s.get(&htp, 3));
+    JN_TRY(s.get(&hhist, HV_MAX));
+    JN_TRY(s.get(&hstart, HV_MAX + 1));
+    JN_TRY(s.get(&hcur, HV_MAX));
+    JN_TRY(s.get(&hr, rows_ok));
+    JN_TRY(zero(c, hhist, sizeof(unsigned long long) * HV_MAX));
+    JN_TRY(launch(c, K_SEGMENTS, k_segments, dim3(1), dim3(32), 0, reinterpret_cast<const unsigned long long*>(seg + 1),
+                  seg, 1, hseg_c, htp, (uint64_t*)nullptr));
+    HeavyIdxDigit<K> dh{hs};
+    auto kh = k_seg_hist_rows<R, HeavyIdxDigit<K>>;
+    const int gh = persistent_grid(c, (const void*)kh, SC_T, sizeof(uint32_t) * HV_MAX);
+    JN_TRY(launch(c, K_HIST, kh, dim3(gh), dim3(SC_T), sizeof(uint32_t) * HV_MAX, rows, seg, (const uint64_t*)hseg_c,
+                  (const uint64_t*)htp, 1, dh, HV_MAX, hhist));
+    JN_TRY(scan_u64(c, reinterpret_cast<const uint64_t*>(hhist), hstart, HV_MAX));
+    JN_TRY(launch(c, K_MISC, k_init_cursor, dim3((HV_MAX + 255) / 256), dim3(256), 0, (const uint64_t*)hstart, hcur,
+                  (int64_t)HV_MAX));
+    auto ks = k_scatter<K, false, false, HeavyIdxDigit<K>>;
+    const size_t sm = scatter_smem<K, false>();
+    const int gs = persistent_grid(c, (const void*)ks, SC_T, sm);
+    PartIn<K, false> in{nullptr, nullptr, nullptr, rows, rows_ok, nullptr, nullptr};
+    JN_TRY(launch(c, K_SCATTER, ks, dim3(gs), dim3(SC_T), sm, in, seg, (const uint64_t*)hseg_c, (const uint64_t*)htp,
+                  1, dh, HV_MAX, (const uint32_t*)nullptr, 0u, hcur, hr, c->d_err));
+    outp->hrows = hr;
+    outp->hoff = hstart;
+    return JN_OK;
+}
+
+// Region path (jn_region.cuh): level-1 regions of both tables (b1 bits of
+// the key hash, plus the heavy digit F1), then one block per region splits it
+// into 2^b2 partitions of rows.  With `filter`, table `first` builds the
+// key-presence slices and the other table is thinned by them (Algorithm 1's
+// pre-filter, one side).  d_small[0] / [1] receive R's / S's rows kept.
+template <typename K, typename D1>
+static jn_status region_partition(jn_ctx* c, Scratch& s, const Cols<K>& R, const Cols<K>& S, int b1, int b2, D1 d1,
+                                  const HeavySet<K>* hs, bool filter, int first, int fb, Partitioned<K>* PR,
+                                  Partitioned<K>* PS, uint64_t* d_small) {
+    using RW = Row<K, false>;
+    using SH = RgShape<K>;
+    const int F1 = 1 << b1, F2 = 1 << b2;
+    const int nd1 = F1 + (hs ? 1 : 0);
+    const int G = c->num_sms;
+    const Cols<K>* T[2] = {&R, &S};
+    Partitioned<K>* P[2] = {PR, PS};
+    RW* rows1[2];
+    uint64_t* start1[2];
+    uint32_t* choff[2];
+    int64_t chunk[2], nch[2];
+    // level-1 histograms of both key columns (the keys land before the payloads)
+    for (int t = 0; t < 2; t++) {
+        const int64_t n = T[t]->n;
+        const int64_t tiles = (int64_t)ceil_div((uint64_t)n, SH::T1);
+        // about eight chunks per block, so blocks finish together
+        const int64_t ct = max((int64_t)1, (int64_t)ceil_div((uint64_t)tiles, 8 * (uint64_t)G));
+        chunk[t] = ct * SH::T1;
+        nch[t] = (int64_t)ceil_div((uint64_t)n, (uint64_t)chunk[t]);
+        uint32_t* hist;
+        uint64_t* tot;
+        JN_TRY(s.get(&hist, (size_t)nch[t] * nd1));
+        JN_TRY(s.get(&choff[t], (size_t)nch[t] * nd1));
+        JN_TRY(s.get(&tot, nd1));
+        JN_TRY(s.get(&start1[t], nd1 + 1));
+        auto kh = k_chunk_hist<K, D1>;
+        JN_TRY(launch(c, K_CHUNK_HIST, kh, dim3((unsigned)min(nch[t], (int64_t)4 * G)), dim3(512), sizeof(uint32_t) * nd1,
+                      T[t]->key, n, chunk[t], d1, nd1, hist));
+        JN_TRY(launch(c, K_CHUNK_HIST, k_chunk_scan, dim3((nd1 + 31) / 32), dim3(32, 32), 0, (const uint32_t*)hist, nch[t],
+                      nd1, choff[t], tot));
+        JN_TRY(scan_u64(c, tot, start1[t], nd1));
+    }
+    const bool keep = !RecomputeDigit<D1>::value;
+    for (int t = 0; t < 2; t++) {
+        JN_TRY(t == 0 ? wait_copies_r(c) : wait_copies(c, true));
+        const int64_t n = T[t]->n;
+        JN_TRY(s.get(&rows1[t], (size_t)n + HJ_PAD));
+        auto k1 = k_region1_scatter<K, D1>;
+        JN_TRY(launch(c, K_REGION1, k1, dim3((unsigned)min(nch[t], (int64_t)G)), dim3(RG_T),
+                      Region1Smem<K>::bytes(keep), T[t]->key, T[t]->pay, n, chunk[t], d1, nd1,
+                      (const uint32_t*)choff[t], (const uint64_t*)start1[t], rows1[t], c->d_err));
+    }
+    // level 2: the building table first, then the thinned one
+    uint32_t* bitmap = nullptr;
+    const int swords = fb - b1 >= 5 ? 1 << (fb - b1 - 5) : 1;
+    if (filter) JN_TRY(s.get(&bitmap, (size_t)F1 * swords));
+    for (int q = 0; q < 2; q++) {
+        const int t = q == 0 ? first : 1 - first;
+        const int64_t n = T[t]->n;
+        RW* rows;
+        uint32_t *pb, *pc;
+        JN_TRY(s.get(&rows, (size_t)n + HJ_PAD));
+        JN_TRY(s.get(&pb, (size_t)F1 * F2));
+        JN_TRY(s.get(&pc, (size_t)F1 * F2));
+        auto k2 = !filter ? k_region2<K, false, false> : q == 0 ? k_region2<K, true, false> : k_region2<K, false, true>;
+        JN_TRY(launch(c, K_REGION2, k2, dim3((unsigned)min(F1, G)), dim3(RG_T), Region2Smem<K>::bytes(),
+                      (const RW*)rows1[t], (uint64_t)n + HJ_PAD, (const uint64_t*)start1[t], F1, b1, b2, bitmap, fb,
+                      rows, pb, pc, reinterpret_cast<unsigned long long*>(d_small + t), c->d_err));
+        P[t]->rows = rows;
+        P[t]->pbeg = pb;
+        P[t]->pcnt = pc;
+        if (hs) JN_TRY(group_heavy<K>(c, s, (const RW*)rows1[t], (uint64_t)n + HJ_PAD, start1[t] + F1, *hs, P[t]));
+    }
+    return JN_OK;
+}
+
 template <typename K>
 jn_status run_hash(jn_ctx* c, const Cols<K>& R, const Cols<K>& S, int mode, OutPlan* plan,
                    RunResult* res, bool sort_merge) {
@@ -667,27 +797,61 @@ jn_status run_hash(jn_ctx* c, const Cols<K>& R, const Cols<K>& S, int mode, OutP
         fside = 1;
     else if (tu.prefilter == 3)
         fside = 2;
-    const bool pre = fside != 0;
-    int b = tu.radix_bits;
-    if (b == 0) {
-        // expected R rows per partition: the table capacity when the filter
-        // will thin R's rows out, half of it otherwise
-        uint64_t target = (fside & 2) ? cap_of<K>() : cap_of<K>() / 2;
-        b = ceil_log2((nr + target - 1) / target);
-        if (b > 20) b = 20;
+    // partition path: regions (one level-1 pass, one block per region for the
+    // second level, the filter built per region in shared memory) unless two
+    // radix passes are asked for or the columns are read in place from host
+    // memory.  The region path thins one table: the one the pre-filter names,
+    // the larger one (S on a tie) when both are asked for.
+    bool region = tu.hash_path != 1 && !R.host && !S.host;
+    const int fside_rg = fside == 3 ? (ns >= nr ? 1 : 2) : fside;
+    auto radix_bits_for = [&](int fs) {
+        int bb = tu.radix_bits;
+        if (bb == 0) {
+            // expected R rows per partition: the table capacity when the filter
+            // will thin R's rows out, half of it otherwise
+            uint64_t target = (fs & 2) ? cap_of<K>() : cap_of<K>() / 2;
+            bb = ceil_log2((nr + target - 1) / target);
+            if (bb > 20) bb = 20;
+        }
+        return bb;
+    };
+    int b = radix_bits_for(region ? fside_rg : fside);
+    int b1 = 0;
+    if (region) {
+        // 512 level-1 regions at most unless the second level would need more
+        // than 8 bits: the level-1 scatter runs at 1.0 ms per 256M rows with
+        // 512 digits and 1.4 ms with 1024 (GB300)
+        b1 = tu.radix_bits1 ? tu.radix_bits1 : max(min(b, 9), b - 8);
+        if (b1 > b) b1 = b;
+        if (b1 > 10 || b - b1 > 8) region = false;  // beyond the region kernels' digit tables
+        else fside = fside_rg;
+        if (!region) b = radix_bits_for(fside);
     }
-    int b1 = tu.radix_bits1 ? tu.radix_bits1 : b / 2;
-    if (b1 > b) b1 = b;
-    const int b1max = heavy ? 9 : 10;  // pass 1 needs F1 (+1 heavy) <= 1024 digits
-    if (b1 > b1max) b1 = b1max;
-    if (b - b1 > 10) b1 = b - 10;
-    if (b1 > b1max) return fail(c, JN_ERR_UNSUPPORTED, "radix bits too large for two passes");
+    if (!region) {
+        b1 = tu.radix_bits1 ? tu.radix_bits1 : b / 2;
+        if (b1 > b) b1 = b;
+        const int b1max = heavy ? 9 : 10;  // pass 1 needs F1 (+1 heavy) <= 1024 digits
+        if (b1 > b1max) b1 = b1max;
+        if (b - b1 > 10) b1 = b - 10;
+        if (b1 > b1max) return fail(c, JN_ERR_UNSUPPORTED, "radix bits too large for two passes");
+    }
+    const bool pre = !region && fside != 0;  // presence bitmaps of the two-pass path
     const int b2 = b - b1;
     const int F1 = 1 << b1, P = 1 << b;
     const int nd1 = F1 + (heavy ? 1 : 0);
     int fb = tu.filter_bits ? tu.filter_bits : ceil_log2(nr + ns) + 1;
-    if (fb < 10) fb = 10;
-    if (fb > 28 && tu.filter_bits == 0) fb = 28;
+    if (region) {
+        // bitmap bits: the building table's key count, rounded up, in slices of
+        // 2^5 .. 2^RG_SLICE_LOG bits per region
+        const uint64_t nb = (fside & 1) ? nr : ns;
+        if (tu.filter_bits == 0) fb = ceil_log2(nb) + 1;
+        if (fb < b1 + 5) fb = b1 + 5;
+        if (fb > b1 + RG_SLICE_LOG) fb = b1 + RG_SLICE_LOG;
+        if (fb > 32) fb = 32;
+    } else {
+        if (fb < 10) fb = 10;
+        if (fb > 28 && tu.filter_bits == 0) fb = 28;
+    }
     const uint64_t fwords = pre ? (uint64_t(1) << fb) / 32 : 0;
     const uint32_t fmask = (uint32_t)((uint64_t(1) << fb) - 1);
 
@@ -699,13 +863,15 @@ jn_status run_hash(jn_ctx* c, const Cols<K>& R, const Cols<K>& S, int mode, OutP
     unsigned long long *h1R, *h1S;
     JN_TRY(s.get(&h1R, nd1));
     JN_TRY(s.get(&h1S, nd1));
-    JN_TRY(zero(c, h1R, sizeof(unsigned long long) * nd1));
-    JN_TRY(zero(c, h1S, sizeof(unsigned long long) * nd1));
-    if (fside & 1) {  // R's keys, filtering S
+    if (!region) {
+        JN_TRY(zero(c, h1R, sizeof(unsigned long long) * nd1));
+        JN_TRY(zero(c, h1S, sizeof(unsigned long long) * nd1));
+    }
+    if (pre && (fside & 1)) {  // R's keys, filtering S
         JN_TRY(s.get(&bmR, fwords));
         JN_TRY(zero(c, bmR, fwords * 4));
     }
-    if (fside & 2) {  // S's keys, filtering R
+    if (pre && (fside & 2)) {  // S's keys, filtering R
         JN_TRY(s.get(&bmS, fwords));
         JN_TRY(zero(c, bmS, fwords * 4));
     }
@@ -775,19 +941,23 @@ jn_status run_hash(jn_ctx* c, const Cols<K>& R, const Cols<K>& S, int mode, OutP
                                        d_small + 1)));
         return JN_OK;
     };
+    auto region_all = [&](auto d1) -> jn_status {
+        return region_partition<K, decltype(d1)>(c, s, R, S, b1, b2, d1, heavy ? &hs : nullptr, fside != 0,
+                                                 (fside & 1) ? 0 : 1, fb, &PR, &PS, d_small);
+    };
     if (heavy) {
         HeavyHashDigit<K> d1{32 - b1, (uint32_t)(F1 - 1), (uint32_t)F1, hs, nullptr};
-        JN_TRY(pass_all(d1));
+        JN_TRY(region ? region_all(d1) : pass_all(d1));
     } else {
         HashDigit d1{32 - b1, (uint32_t)(F1 - 1)};
-        JN_TRY(pass_all(d1));
+        JN_TRY(region ? region_all(d1) : pass_all(d1));
     }
     // ---- 4. work items and the count pass ----
     uint64_t *items, *iprefix;
     JN_TRY(s.get(&items, P));
     JN_TRY(s.get(&iprefix, P + 1));
-    JN_TRY(launch(c, K_ITEMS, k_items, dim3((P + 255) / 256), dim3(256), 0, (const uint64_t*)PR.off,
-                  (const uint64_t*)PS.off, P, cap_of<K>(), items, (unsigned long long*)(d_small + 15)));
+    JN_TRY(launch(c, K_ITEMS, k_items, dim3((P + 255) / 256), dim3(256), 0, PR.view(), PS.view(), P, cap_of<K>(),
+                  items, (unsigned long long*)(d_small + 15)));
     JN_TRY(scan_u64(c, items, iprefix, P));
     uint64_t h[16];
     JN_TRY(launch(c, K_MISC, k_copy_words, dim3(1), dim3(32), 0, (const uint64_t*)(iprefix + P),
@@ -804,7 +974,8 @@ jn_status run_hash(jn_ctx* c, const Cols<K>& R, const Cols<K>& S, int mode, OutP
     info.prefilter = fside == 3 ? 1 : fside == 1 ? 2 : fside == 2 ? 3 : 0;
     info.radix_bits = b;
     info.radix_bits1 = b1;
-    info.filter_bits = pre ? fb : 0;
+    info.filter_bits = fside ? fb : 0;
+    info.hash_path = region ? 2 : 1;
     info.heavy_keys = 0;
     // the join kernel stages rows with 16-byte bulk copies from these arrays
     if ((((uintptr_t)PR.rows) | ((uintptr_t)PS.rows)) & 15)
@@ -819,9 +990,8 @@ jn_status run_hash(jn_ctx* c, const Cols<K>& R, const Cols<K>& S, int mode, OutP
     JN_TRY(s.get(&chk, 1));
     JN_TRY(zero(c, chk, 8));
     if (nitems) {
-        JN_TRY(launch(c, K_ITEMS, k_item_desc, dim3((unsigned)ceil_div(nitems, 256)), dim3(256), 0,
-                      (const uint64_t*)PR.off, (const uint64_t*)PS.off, (const uint64_t*)iprefix, P, cap_of<K>(),
-                      idesc));
+        JN_TRY(launch(c, K_ITEMS, k_item_desc, dim3((unsigned)ceil_div(nitems, 256)), dim3(256), 0, PR.view(),
+                      PS.view(), (const uint64_t*)iprefix, P, cap_of<K>(), idesc));
         const int cm = mode == MODE_AGG ? MODE_AGG : MODE_COUNT;
         if (sort_merge) {
             // every R chunk sorted by key once, into a copy the count and emit passes read
@@ -1079,12 +1249,14 @@ struct HashBatchRun : BatchRun {
                 break;
             const uint64_t* roff = start;
             const uint64_t* soff = start + P;
-            if ((st = launch(c, K_ITEMS, k_items, dim3((unsigned)ceil_div(P, 256)), dim3(256), 0, roff, soff, (int)P,
-                             cap, items, (unsigned long long*)nullptr)) != JN_OK)
+            if ((st = launch(c, K_ITEMS, k_items, dim3((unsigned)ceil_div(P, 256)), dim3(256), 0,
+                             PartView{roff, nullptr, nullptr}, PartView{soff, nullptr, nullptr}, (int)P, cap, items,
+                             (unsigned long long*)nullptr)) != JN_OK)
                 break;
             if ((st = scan_u64(c, items, iprefix, (int64_t)P)) != JN_OK) break;
-            if ((st = launch(c, K_ITEMS, k_item_desc, dim3((unsigned)ceil_div(item_bound, 256)), dim3(256), 0, roff,
-                             soff, (const uint64_t*)iprefix, (int)P, cap, idesc)) != JN_OK)
+            if ((st = launch(c, K_ITEMS, k_item_desc, dim3((unsigned)ceil_div(item_bound, 256)), dim3(256), 0,
+                             PartView{roff, nullptr, nullptr}, PartView{soff, nullptr, nullptr},
+                             (const uint64_t*)iprefix, (int)P, cap, idesc)) != JN_OK)
                 break;
             auto kc = k_hash_join<K, MODE_COUNT, false>;
             const size_t smc = hash_smem<K>(MODE_COUNT);

@@ -80,9 +80,19 @@ HASH_CASES = [
 ]
 
 
+def reported_prefilter(path, pre, nr, ns):
+    """Tables the pre-filter thins, as jn_run_info reports it: the two-pass path
+    filters what it is asked to; the region path filters one table (the larger
+    one, S on a tie, when both are asked for)."""
+    if path == 1 or pre in (0, 2, 3):
+        return pre
+    return 2 if ns >= nr else 3
+
+
 @pytest.mark.parametrize("case", HASH_CASES)
 @pytest.mark.parametrize("pre", [0, 1, 2, 3])  # off, both tables, only S, only R
-def test_hash_cases(ctx, case, pre):
+@pytest.mark.parametrize("path", [1, 2])        # two radix passes, regions
+def test_hash_cases(ctx, case, pre, path):
     nr, ns, lo, hi, dt = case
     r = keys(nr, lo, hi, 3, 0, dt)
     s = keys(ns, lo, hi, 3, 1, dt)
@@ -91,42 +101,91 @@ def test_hash_cases(ctx, case, pre):
     else:
         r, s = with_edges(r, [I64_MIN, I64_MAX], 5), with_edges(s, [I64_MAX, I64_MIN], 6)
     exp = canon(O.hash_join(r.numpy(), s.numpy()))
-    ctx.set_tuning(prefilter=pre)
+    ctx.set_tuning(prefilter=pre, hash_path=path)
     try:
         got = jn.jn_hash(ctx, jn.table(r.to(DEV)), jn.table(s.to(DEV)))
         if nr and ns:
-            assert ctx.run_info()["prefilter"] == pre
+            info = ctx.run_info()
+            assert info["prefilter"] == reported_prefilter(path, pre, nr, ns)
+            assert info["hash_path"] == path
+        c, h = jn.jn_aggregate(ctx, jn.JN_ALGO_HASH, jn.table(r.to(DEV)), jn.table(s.to(DEV)))
     finally:
-        ctx.set_tuning(prefilter=-1)
+        ctx.set_tuning(prefilter=-1, hash_path=0)
     assert np.array_equal(canon(got), exp)
+    assert c == exp.shape[0] and h == O.checksum_pairs(exp)
 
 
 @pytest.mark.parametrize("sizes", [(1 << 20, (1 << 22) + 3, 2), ((1 << 22) + 5, 1 << 20, 3),
                                    ((1 << 21) + 7, (1 << 21) + 1, 1)])
-def test_hash_auto_prefilter_sides(ctx, sizes):
-    # the automatic choice filters only the larger table when one is 2x the other
+@pytest.mark.parametrize("path", [1, 2])
+def test_hash_auto_prefilter_sides(ctx, sizes, path):
+    # the automatic choice filters only the larger table when one is 2x the
+    # other; the region path always filters one table (the larger one)
     nr, ns, side = sizes
     r = keys(nr, 0, 1 << 23, 41, 0)
     s = keys(ns, 0, 1 << 23, 41, 1)
     exp = canon(O.hash_join(r.numpy(), s.numpy()))
-    ctx.set_tuning(prefilter=-1)
-    got = jn.jn_hash(ctx, jn.table(r.to(DEV)), jn.table(s.to(DEV)))
-    assert ctx.run_info()["prefilter"] == side
+    ctx.set_tuning(prefilter=-1, hash_path=path)
+    try:
+        got = jn.jn_hash(ctx, jn.table(r.to(DEV)), jn.table(s.to(DEV)))
+        assert ctx.run_info()["prefilter"] == reported_prefilter(path, side, nr, ns)
+    finally:
+        ctx.set_tuning(hash_path=0)
     assert np.array_equal(canon(got), exp)
 
 
-@pytest.mark.parametrize("bits", [(1, 1), (3, 2), (5, 0), (12, 6), (16, 8)])
-def test_hash_result_independent_of_partitioning(ctx, bits):
+@pytest.mark.parametrize("bits", [(1, 1), (3, 2), (5, 0), (12, 6), (16, 8), (18, 10), (19, 10)])
+@pytest.mark.parametrize("path", [1, 2])
+def test_hash_result_independent_of_partitioning(ctx, bits, path):
     b, b1 = bits
     r = keys(30000, 0, 9000, 8, 0)
     s = keys(45000, 0, 9000, 8, 1)
     exp = canon(O.hash_join(r.numpy(), s.numpy()))
-    ctx.set_tuning(radix_bits=b, radix_bits1=b1, prefilter=1)
+    ctx.set_tuning(radix_bits=b, radix_bits1=b1, prefilter=1, hash_path=path)
     try:
         got = jn.jn_hash(ctx, jn.table(r.to(DEV)), jn.table(s.to(DEV)))
+        # the region path holds up to 10 + 8 bits; beyond, two radix passes run
+        taken = 1 if path == 1 or b - (b1 or min(b, 10)) > 8 else 2
+        assert ctx.run_info()["hash_path"] == taken
     finally:
-        ctx.set_tuning(radix_bits=0, radix_bits1=0, prefilter=-1)
+        ctx.set_tuning(radix_bits=0, radix_bits1=0, prefilter=-1, hash_path=0)
     assert np.array_equal(canon(got), exp)
+
+
+@pytest.mark.parametrize("dt", [torch.int32, torch.int64])
+@pytest.mark.parametrize("pre", [0, 2, 3])
+def test_region_path_many_chunks_ragged(ctx, dt, pre):
+    # level-1 chunks of several tiles, a ragged last tile in every chunk and
+    # region, both filter directions, payloads off a 16-byte boundary
+    nr, ns = 3 * 8192 * 152 + 4099, 2 * 8192 * 152 + 777
+    r = keys(nr, 0, 1 << 22, 13, 0, dt)
+    s = keys(ns, 0, 1 << 22, 13, 1, dt)
+    rp = datagen.uniform_int(nr + 1, I32_MIN, I32_MAX, 13, 2)
+    sp = datagen.uniform_int(ns + 3, I32_MIN, I32_MAX, 13, 3)
+    rpd, spd = rp.to(DEV), sp.to(DEV)
+    R = jn.table(r.to(DEV), payload=rpd[1:])
+    S = jn.table(s.to(DEV), payload=spd[3:])
+    cnt, chk = O.equi_count_checksum(r.numpy(), s.numpy(), rp[1:].numpy(), sp[3:].numpy())
+    ctx.set_tuning(prefilter=pre, hash_path=2)
+    try:
+        got = jn.jn_hash(ctx, R, S)
+        info = ctx.run_info()
+        assert info["hash_path"] == 2 and info["prefilter"] == pre
+        agg = jn.jn_aggregate(ctx, jn.JN_ALGO_HASH, R, S)
+    finally:
+        ctx.set_tuning(prefilter=-1, hash_path=0)
+    assert agg == (cnt, chk)
+    assert got.shape[0] == cnt and O.checksum_pairs(got.cpu().numpy()) == chk
+    exp = canon(O.hash_join(r.numpy(), s.numpy(), rp[1:].numpy(), sp[3:].numpy()))
+    assert np.array_equal(canon(got), exp)
+    # rows kept: every non-heavy row of the unfiltered table, a superset of the
+    # rows with a common key in the filtered one
+    kept = (info["r_survivors"], info["s_survivors"])
+    common_r = int(np.isin(r.numpy(), s.numpy()).sum())
+    common_s = int(np.isin(s.numpy(), r.numpy()).sum())
+    assert kept[0] >= common_r and kept[1] >= common_s
+    if pre == 0:
+        assert kept == (nr, ns)
 
 
 def test_hash_unaligned_and_host_columns(ctx):
@@ -327,8 +386,9 @@ def test_hash_heavy_keys(ctx, theta, dt):
     cnt, chk = O.equi_count_checksum(r.numpy(), s.numpy(), rp.numpy(), sp.numpy())
     R = jn.table(r.to(DEV), payload=rp.to(DEV))
     S = jn.table(s.to(DEV), payload=sp.to(DEV))
-    for heavy, pre in ((64, 1), (0, 1), (64, 2), (64, 3)):
-        ctx.set_tuning(heavy=heavy, prefilter=pre)
+    for heavy, pre, path in ((64, 1, 1), (0, 1, 1), (64, 2, 1), (64, 3, 1), (64, 1, 2), (0, 1, 2), (64, 3, 2),
+                             (64, 0, 2)):
+        ctx.set_tuning(heavy=heavy, prefilter=pre, hash_path=path)
         try:
             assert jn.jn_aggregate(ctx, jn.JN_ALGO_HASH, R, S) == (cnt, chk)
             info = ctx.run_info()
@@ -339,7 +399,7 @@ def test_hash_heavy_keys(ctx, theta, dt):
                 assert got.shape[0] == cnt
                 assert O.checksum_pairs(got.cpu().numpy()) == chk
         finally:
-            ctx.set_tuning(heavy=-1, prefilter=-1)
+            ctx.set_tuning(heavy=-1, prefilter=-1, hash_path=0)
     if cnt <= 3_000_000:
         ctx.set_tuning(heavy=64)
         try:
