@@ -40,7 +40,7 @@ constexpr int RG_T = 512;               // threads of the region kernels (16 row
 constexpr int RG_STAGE = 65536 + 64;    // bytes per staging buffer (a tile and its 16-byte widening)
 constexpr int RG_NDMAX = 1026;          // level-1 digits at most (1024 + the heavy digit, even)
 constexpr int RG_F2MAX = 256;           // level-2 digits at most
-constexpr int RG_SLICE_LOG = 18;        // bitmap bits per region at most (2^18 bits = 32 KB)
+constexpr int RG_SLICE_LOG = 19;        // bitmap bits per region at most (2^19 bits = 64 KB)
 
 // Tile shapes: a staged tile fills one 64 KB stage.
 template <typename K>
