@@ -44,6 +44,10 @@ namespace jnx {
 constexpr int HJ_T = JN_HJ_T;        // threads per join block
 constexpr int HJ_CAP = JN_HJ_CAP;    // R rows per shared-memory table (int32 keys)
 constexpr int HJ_SCH = JN_HJ_SCH;    // S rows per staged chunk
+#ifndef JN_HJ_PU
+#define JN_HJ_PU 4
+#endif
+constexpr int HJ_PU = JN_HJ_PU;      // S rows a thread probes per round
 
 #ifndef JN_SLICE_PAIRS
 #define JN_SLICE_PAIRS (1ull << 24)  // host outputs of at least this many pairs are copied back in slices
@@ -428,24 +432,36 @@ k_hash_join(const Row<K, false>* __restrict__ rrows, const Row<K, false>* __rest
             const int sn = min(HJ_SCH, d.sn - sc * HJ_SCH);
             const R* srow = reinterpret_cast<const R*>((b ? g_s1 : g_s0) + span_off<R>(sbeg));
             const int rounds = (sn + HJ_T - 1) / HJ_T;
-            for (int r = 0; r < rounds; r++) {
-                const int j = r * HJ_T + threadIdx.x;
-                R x;
-                x.key = 0;
-                x.pay = 0;
-                uint32_t m = 0, beg = 0;
-                unsigned long long fs = 0;
-                if (j < sn) {
-                    x = srow[j];
+            // HJ_PU S rows per thread per round: their lookups and warp scans
+            // overlap and one cursor reservation serves them all, while each
+            // row's pairs still go out as one coalesced run per warp
+            for (int r = 0; r < rounds; r += HJ_PU) {
+                R x[HJ_PU];
+                uint32_t m[HJ_PU], beg[HJ_PU];
+                unsigned long long fs[HJ_PU];
+#pragma unroll
+                for (int u = 0; u < HJ_PU; u++) {
+                    const int j = (r + u) * HJ_T + threadIdx.x;
+                    x[u].key = 0;
+                    x[u].pay = 0;
+                    m[u] = 0;
+                    beg[u] = 0;
+                    fs[u] = 0;
+                    if (j < sn) x[u] = srow[j];
+                }
+#pragma unroll
+                for (int u = 0; u < HJ_PU; u++) {
+                    const int j = (r + u) * HJ_T + threadIdx.x;
+                    if (j >= sn) continue;
                     if (MODE == MODE_EMIT) {
                         uint32_t p = 0;
-                        if (x.key == KMIN) {
+                        if (x[u].key == KMIN) {
                             p = e_tab[TS].packed;
                         } else {
-                            uint32_t h = oa_slot(khash(x.key), bits, TS);
+                            uint32_t h = oa_slot(khash(x[u].key), bits, TS);
                             for (int probe = 0; probe < TS; probe++) {
                                 const RunSlot<K> t = e_tab[h];
-                                if (t.key == x.key) {
+                                if (t.key == x[u].key) {
                                     p = t.packed;
                                     break;
                                 }
@@ -453,18 +469,18 @@ k_hash_join(const Row<K, false>* __restrict__ rrows, const Row<K, false>* __rest
                                 h = (h + 1 == (uint32_t)TS) ? 0u : h + 1;
                             }
                         }
-                        m = p >> 16;
-                        beg = (p & 0xffffu) - m;
-                    } else if (x.key == KMIN) {
-                        m = s_mincnt;
-                        if (MODE == MODE_AGG) fs = s_minf;
+                        m[u] = p >> 16;
+                        beg[u] = (p & 0xffffu) - m[u];
+                    } else if (x[u].key == KMIN) {
+                        m[u] = s_mincnt;
+                        if (MODE == MODE_AGG) fs[u] = s_minf;
                     } else {
-                        uint32_t h = oa_slot(khash(x.key), bits, ts);
+                        uint32_t h = oa_slot(khash(x[u].key), bits, ts);
                         for (int probe = 0; probe < ts; probe++) {
                             const K kk = o_key[h];
-                            if (kk == x.key) {
-                                m = o_cnt[h];
-                                if (MODE == MODE_AGG) fs = o_f[h];
+                            if (kk == x[u].key) {
+                                m[u] = o_cnt[h];
+                                if (MODE == MODE_AGG) fs[u] = o_f[h];
                                 break;
                             }
                             if (kk == KMIN) break;
@@ -473,29 +489,41 @@ k_hash_join(const Row<K, false>* __restrict__ rrows, const Row<K, false>* __rest
                     }
                 }
                 if (MODE == MODE_EMIT) {
-                    const uint32_t incl = warp_incl_scan(m);
-                    const uint32_t wt = __shfl_sync(0xffffffffu, incl, 31);
+                    uint32_t incl[HJ_PU], wt[HJ_PU], wsum = 0;
+#pragma unroll
+                    for (int u = 0; u < HJ_PU; u++) {
+                        incl[u] = warp_incl_scan(m[u]);
+                        wt[u] = __shfl_sync(0xffffffffu, incl[u], 31);
+                        wsum += wt[u];
+                    }
                     uint32_t base = 0;
-                    if (lane == 0 && wt) base = atomicAdd(&s_cursor, wt);
+                    if (lane == 0 && wsum) base = atomicAdd(&s_cursor, wsum);
                     base = __shfl_sync(0xffffffffu, base, 0);
-                    const uint64_t o = ibase + base + (incl - m);
-                    // a short run is written by its lane (the lanes' first pairs
-                    // are neighbours and go out together); a long run by the
-                    // whole warp, 32 pairs at a time
-                    const bool longr = m > 4;
-                    if (!longr)
-                        for (uint32_t i = 0; i < m; i++) out[o + i] = jn_pair{s_pay[beg + i], x.pay};
-                    for (unsigned lanes = __ballot_sync(0xffffffffu, longr); lanes; lanes &= lanes - 1) {
-                        const int src = __ffs(lanes) - 1;
-                        const uint32_t bm = __shfl_sync(0xffffffffu, m, src);
-                        const uint32_t bb = __shfl_sync(0xffffffffu, beg, src);
-                        const int32_t bp = __shfl_sync(0xffffffffu, x.pay, src);
-                        const uint64_t bo = __shfl_sync(0xffffffffu, o, src);
-                        for (uint32_t i = lane; i < bm; i += 32) out[bo + i] = jn_pair{s_pay[bb + i], bp};
+#pragma unroll
+                    for (int u = 0; u < HJ_PU; u++) {
+                        const uint64_t o = ibase + base + (incl[u] - m[u]);
+                        base += wt[u];
+                        // a short run is written by its lane (the lanes' first pairs
+                        // are neighbours and go out together); a long run by the
+                        // whole warp, 32 pairs at a time
+                        const bool longr = m[u] > 4;
+                        if (!longr)
+                            for (uint32_t i = 0; i < m[u]; i++) out[o + i] = jn_pair{s_pay[beg[u] + i], x[u].pay};
+                        for (unsigned lanes = __ballot_sync(0xffffffffu, longr); lanes; lanes &= lanes - 1) {
+                            const int src = __ffs(lanes) - 1;
+                            const uint32_t bm = __shfl_sync(0xffffffffu, m[u], src);
+                            const uint32_t bb = __shfl_sync(0xffffffffu, beg[u], src);
+                            const int32_t bp = __shfl_sync(0xffffffffu, x[u].pay, src);
+                            const uint64_t bo = __shfl_sync(0xffffffffu, o, src);
+                            for (uint32_t i = lane; i < bm; i += 32) out[bo + i] = jn_pair{s_pay[bb + i], bp};
+                        }
                     }
                 } else {
-                    acc += m;
-                    if (MODE == MODE_AGG && m) csum += fs * chk_g(x.pay);
+#pragma unroll
+                    for (int u = 0; u < HJ_PU; u++) {
+                        acc += m[u];
+                        if (MODE == MODE_AGG && m[u]) csum += fs[u] * chk_g(x[u].pay);
+                    }
                 }
             }
             __syncthreads();  // this S buffer is free: stage the chunk after next
