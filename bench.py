@@ -4,7 +4,10 @@ Default workload: the large equi-join, R = S = 2^28 rows of (int32 key,
 int32 payload = row id), keys Zipf(theta) over 2^28 values (theta = 0 by
 default), run as the pre-filtered, radix-partitioned hash join with the exact
 count pass and one exact output allocation.  A step is one full jn_hash call
-(pre-filter, two partition passes, count pass, scan, allocation, emit).
+(partition with the pre-filter, count pass, scan, allocation, emit); the
+partition path is the one the library takes (regions by default: one radix
+pass, then one block per region splits it and keeps the pre-filter's bitmap
+slice of the region in shared memory).
 
 Prints one JSON line.  `value` = (|R| + |S| + M) / time per step, in
 tuples/s ("join tuples/s in+out"), with the inputs already in device memory.
@@ -71,8 +74,7 @@ def make_workload(name, theta, device, small=False, rows_log2=0, r_rows_log2=0):
                               dbits),
                            "R_rows": nr, "S_rows": n, "key": "int64" if i64 else "int32",
                            "zipf_theta": theta, "key_domain": 1 << dbits, "payload": "int32 row id",
-                           "algo": ("jn_sort_merge" if sm else "jn_hash")
-                           + " (pre-filter, 2-pass radix partition, count, emit)"}}
+                           "algo": "jn_sort_merge" if sm else "jn_hash"}}
     if name == "band":
         nr, ns = (1 << 20, 1 << 24) if not small else (1 << 16, 1 << 20)
         ra, rk = D.band_columns(nr, 24, seed=0, stream=0, device=device)
@@ -128,21 +130,34 @@ def run_step(jn, ctx, w, R, S, out=None):
 # ------------------------------------------------------------ roofline --
 
 def algorithmic_bytes(kind, info, nr, ns, m, ksize):
-    """Algorithmic bytes per kernel for one step: what each kernel must read and write at least."""
+    """Algorithmic bytes per kernel for one step, as SURVEY 8(d) counts the
+    hash join: the partition step reads every input tuple once and writes
+    every surviving tuple once; the join reads the partitioned copy once and
+    writes 8 bytes per pair.  Intermediate copies (a second partition pass,
+    the region path's level-1 rows) are not algorithmic, so where a step is
+    split over kernels each byte of the floor is credited to exactly one:
+      two radix passes: the four scatter launches together make one pass;
+      region path: level 1 reads the input, level 2 writes the partitioned copy.
+    Kernels outside the floor (histograms, the pre-filter's key read, the count
+    pass, which 8(d) counts as overhead) get the bytes they must move at least."""
     sr, ss = info["r_survivors"], info["s_survivors"]
     surv = sr + ss
     row = ksize + 4
     if kind == "hash":
+        heavy = info.get("heavy_pairs", 0)
         return {
             "presence": ksize * (nr + ns),
-            "scatter": row * (nr + ns) + row * surv + 2 * row * surv,
+            "chunk_hist": ksize * (nr + ns),
+            "scatter": row * (nr + ns) + row * surv,
+            "region1": row * (nr + ns),
+            "region2": row * surv,
             "histogram": ksize * surv,
             "hash_count": row * surv,
-            "hash_emit": row * surv + 8 * (m - info.get("heavy_pairs", 0)),
+            "hash_emit": row * surv + 8 * (m - heavy),
             "sort_chunks": 2 * row * sr,
             "sort_count": row * surv,
-            "sort_emit": row * surv + 8 * (m - info.get("heavy_pairs", 0)),
-            "cross_emit": 8 * info.get("heavy_pairs", 0),
+            "sort_emit": row * surv + 8 * (m - heavy),
+            "cross_emit": 8 * heavy,
         }
     if kind == "band":
         return {
@@ -857,6 +872,11 @@ def main():
         m = out.shape[0]
         del out
     info = ctx.run_info()
+    if w["kind"] == "hash":
+        w["config"]["algo"] += (" (region partition: one radix pass, a block per region splits it with the "
+                                "pre-filter's bitmap slice in shared memory; count, emit)"
+                                if info.get("hash_path") == 2 else
+                                " (pre-filter bitmaps, two radix passes, count, emit)")
 
     ctx.reset_stats()
     ctx.set_profiling(True)
@@ -923,14 +943,10 @@ def main():
                     "frac": a / peak, "traffic": None, "ops_per_pair": ops,
                     "peak_kind": "derived: %d SMs x 128 INT32 lanes x %.0f MHz / %d integer ops per pair"
                                  % (nsm, sm_mhz, ops)}
-    # DRAM traffic per launch of the dominant kernel from one ncu launch list of
-    # this exact workload and tuning (dram__bytes_read.sum + dram__bytes_write.sum);
-    # any other configuration reports null
-    if (roof and roof["kernel"] == "scatter" and args.workload == "hash" and not args.small
-            and not args.rows_log2 and not args.r_rows_log2 and args.theta == 0 and info.get("prefilter") == 1
-            and info.get("radix_bits") == 16):
-        roof["traffic"] = 3.129e9
-        roof["traffic_note"] = "ncu launch list, mean over the four scatter launches of a step"
+    # DRAM traffic (dram__bytes_read.sum + dram__bytes_write.sum) is not taken
+    # here: it comes from ncu captures of the current kernels (profiles/)
+    if roof:
+        roof["traffic"] = None
     floor = None
     if w["kind"] in ("hash", "band"):
         fb = 24 * (nr + ns) + 8 * m

@@ -28,35 +28,90 @@ def ctx():
     c.close()
 
 
-def test_equi_256m_x_256m_theta0(ctx):
-    n, bits = 1 << 28, 28
-    r = D.zipf_keys(n, 0.0, bits, seed=0, stream=0, device=DEV)
-    s = D.zipf_keys(n, 0.0, bits, seed=0, stream=1, device=DEV)
-    ids = D.row_ids(n, DEV)
-    R, S = jn.table(r, payload=ids), jn.table(s, payload=ids)
-    jn.jn_autotune(ctx, jn.JN_ALGO_HASH, R, S)  # the bench's launch configuration
-    out = torch.as_tensor(jn.jn_hash(ctx, R, S), device=DEV)
+def key_counts(keys, others):
+    """Rows of `keys` with each value of `others` (int32 or int64 columns):
+    the multiplicity c(k) of every row's key in the other table."""
+    u, c = torch.unique(keys, return_counts=True)
+    pos = torch.searchsorted(u, others).clamp(max=u.numel() - 1)
+    return torch.where(u[pos] == others, c[pos], torch.zeros_like(c[pos]))
+
+
+def check_materialised(r, s, out, sample_seed=3):
+    """Properties of a materialised equi-join of row-id payloads that hold at
+    any size, plus a seeded sample of S rows pair by pair against oracle O2."""
+    n_r, n_s = r.numel(), s.numel()
     m = out.shape[0]
-    c_r = torch.bincount(r, minlength=1 << bits)
-    c_s = torch.bincount(s, minlength=1 << bits)
-    assert m == int((c_r * c_s).sum())  # closed form: sum over keys of c_R * c_S
+    c_r_of_s = key_counts(r, s)  # for every S row: R rows with its key
+    c_s_of_r = key_counts(s, r)
+    assert m == int(c_r_of_s.sum())  # closed form: sum over keys of c_R * c_S
     pr, ps = out[:, 0].long(), out[:, 1].long()
-    del out
-    assert torch.equal(r[pr], s[ps])  # every pair joins equal keys
-    assert torch.equal(torch.bincount(ps, minlength=n), c_r[s.long()])  # each S row: all its matches
-    del c_s
-    code, _ = torch.sort(pr * n + ps)
+    assert bool((pr >= 0).all() and (pr < n_r).all() and (ps >= 0).all() and (ps < n_s).all())
+    for lo in range(0, m, 1 << 28):  # every pair joins equal keys
+        hi = min(m, lo + (1 << 28))
+        assert torch.equal(r[pr[lo:hi]], s[ps[lo:hi]])
+    assert torch.equal(torch.bincount(ps, minlength=n_s), c_r_of_s)  # each S row: all its matches
+    assert torch.equal(torch.bincount(pr, minlength=n_r), c_s_of_r)  # each R row: all its matches
+    del c_r_of_s, c_s_of_r
+    code, _ = torch.sort(pr * n_s + ps)
     assert not bool((code[1:] == code[:-1]).any())  # no pair twice
     del code
     # a seeded sample of S rows, pair by pair against the oracle (the sample
     # is the build side, all of R probes it)
-    idx = D.uniform_int(512, 0, n, seed=3, stream=0, dtype=torch.int64)
+    idx = D.uniform_int(512, 0, n_s, seed=sample_seed, stream=0, dtype=torch.int64)
     sk = s.cpu()[idx].numpy()
     exp = O.hash_join(sk, r.cpu().numpy(), idx.numpy().astype(np.int32), None)
     exp = O.sort_pairs(exp[:, ::-1].copy())  # (r row, s row)
     sel = torch.isin(ps, idx.to(DEV))
     got = O.sort_pairs(torch.stack([pr[sel], ps[sel]], 1).int().cpu().numpy())
     assert np.array_equal(got, exp)
+
+
+@pytest.mark.parametrize("theta", [0.0, 0.5])
+def test_equi_256m_x_256m(ctx, theta):
+    # theta = 0: 2.7e8 pairs; theta = 0.5: 1.34e9 pairs (10.7 GB), frequent keys
+    n, bits = 1 << 28, 28
+    cdf = D.zipf_cdf(theta, 1 << bits, DEV) if theta else None
+    r = D.zipf_keys(n, theta, bits, seed=0, stream=0, device=DEV, cdf=cdf)
+    s = D.zipf_keys(n, theta, bits, seed=0, stream=1, device=DEV, cdf=cdf)
+    del cdf
+    ids = D.row_ids(n, DEV)
+    R, S = jn.table(r, payload=ids), jn.table(s, payload=ids)
+    jn.jn_autotune(ctx, jn.JN_ALGO_HASH, R, S)  # the bench's launch configuration
+    out = torch.as_tensor(jn.jn_hash(ctx, R, S), device=DEV)
+    if theta:
+        assert ctx.run_info()["heavy_keys"] > 0  # the frequent-key path took part
+    check_materialised(r, s, out)
+
+
+def test_equi_256m_x_256m_theta1_count_and_checksum(ctx):
+    # about 3e14 pairs: counted, not stored (Sec. 5.3's "results not stored"
+    # mode); the count is the exact closed form, the checksum the oracle's
+    n, bits = 1 << 28, 28
+    cdf = D.zipf_cdf(1.0, 1 << bits, DEV)
+    r = D.zipf_keys(n, 1.0, bits, seed=0, stream=0, device=DEV, cdf=cdf)
+    s = D.zipf_keys(n, 1.0, bits, seed=0, stream=1, device=DEV, cdf=cdf)
+    del cdf
+    ids = D.row_ids(n, DEV)
+    R, S = jn.table(r, payload=ids), jn.table(s, payload=ids)
+    cnt, chk = jn.jn_aggregate(ctx, jn.JN_ALGO_HASH, R, S)
+    assert ctx.run_info()["heavy_keys"] > 0
+    c_r = torch.bincount(r, minlength=1 << bits)
+    c_s = torch.bincount(s, minlength=1 << bits)
+    assert cnt == int((c_r * c_s).sum())
+    del c_r, c_s
+    ecnt, echk = O.equi_count_checksum(r.cpu().numpy(), s.cpu().numpy(), ids.cpu().numpy(), ids.cpu().numpy())
+    assert (cnt, chk) == (ecnt, echk)
+
+
+def test_equi_int64_128m_x_128m(ctx):
+    n = 1 << 27
+    r = D.zipf_keys(n, 0.0, 28, seed=0, stream=0, device=DEV, dtype=torch.int64)
+    s = D.zipf_keys(n, 0.0, 28, seed=0, stream=1, device=DEV, dtype=torch.int64)
+    ids = D.row_ids(n, DEV)
+    R, S = jn.table(r, payload=ids), jn.table(s, payload=ids)
+    jn.jn_autotune(ctx, jn.JN_ALGO_HASH, R, S)
+    out = torch.as_tensor(jn.jn_hash(ctx, R, S), device=DEV)
+    check_materialised(r, s, out, sample_seed=4)
 
 
 def test_band_1m_x_16m_w95(ctx):
