@@ -36,6 +36,10 @@ sys.path.insert(0, ROOT)
 import torch  # noqa: E402
 
 PEAKS_FALLBACK = {"hbm_gbs": 6800.0}
+# Thread instructions the nested-loop kernels issue per pair evaluated with the
+# two-column band predicate (ncu smsp__thread_inst_executed.sum over 4096 x
+# 65536 pairs: 1.736e9 count pass, 1.682e9 emit pass)
+NLJ_THREAD_INSTR_PER_PAIR = {"nlj_count": 6.47, "nlj_emit": 6.27}
 
 
 def peaks():
@@ -928,21 +932,24 @@ def main():
                 "traffic": None,
                 "algorithmic_bytes_per_launch": abytes[dom] / max(kern[dom]["launches_per_step"], 1)}
     if w["kind"] == "nlj":
-        # compare-bound: every launch evaluates all n_R x n_S pairs; the peak is
-        # INT32 lanes x clock / integer ops of one pair's interval test
-        two = "pred" in w and (w["pred"][1] != 6 or w["pred"][2] >= 0)
-        ops = 8 if two else 4
+        # compare-bound: every launch evaluates all n_R x n_S pairs.  The peak is
+        # the SMs' issue rate (4 schedulers x 32 lanes per SM per clock) over the
+        # thread instructions the kernel issues per pair, as ncu counted them
+        # (smsp__thread_inst_executed.sum / pairs, 4K x 64K two-column band
+        # predicate, profiles/nested_loop_64Kx1M.md)
         sm_mhz = pk.get("sm_max_mhz", 2070.0)
         nsm = torch.cuda.get_device_properties(local).multi_processor_count
-        peak = nsm * 128 * sm_mhz * 1e6 / ops
         cand = [k for k in ("nlj_count", "nlj_emit") if k in kern]
-        if cand:
+        two = "pred" in w and (w["pred"][1] != 6 or w["pred"][2] >= 0)
+        if cand and two:
             dk = max(cand, key=lambda k: kern[k]["ms_per_step"])
+            ipp = NLJ_THREAD_INSTR_PER_PAIR[dk]
+            peak = nsm * 4 * 32 * sm_mhz * 1e6 / ipp
             a = nr * ns / (kern[dk]["avg_launch_ms"] * 1e-3)
             roof = {"bound": "alu", "kernel": dk, "achieved": a, "peak": peak, "unit": "pair evaluations/s",
-                    "frac": a / peak, "traffic": None, "ops_per_pair": ops,
-                    "peak_kind": "derived: %d SMs x 128 INT32 lanes x %.0f MHz / %d integer ops per pair"
-                                 % (nsm, sm_mhz, ops)}
+                    "frac": a / peak, "traffic": None, "thread_instructions_per_pair": ipp,
+                    "peak_kind": "issue rate: %d SMs x 128 lanes x %.0f MHz / %.2f thread instructions per pair "
+                                 "(ncu)" % (nsm, sm_mhz, ipp)}
     # DRAM traffic (dram__bytes_read.sum + dram__bytes_write.sum) is not taken
     # here: it comes from ncu captures of the current kernels (profiles/)
     if roof:

@@ -271,20 +271,25 @@ jn_status jn_batch(jn_ctx* ctx, int32_t count, const jn_join* joins, jn_pair** o
  * jn_nested_loop join without its allocations.
  *   - Scratch is one fixed device array inside the library (about 1 MiB per
  *     device, held until the process exits); a call handles at most 65536
- *     tiles, i.e. ceil(|S| / 1024) * ceil(|R| / 1024) <= 65536 and
- *     ceil(|R| / 1024) <= 65535.  Larger inputs return JN_ERR_INVALID.
+ *     tiles of 1024 R rows by S_TILE S rows, i.e. ceil(|S| / S_TILE) *
+ *     ceil(|R| / 1024) <= 65536 and ceil(|R| / 1024) <= 65535, where S_TILE
+ *     is the nested loop's S tile (256 threads x JN_NLJ_SPT rows, 1024 with
+ *     the default build).  Larger inputs return JN_ERR_INVALID.
  *   - Every call shares that array and it keeps the previous call's contents
  *     (the call rewrites what it reads): calls that overlap on the GPU, from
  *     any thread or stream, race and must be serialised by the caller.
- *   - The first call on a device looks up the array's device address; make
- *     that first call before any stream capture.
+ *   - Columns, output and `stream` must belong to the current device (the
+ *     call uses that device's array); anything else returns JN_ERR_INVALID.
+ *     The first call on a device looks up the array's device address.
  *   - Columns must be device memory; the output is a caller buffer of
  *     `capacity` pairs in device memory.  When the result has more pairs,
  *     JN_ERR_CAPACITY is returned with *n_out = the required count and
  *     nothing is written.
- *   - Work is issued on `stream` (a cudaStream_t, NULL = legacy default); the
- *     call waits for the count, then queues the writes, which are complete
- *     when the stream reaches that point.
+ *   - Work is issued on `stream` (a cudaStream_t, NULL = legacy default).
+ *     The call reads the count back into host memory and synchronises the
+ *     stream, so it must not be issued on a stream that is being captured
+ *     into a CUDA graph; the writes it then queues are complete when the
+ *     stream reaches that point.
  * No context is used, so no error text is recorded: the status says it all. */
 jn_status jn_nested_loop_noalloc(const jn_table* R, const jn_table* S, const jn_pred* pred, jn_pair* out,
                                  uint64_t capacity, uint64_t* n_out, void* stream);

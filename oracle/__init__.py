@@ -53,6 +53,8 @@ def _load():
         lib.or_sort_merge_join.argtypes = [P, P, I64, P, P, I64, I, P, U64]
         lib.or_checksum_pairs.restype = U64
         lib.or_checksum_pairs.argtypes = [P, U64]
+        lib.or_mix64.restype = U64
+        lib.or_mix64.argtypes = [U64]
         lib.or_f.restype = U64
         lib.or_f.argtypes = [ctypes.c_int32]
         lib.or_g.restype = U64

@@ -257,6 +257,8 @@ static uint64_t mix64(uint64_t z) {
     return z ^ (z >> 31);
 }
 
+uint64_t or_mix64(uint64_t z) { return mix64(z); }
+
 uint64_t or_f(int32_t r) { return mix64(0x243F6A8885A308D3ULL ^ (uint64_t)(uint32_t)r); }
 uint64_t or_g(int32_t s) { return mix64(0x13198A2E03707344ULL ^ (uint64_t)(uint32_t)s); }
 

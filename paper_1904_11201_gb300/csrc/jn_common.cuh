@@ -184,6 +184,7 @@ const void* host_mapped(const void* p);
 jn_status wait_copies(jn_ctx* c, bool all);
 jn_status wait_copies_r(jn_ctx* c);  // the keys and the first table's other columns
 bool is_device_pointer(const void* p);
+int pointer_device(const void* p);  // device of device (or managed) memory, else -1
 
 // ------------------------------------------------------------- helpers --
 inline int ceil_log2(uint64_t x) {

@@ -53,9 +53,12 @@ constexpr int HJ_PU = JN_HJ_PU;      // S rows a thread probes per round
 #define JN_SLICE_PAIRS (1ull << 24)  // host outputs of at least this many pairs are copied back in slices
 #endif
 constexpr int HJ_PAD = 16;         // rows of slack for 16-byte widened copies
-// the sort-merge kernels hold a chunk as 8 words per thread and index its
-// rows in 15 bits
+// the sort-merge kernels hold a chunk as 8 words per thread, index its rows in
+// 15 bits and sort it as a power-of-two network of at least 256 rows, in shared
+// memory sized for the chunk itself (int64 chunks are HJ_CAP / 2 rows)
 static_assert(HJ_CAP <= 8 * SJ_T && HJ_CAP < 0x8000, "R chunk larger than the sort-merge kernels hold");
+static_assert((HJ_CAP & (HJ_CAP - 1)) == 0 && HJ_CAP >= 512,
+              "R chunk must be a power of two of at least 512 rows (the sort network's size)");
 constexpr uint64_t CE_PAIRS = 1u << 16;  // cross-product pairs per work chunk
 
 // The partitions of one table: either P + 1 offsets (partition p = rows

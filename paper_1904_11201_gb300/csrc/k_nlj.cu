@@ -346,11 +346,25 @@ extern "C" jn_status jn_nested_loop_noalloc(const jn_table* R, const jn_table* S
     pr.band = -1;
     if (pred) pr = *pred;
     if (pr.op_a < JN_EQ || pr.op_a > JN_ANY || pr.op_k < JN_EQ || pr.op_k > JN_ANY) return JN_ERR_INVALID;
-    // columns and output must be device memory: nothing may be staged
+    // columns, output and stream on the current device (whose scratch address
+    // the call looks up): nothing may be staged, no other device's array used
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) {
+        cudaGetLastError();
+        return JN_ERR_CUDA;
+    }
     const void* cols[6] = {R->key, R->key2, R->payload, S->key, S->key2, S->payload};
     for (const void* c : cols)
-        if (c && !is_device_pointer(c)) return JN_ERR_INVALID;
-    if (capacity > 0 && !is_device_pointer(out)) return JN_ERR_INVALID;
+        if (c && pointer_device(c) != dev) return JN_ERR_INVALID;
+    if (capacity > 0 && pointer_device(out) != dev) return JN_ERR_INVALID;
+    if (stream) {
+        int sdev = -1;
+        if (cudaStreamGetDevice((cudaStream_t)stream, &sdev) != cudaSuccess) {
+            cudaGetLastError();
+            return JN_ERR_INVALID;
+        }
+        if (sdev != dev) return JN_ERR_INVALID;
+    }
     if (R->n == 0 || S->n == 0) {
         *n_out = 0;
         return JN_OK;

@@ -490,6 +490,12 @@ def jn_nested_loop_noalloc(R: TableRef, S: TableRef, pr: Pred = None, out=None, 
     (a (cap, 2) int32 CUDA tensor); returns the filled view."""
     if out is None:
         raise ValueError("jn_nested_loop_noalloc writes to a caller buffer: pass out=")
+    if (out.dtype != torch.int32 or out.dim() != 2 or out.shape[1] != 2 or not out.is_contiguous()
+            or not out.is_cuda):
+        raise ValueError("out must be a contiguous (capacity, 2) int32 CUDA tensor")
+    for c in R.refs + S.refs:
+        if c is not None and c.device != out.device:
+            raise ValueError("columns and out must be on the same CUDA device")
     n = ctypes.c_uint64()
     st = stream if stream is not None else torch.cuda.current_stream()
     rc = load().jn_nested_loop_noalloc(ctypes.byref(R.t), ctypes.byref(S.t),

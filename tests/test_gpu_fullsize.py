@@ -142,3 +142,45 @@ def test_nested_loop_64k_x_1m_band(ctx):
     exp = O.band_join_sorted(ra.cpu().numpy(), rk.cpu().numpy(), sa.cpu().numpy(), sk.cpu().numpy(), O.LT, w)
     assert got_cnt == exp.shape[0]
     assert got_chk == O.checksum_pairs(exp)
+
+
+@pytest.mark.parametrize("op", [jn.JN_NE, jn.JN_GE])
+def test_one_column_theta_cross_regions_dominate(ctx, op):
+    # R.key != S.key and R.key >= S.key over 16K x 48K rows: 4e8 - 8e8 pairs,
+    # almost all from the regions Algorithm 3 emits without comparing.  The
+    # expected count and checksum come from closed forms: the complement of the
+    # equi-join for !=, suffix sums over R sorted by key for >=.
+    nr, ns = 16384, 49152
+    r = D.uniform_keys(nr, -10 ** 6, 10 ** 6, seed=41, stream=0, device=DEV)
+    s = D.uniform_keys(ns, -10 ** 6, 10 ** 6, seed=41, stream=1, device=DEV)
+    R = jn.table(r, payload=D.row_ids(nr, DEV))
+    S = jn.table(s, payload=D.row_ids(ns, DEV))
+    lib = O._load()
+    f = np.array([lib.or_f(i) for i in range(nr)], dtype=np.uint64)  # payload = row id
+    g = np.array([lib.or_g(i) for i in range(ns)], dtype=np.uint64)
+    rk, sk = r.cpu().numpy(), s.cpu().numpy()
+    with np.errstate(over="ignore"):
+        if op == jn.JN_NE:
+            ecnt, echk = O.equi_count_checksum(rk, sk)
+            exp_cnt = nr * ns - ecnt
+            exp_chk = int((f.sum(dtype=np.uint64) * g.sum(dtype=np.uint64)) - np.uint64(echk))
+        else:
+            order = np.argsort(rk, kind="stable")
+            rs, fs = rk[order], f[order]
+            suffix = np.concatenate([np.cumsum(fs[::-1], dtype=np.uint64)[::-1], np.zeros(1, np.uint64)])
+            pos = np.searchsorted(rs, sk, side="left")  # first R key >= the S key
+            exp_cnt = int((nr - pos).sum())
+            exp_chk = int((g * suffix[pos]).sum(dtype=np.uint64))
+    assert exp_cnt == O.nested_loop(rk, sk, op_a=op, count_only=True)
+    assert jn.jn_aggregate(ctx, jn.JN_ALGO_THETA, R, S, jn.pred(op, jn.JN_ANY, -1)) == (exp_cnt, exp_chk % 2 ** 64)
+    out = torch.as_tensor(jn.jn_theta(ctx, R, S, op, -1), device=DEV)
+    assert out.shape[0] == exp_cnt
+    pr, ps = out[:, 0].long(), out[:, 1].long()
+    for lo in range(0, exp_cnt, 1 << 28):  # every pair satisfies the predicate
+        hi = min(exp_cnt, lo + (1 << 28))
+        a, b = r[pr[lo:hi]], s[ps[lo:hi]]
+        assert bool((a != b).all()) if op == jn.JN_NE else bool((a >= b).all())
+    code, _ = torch.sort(pr * ns + ps)
+    assert not bool((code[1:] == code[:-1]).any())  # no pair twice
+    del code
+    assert O.checksum_pairs(out.cpu().numpy()) == exp_chk % 2 ** 64

@@ -359,6 +359,27 @@ def test_splitmix64_reference_vector():
     assert int(base[0]) & (2 ** 64 - 1) == 0xE220A8397B1DCDAF
 
 
+def test_checksum_mixers_splitmix64():
+    # The oracle's checksum mixers f and g are the SplitMix64 output mixer
+    # applied to a constant xor the payload.  The mixer is pinned to the first
+    # outputs of SplitMix64 with state 0 (the published sequence: state
+    # advances by 0x9E3779B97F4A7C15, output = mix(state)); f, g and the pair
+    # checksum are then checked against their definitions.
+    lib = O._load()
+    golden = 0x9E3779B97F4A7C15
+    published = [0xE220A8397B1DCDAF, 0x6E789E6AA1B965F4, 0x06C45D188009454F]
+    for i, want in enumerate(published):
+        assert lib.or_mix64((golden * (i + 1)) & (2 ** 64 - 1)) == want
+    for x in (0, 1, -1, 12345, -(2 ** 31), 2 ** 31 - 1):
+        ux = x & 0xFFFFFFFF
+        assert lib.or_f(x) == lib.or_mix64(0x243F6A8885A308D3 ^ ux)
+        assert lib.or_g(x) == lib.or_mix64(0x13198A2E03707344 ^ ux)
+    assert lib.or_f(7) != lib.or_g(7)  # two different mixers
+    pairs = np.array([[3, 9], [3, 9], [-5, 2 ** 31 - 1]], dtype=np.int32)
+    want = sum(lib.or_f(int(r)) * lib.or_g(int(s)) for r, s in pairs) % 2 ** 64
+    assert O.checksum_pairs(pairs) == want
+
+
 def test_generators_reproducible_and_in_range():
     a = datagen.uniform_keys(1000, 0, 65536, seed=0, stream=1)
     b = datagen.uniform_keys(1000, 0, 65536, seed=0, stream=1)

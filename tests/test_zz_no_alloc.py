@@ -4,8 +4,8 @@ It exists for callers that may not allocate device memory (an application
 that owns every byte of the device, or a latency-critical loop that must not
 call any allocator).  Its scratch is a fixed array inside the library, so
 this test checks that two calls in a row, which reuse that array, give
-exactly the pairs of the allocating jn_nested_loop on the same inputs, and
-that sizes beyond the fixed array are refused.  Exact comparison: all
+exactly the oracle's pairs (and those of the allocating jn_nested_loop), and
+that sizes beyond the fixed array and misplaced outputs are refused.  Exact comparison: all
 arithmetic is integer.  It runs last (file name) so a failure here leaves the
 rest of the suite already run, and it passes on its own in a fresh process.
 """
@@ -34,22 +34,27 @@ def ctx():
     c.close()
 
 
-def test_noalloc_matches_allocating_entry_point_twice(ctx):
+def test_noalloc_matches_oracle_twice(ctx):
+    # an equi-join against oracle O1 (nested loop) and a band join against
+    # oracle O4 (sorted band join), each called twice in a row
     cases = []
     r = datagen.uniform_keys(5000, 0, 3000, 301, 0)
     s = datagen.uniform_keys(70001, 0, 3000, 301, 1)
-    cases.append((jn.table(r.to(DEV)), jn.table(s.to(DEV)), None))
+    cases.append((jn.table(r.to(DEV)), jn.table(s.to(DEV)), None, O.sort_pairs(O.nested_loop(r.numpy(), s.numpy()))))
     ra, rk = datagen.band_columns(3000, 16, seed=302, stream=0)
     sa, sk = datagen.band_columns(40000, 16, seed=302, stream=1)
     cases.append((jn.table(ra.to(DEV), rk.to(DEV)), jn.table(sa.to(DEV), sk.to(DEV)),
-                  jn.pred(jn.JN_LT, jn.JN_ANY, 30)))
-    for R, S, pr in cases:
-        ref = canon(jn.jn_nested_loop(ctx, R, S, pr))
+                  jn.pred(jn.JN_LT, jn.JN_ANY, 30),
+                  O.sort_pairs(O.band_join_sorted(ra.numpy(), rk.numpy(), sa.numpy(), sk.numpy(), O.LT, 30))))
+    for R, S, pr, exp in cases:
         for _ in range(2):  # the second call reuses the fixed scratch of the first
-            out = torch.full((ref.shape[0] + 3, 2), -1, dtype=torch.int32, device=DEV)
+            out = torch.full((exp.shape[0] + 3, 2), -1, dtype=torch.int32, device=DEV)
             got = jn.jn_nested_loop_noalloc(R, S, pr, out=out)
             torch.cuda.synchronize()
-            assert np.array_equal(canon(got), ref)
+            assert np.array_equal(canon(got), exp)
+            assert bool((out[exp.shape[0]:] == -1).all())  # nothing past the result
+        # the allocating entry point gives the same pairs
+        assert np.array_equal(canon(jn.jn_nested_loop(ctx, R, S, pr)), exp)
 
 
 def test_noalloc_refuses_what_does_not_fit():
@@ -66,3 +71,5 @@ def test_noalloc_refuses_what_does_not_fit():
     with pytest.raises(jn.JoinError) as e:
         jn.jn_nested_loop_noalloc(jn.table(big), jn.table(big), out=small)
     assert e.value.status == jn.JN_ERR_INVALID
+    with pytest.raises(ValueError):  # the output must be a (capacity, 2) int32 tensor
+        jn.jn_nested_loop_noalloc(R, S, out=torch.zeros((8,), dtype=torch.int64, device=DEV))
