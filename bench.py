@@ -799,6 +799,8 @@ def main():
     ap.add_argument("--prefilter", type=int, default=-1,
                     help="-1 auto, 0 off, 1 both tables, 2 only S, 3 only R")
     ap.add_argument("--radix-bits", type=int, default=0)
+    ap.add_argument("--table-rows", type=int, default=0,
+                    help="hash: R rows per shared-memory table (0 = the key type's full table)")
     ap.add_argument("--theta-groups", type=int, default=0, help="band: log2 of the key groups (0 = autotune)")
     ap.add_argument("--aggregate", action="store_true",
                     help="count + checksum without storing pairs (results too large to store)")
@@ -833,8 +835,9 @@ def main():
     dev = "cuda:%d" % local
     stream = torch.cuda.current_stream(local)
     ctx = jn.Context(local, stream)
-    if args.prefilter != -1 or args.radix_bits or args.theta_groups:
-        ctx.set_tuning(prefilter=args.prefilter, radix_bits=args.radix_bits, theta_groups=args.theta_groups)
+    if args.prefilter != -1 or args.radix_bits or args.theta_groups or args.table_rows:
+        ctx.set_tuning(prefilter=args.prefilter, radix_bits=args.radix_bits, theta_groups=args.theta_groups,
+                       table_rows=args.table_rows)
     if args.workload in ("batch", "serve"):
         (batch_main if args.workload == "batch" else serve_main)(args, world, rank, local, dev, stream, jn, ctx)
         ctx.close()
@@ -853,7 +856,8 @@ def main():
     nr, ns = rk.shape[0], sk.shape[0]
     ksize = rk.element_size()
     torch.cuda.synchronize()
-    if args.prefilter == -1 and not args.radix_bits and not args.theta_groups and not args.no_autotune:
+    if (args.prefilter == -1 and not args.radix_bits and not args.theta_groups and not args.table_rows
+            and not args.no_autotune):
         # the library's autotuner times its candidate tunings before the warm-up
         algo = {"hash": jn.JN_ALGO_SORT if w.get("sort") else jn.JN_ALGO_HASH, "band": jn.JN_ALGO_THETA,
                 "nlj": jn.JN_ALGO_NLJ}[w["kind"]]
@@ -881,6 +885,7 @@ def main():
                                 "pre-filter's bitmap slice in shared memory; count, emit)"
                                 if info.get("hash_path") == 2 else
                                 " (pre-filter bitmaps, two radix passes, count, emit)")
+        w["config"]["table_rows"] = int(info["table_rows"])  # R rows per shared-memory table
 
     ctx.reset_stats()
     ctx.set_profiling(True)

@@ -114,7 +114,13 @@ typedef struct {
                               S on a tie, when both are named).  Auto = 2 unless the
                               columns are read in place from host memory or more than
                               18 partition bits are needed                              */
-    int32_t reserved[5];
+    int32_t table_rows;    /* R rows per shared-memory table of the hash and sort-merge
+                              joins (the "bucket" a work item holds): 0 = the key type's
+                              full table (4096 rows for int32 keys, 2048 for int64), or
+                              half of it; a value the join does not support makes it
+                              return JN_ERR_UNSUPPORTED. jn_set_tuning accepts 0, 1024,
+                              2048 and 4096                                             */
+    int32_t reserved[4];
 } jn_tuning;
 
 /* Per-kernel launch statistics (profiling mode). */
@@ -148,7 +154,8 @@ typedef struct {
                                    always >= result                                 */
     uint64_t hash_path;         /* partition path taken by the hash / sort-merge join:
                                    1 two radix passes, 2 regions (see jn_tuning)     */
-    uint64_t reserved[2];
+    uint64_t table_rows;        /* R rows per shared-memory table the join used     */
+    uint64_t reserved[1];
 } jn_run_info;
 
 typedef struct jn_ctx jn_ctx;

@@ -417,7 +417,8 @@ jn_status jn_set_tuning(jn_ctx* c, const jn_tuning* t) {
     if (t->prefilter < -1 || t->prefilter > 3 || t->radix_bits < 0 || t->radix_bits > 20 || t->radix_bits1 < 0 || t->radix_bits1 > 10 ||
         t->filter_bits < 0 || t->filter_bits > 30 || t->theta_groups < 0 || t->theta_groups > 10 ||
         t->nlj_tile_r < 0 || (t->nlj_tile_r % 256) != 0 || t->nlj_tile_r > 4096 || t->part_rows < 0 ||
-        t->host_io < 0 || t->host_io > 3)
+        t->host_io < 0 || t->host_io > 3 || t->hash_path < 0 || t->hash_path > 2 ||
+        (t->table_rows != 0 && t->table_rows != 1024 && t->table_rows != 2048 && t->table_rows != 4096))
         return fail(c, JN_ERR_INVALID, "tuning value out of range");
     c->tune = *t;
     return JN_OK;

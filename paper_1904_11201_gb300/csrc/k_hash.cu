@@ -135,11 +135,12 @@ struct alignas(2 * sizeof(K)) RunSlot {
     uint32_t packed;
 };
 
-// Shared-memory layout of the join kernel (bytes), shared by host and device.
-template <typename K, int MODE>
+// Shared-memory layout of the join kernel (bytes), shared by host and device,
+// for a table of CAP_ R rows.
+template <typename K, int MODE, int CAP_ = cap_of<K>()>
 struct JoinSmem {
     using R = Row<K, false>;
-    static constexpr int CAP = cap_of<K>();
+    static constexpr int CAP = CAP_;
     static constexpr int GR = CAP + 32 / (int)sizeof(R) + 2;     // staged R rows (widened span)
     static constexpr int GS = HJ_SCH + 32 / (int)sizeof(R) + 2;  // staged S rows per buffer
     static constexpr int TS = (CAP * 5) / 4;                     // open-addressing slots
@@ -176,8 +177,8 @@ __device__ __forceinline__ uint32_t oa_slot(uint32_t h, int bits, int ts) {
 //                 lookup however many rows share the key.
 // The partitioned rows are library scratch, 16-byte aligned and padded by
 // HJ_PAD rows, so every widened copy stays inside its allocation.
-template <typename K, int MODE, bool MERGE = false>
-__global__ void __launch_bounds__(HJ_T, JN_HJ_MINB)
+template <typename K, int MODE, bool MERGE = false, int CAP = cap_of<K>()>
+__global__ void __launch_bounds__(HJ_T, (CAP < cap_of<K>() && MODE != MODE_EMIT) ? 3 : JN_HJ_MINB)
 k_hash_join(const Row<K, false>* __restrict__ rrows, const Row<K, false>* __restrict__ srows,
             const Item* __restrict__ items, const uint64_t* __restrict__ nitems_p, int bits,
             unsigned long long* __restrict__ item_val,
@@ -185,7 +186,7 @@ k_hash_join(const Row<K, false>* __restrict__ rrows, const Row<K, false>* __rest
             jn_pair* __restrict__ out, unsigned int* __restrict__ err, uint64_t item_lo = 0,
             uint64_t item_hi = ~0ull) {
     using R = Row<K, false>;
-    using L = JoinSmem<K, MODE>;
+    using L = JoinSmem<K, MODE, CAP>;
     constexpr int TS = L::TS;
     extern __shared__ __align__(128) unsigned char smem[];
     unsigned char* g_r = smem;
@@ -559,10 +560,20 @@ k_hash_join(const Row<K, false>* __restrict__ rrows, const Row<K, false>* __rest
 }
 
 template <typename K>
-static size_t hash_smem(int mode) {
-    if (mode == MODE_EMIT) return JoinSmem<K, MODE_EMIT>::BYTES;
-    if (mode == MODE_AGG) return JoinSmem<K, MODE_AGG>::BYTES;
-    return JoinSmem<K, MODE_COUNT>::BYTES;
+static size_t hash_smem(int mode, int cap = cap_of<K>()) {
+    constexpr int C = cap_of<K>(), H = C / 2;
+    if (mode == MODE_EMIT) return cap == C ? JoinSmem<K, MODE_EMIT>::BYTES : JoinSmem<K, MODE_EMIT, H>::BYTES;
+    if (mode == MODE_AGG) return cap == C ? JoinSmem<K, MODE_AGG>::BYTES : JoinSmem<K, MODE_AGG, H>::BYTES;
+    return cap == C ? JoinSmem<K, MODE_COUNT>::BYTES : JoinSmem<K, MODE_COUNT, H>::BYTES;
+}
+
+// The join kernel for a table of `cap` R rows (the full table or half of it),
+// with or without the skewed-input build.
+template <typename K, int MODE>
+static auto hash_join_kernel(bool merge, int cap) {
+    constexpr int C = cap_of<K>(), H = C / 2;
+    if (cap == C) return merge ? k_hash_join<K, MODE, true, C> : k_hash_join<K, MODE, false, C>;
+    return merge ? k_hash_join<K, MODE, true, H> : k_hash_join<K, MODE, false, H>;
 }
 
 static int persistent_grid(jn_ctx* c, const void* fn, int threads, size_t smem) {
@@ -813,6 +824,11 @@ jn_status run_hash(jn_ctx* c, const Cols<K>& R, const Cols<K>& S, int mode, OutP
     }
     const jn_tuning& tu = c->tune;
     // ---- parameters ----
+    // R rows per shared-memory table: the full table or half of it (a smaller
+    // table doubles the partitions for the same rows per partition)
+    const int cap = tu.table_rows ? tu.table_rows : cap_of<K>();
+    if (cap != cap_of<K>() && cap != cap_of<K>() / 2)
+        return fail(c, JN_ERR_UNSUPPORTED, "table_rows must be 0, the key type's table size or half of it");
     bool heavy = tu.heavy >= 1 || (tu.heavy == -1 && nr + ns >= (1u << 20));
     const int64_t heavy_rows = tu.heavy >= 2 ? tu.heavy : cap_of<K>() / 4;  // rows that make a key heavy
     // which tables the pre-filter thins: bit 0 S (by R's keys), bit 1 R (by S's keys)
@@ -840,7 +856,7 @@ jn_status run_hash(jn_ctx* c, const Cols<K>& R, const Cols<K>& S, int mode, OutP
         if (bb == 0) {
             // expected R rows per partition: the table capacity when the filter
             // will thin R's rows out, half of it otherwise
-            uint64_t target = (fs & 2) ? cap_of<K>() : cap_of<K>() / 2;
+            uint64_t target = (fs & 2) ? cap : cap / 2;
             bb = ceil_log2((nr + target - 1) / target);
             if (bb > 20) bb = 20;
         }
@@ -987,7 +1003,7 @@ jn_status run_hash(jn_ctx* c, const Cols<K>& R, const Cols<K>& S, int mode, OutP
     uint64_t *items, *iprefix;
     JN_TRY(s.get(&items, P));
     JN_TRY(s.get(&iprefix, P + 1));
-    JN_TRY(launch(c, K_ITEMS, k_items, dim3((P + 255) / 256), dim3(256), 0, PR.view(), PS.view(), P, cap_of<K>(),
+    JN_TRY(launch(c, K_ITEMS, k_items, dim3((P + 255) / 256), dim3(256), 0, PR.view(), PS.view(), P, cap,
                   items, (unsigned long long*)(d_small + 15)));
     JN_TRY(scan_u64(c, items, iprefix, P));
     uint64_t h[16];
@@ -1007,6 +1023,7 @@ jn_status run_hash(jn_ctx* c, const Cols<K>& R, const Cols<K>& S, int mode, OutP
     info.radix_bits1 = b1;
     info.filter_bits = fside ? fb : 0;
     info.hash_path = region ? 2 : 1;
+    info.table_rows = (uint64_t)cap;
     info.heavy_keys = 0;
     // the join kernel stages rows with 16-byte bulk copies from these arrays
     if ((((uintptr_t)PR.rows) | ((uintptr_t)PS.rows)) & 15)
@@ -1022,27 +1039,26 @@ jn_status run_hash(jn_ctx* c, const Cols<K>& R, const Cols<K>& S, int mode, OutP
     JN_TRY(zero(c, chk, 8));
     if (nitems) {
         JN_TRY(launch(c, K_ITEMS, k_item_desc, dim3((unsigned)ceil_div(nitems, 256)), dim3(256), 0, PR.view(),
-                      PS.view(), (const uint64_t*)iprefix, P, cap_of<K>(), idesc));
+                      PS.view(), (const uint64_t*)iprefix, P, cap, idesc));
         const int cm = mode == MODE_AGG ? MODE_AGG : MODE_COUNT;
         if (sort_merge) {
             // every R chunk sorted by key once, into a copy the count and emit passes read
             JN_TRY(s.get(&rsorted, (size_t)R.n + HJ_PAD));
             auto kso = k_sort_chunks<K>;
-            const size_t sms = SortJoinSmem<K>::sort_bytes(cap_of<K>());
+            const size_t sms = SortJoinSmem<K>::sort_bytes(cap);
             const int gs = (int)min((uint64_t)persistent_grid(c, (const void*)kso, SJ_T, sms), nitems);
             JN_TRY(launch(c, K_SORT_CHUNKS, kso, dim3(gs), dim3(SJ_T), sms, (const RW*)PR.rows, rsorted,
-                          (const Item*)idesc, (const uint64_t*)(iprefix + P), cap_of<K>()));
+                          (const Item*)idesc, (const uint64_t*)(iprefix + P), cap));
             auto kc = cm == MODE_AGG ? k_sort_join<K, MODE_AGG> : k_sort_join<K, MODE_COUNT>;
-            const size_t smc = SortJoinSmem<K>::bytes(cap_of<K>(), cm);
+            const size_t smc = SortJoinSmem<K>::bytes(cap, cm);
             const int gj = (int)min((uint64_t)persistent_grid(c, (const void*)kc, SJ_T, smc), nitems);
             JN_TRY(launch(c, K_SORT_COUNT, kc, dim3(gj), dim3(SJ_T), smc, (const RW*)rsorted, (const RW*)PS.rows,
-                          (const Item*)idesc, (const uint64_t*)(iprefix + P), cap_of<K>(), ival, chk,
+                          (const Item*)idesc, (const uint64_t*)(iprefix + P), cap, ival, chk,
                           (const uint64_t*)nullptr, (jn_pair*)nullptr, (uint64_t)0, ~0ull));
         } else {
-            const size_t smc = hash_smem<K>(cm);
-            auto kc = (cm == MODE_AGG)
-                          ? (skewed ? k_hash_join<K, MODE_AGG, true> : k_hash_join<K, MODE_AGG, false>)
-                          : (skewed ? k_hash_join<K, MODE_COUNT, true> : k_hash_join<K, MODE_COUNT, false>);
+            const size_t smc = hash_smem<K>(cm, cap);
+            auto kc = cm == MODE_AGG ? hash_join_kernel<K, MODE_AGG>(skewed, cap)
+                                     : hash_join_kernel<K, MODE_COUNT>(skewed, cap);
             const int gj = (int)min((uint64_t)persistent_grid(c, (const void*)kc, HJ_T, smc), nitems);
             JN_TRY(launch(c, K_HASH_COUNT, kc, dim3(gj), dim3(HJ_T), smc, (const RW*)PR.rows, (const RW*)PS.rows,
                           (const Item*)idesc, (const uint64_t*)(iprefix + P), b, ival, chk,
@@ -1114,9 +1130,9 @@ jn_status run_hash(jn_ctx* c, const Cols<K>& R, const Cols<K>& S, int mode, OutP
         return JN_OK;
     };
     if (normal > 0) {
-        auto ke = skewed ? k_hash_join<K, MODE_EMIT, true> : k_hash_join<K, MODE_EMIT, false>;
+        auto ke = hash_join_kernel<K, MODE_EMIT>(skewed, cap);
         auto kse = k_sort_join<K, MODE_EMIT>;
-        const size_t sme = sort_merge ? SortJoinSmem<K>::bytes(cap_of<K>(), MODE_EMIT) : hash_smem<K>(MODE_EMIT);
+        const size_t sme = sort_merge ? SortJoinSmem<K>::bytes(cap, MODE_EMIT) : hash_smem<K>(MODE_EMIT, cap);
         const uint64_t pg = sort_merge ? (uint64_t)persistent_grid(c, (const void*)kse, SJ_T, sme)
                                        : (uint64_t)persistent_grid(c, (const void*)ke, HJ_T, sme);
         for (int k = 0; k < nsl; k++) {
@@ -1124,7 +1140,7 @@ jn_status run_hash(jn_ctx* c, const Cols<K>& R, const Cols<K>& S, int mode, OutP
             const int ge = (int)min(pg, ib[k + 1] - ib[k]);
             if (sort_merge)
                 JN_TRY(launch(c, K_SORT_EMIT, kse, dim3(ge), dim3(SJ_T), sme, (const RW*)rsorted,
-                              (const RW*)PS.rows, (const Item*)idesc, (const uint64_t*)(iprefix + P), cap_of<K>(),
+                              (const RW*)PS.rows, (const Item*)idesc, (const uint64_t*)(iprefix + P), cap,
                               (unsigned long long*)nullptr, (unsigned long long*)nullptr, (const uint64_t*)ioff,
                               plan->dev, ib[k], ib[k + 1]));
             else

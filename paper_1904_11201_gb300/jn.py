@@ -49,7 +49,8 @@ class Tuning(ctypes.Structure):
                 ("heavy", ctypes.c_int32), ("theta_groups", ctypes.c_int32),
                 ("nlj_tile_r", ctypes.c_int32), ("graphs", ctypes.c_int32),
                 ("part_rows", ctypes.c_int32), ("host_io", ctypes.c_int32),
-                ("hash_path", ctypes.c_int32), ("reserved", ctypes.c_int32 * 5)]
+                ("hash_path", ctypes.c_int32), ("table_rows", ctypes.c_int32),
+                ("reserved", ctypes.c_int32 * 4)]
 
 
 class Join(ctypes.Structure):
@@ -91,7 +92,8 @@ class RunInfo(ctypes.Structure):
                 ("radix_bits", ctypes.c_int32), ("radix_bits1", ctypes.c_int32),
                 ("filter_bits", ctypes.c_int32), ("scratch_peak", ctypes.c_uint64),
                 ("heavy_pairs", ctypes.c_uint64), ("cartesian_bound", ctypes.c_uint64),
-                ("hash_path", ctypes.c_uint64), ("reserved", ctypes.c_uint64 * 2)]
+                ("hash_path", ctypes.c_uint64), ("table_rows", ctypes.c_uint64),
+                ("reserved", ctypes.c_uint64 * 1)]
 
 
 ADMIT_FN = ctypes.CFUNCTYPE(ctypes.c_int, ctypes.c_void_p, ctypes.c_uint64, ctypes.c_uint64)

@@ -136,20 +136,71 @@ def test_hash_auto_prefilter_sides(ctx, sizes, path):
 
 @pytest.mark.parametrize("bits", [(1, 1), (3, 2), (5, 0), (12, 6), (16, 8), (18, 10), (19, 10)])
 @pytest.mark.parametrize("path", [1, 2])
-def test_hash_result_independent_of_partitioning(ctx, bits, path):
+@pytest.mark.parametrize("table_rows", [0, 2048])
+def test_hash_result_independent_of_partitioning(ctx, bits, path, table_rows):
+    # partition bits, partition path and R rows per shared-memory table shape
+    # the work, never the result (1 and 3 bits leave 9000-row partitions:
+    # several table-sized items each)
     b, b1 = bits
     r = keys(30000, 0, 9000, 8, 0)
     s = keys(45000, 0, 9000, 8, 1)
     exp = canon(O.hash_join(r.numpy(), s.numpy()))
-    ctx.set_tuning(radix_bits=b, radix_bits1=b1, prefilter=1, hash_path=path)
+    ctx.set_tuning(radix_bits=b, radix_bits1=b1, prefilter=1, hash_path=path, table_rows=table_rows)
     try:
         got = jn.jn_hash(ctx, jn.table(r.to(DEV)), jn.table(s.to(DEV)))
+        info = ctx.run_info()
         # the region path holds up to 10 + 8 bits; beyond, two radix passes run
         taken = 1 if path == 1 or b - (b1 or min(b, 10)) > 8 else 2
-        assert ctx.run_info()["hash_path"] == taken
+        assert info["hash_path"] == taken
+        assert info["table_rows"] == (table_rows or 4096)
     finally:
-        ctx.set_tuning(radix_bits=0, radix_bits1=0, prefilter=-1, hash_path=0)
+        ctx.set_tuning(radix_bits=0, radix_bits1=0, prefilter=-1, hash_path=0, table_rows=0)
     assert np.array_equal(canon(got), exp)
+
+
+@pytest.mark.parametrize("dt", [torch.int32, torch.int64])
+@pytest.mark.parametrize("half", [False, True])
+def test_table_rows_skewed_int64_and_sort_merge(ctx, dt, half):
+    # the smaller table with frequent keys (the skewed build), int64 keys and
+    # the sort-merge join, against the oracle's count and checksum and pairs
+    nr, ns = 40000, 70000
+    r = skewed(nr, 1 << 13, 1.0, 31, 0, dt)
+    s = skewed(ns, 1 << 13, 1.0, 31, 1, dt)
+    rp = datagen.uniform_int(nr, I32_MIN, I32_MAX, 31, 5)
+    sp = datagen.uniform_int(ns, I32_MIN, I32_MAX, 31, 6)
+    cnt, chk = O.equi_count_checksum(r.numpy(), s.numpy(), rp.numpy(), sp.numpy())
+    R = jn.table(r.to(DEV), payload=rp.to(DEV))
+    S = jn.table(s.to(DEV), payload=sp.to(DEV))
+    full = 4096 if dt == torch.int32 else 2048
+    rows = full // 2 if half else full
+    for algo in (jn.JN_ALGO_HASH, jn.JN_ALGO_SORT):
+        for heavy in (64, 0):
+            ctx.set_tuning(table_rows=rows, heavy=heavy, radix_bits=4)
+            try:
+                assert jn.jn_aggregate(ctx, algo, R, S) == (cnt, chk)
+                assert ctx.run_info()["table_rows"] == rows
+                got = jn.jn_hash(ctx, R, S) if algo == jn.JN_ALGO_HASH else jn.jn_sort_merge(ctx, R, S)
+            finally:
+                ctx.set_tuning(table_rows=0, heavy=-1, radix_bits=0)
+            assert got.shape[0] == cnt and O.checksum_pairs(got.cpu().numpy()) == chk
+
+
+def test_table_rows_rejected(ctx):
+    # jn_set_tuning takes 0, 1024, 2048 and 4096; a join refuses a size that is
+    # neither its key type's table nor half of it: 1024 rows of int32 keys,
+    # 4096 of int64
+    for bad in (-1, 1000, 3072, 8192):
+        with pytest.raises(jn.JoinError):
+            ctx.set_tuning(table_rows=bad)
+    for dt, rows in ((torch.int32, 1024), (torch.int64, 4096)):
+        R = jn.table(keys(1000, 0, 500, 9, 0, dt).to(DEV))
+        ctx.set_tuning(table_rows=rows)
+        try:
+            with pytest.raises(jn.JoinError) as e:
+                jn.jn_hash(ctx, R, R)
+            assert e.value.status == jn.JN_ERR_UNSUPPORTED
+        finally:
+            ctx.set_tuning(table_rows=0)
 
 
 @pytest.mark.parametrize("dt", [torch.int32, torch.int64])

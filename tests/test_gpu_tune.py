@@ -34,7 +34,10 @@ def test_autotune_hash_then_join_equals_oracle(ctx):
     R, S = jn.table(r.to(DEV)), jn.table(s.to(DEV))
     t = jn.jn_autotune(ctx, jn.JN_ALGO_HASH, R, S)
     assert t["prefilter"] in (0, 1, 2, 3) and 1 <= t["radix_bits"] <= 20
+    assert t["table_rows"] in (2048, 4096)  # the tuner picks the table size too
     assert ctx.tuning()["radix_bits"] == t["radix_bits"]
+    jn.jn_hash(ctx, R, S)
+    assert ctx.run_info()["table_rows"] == t["table_rows"]
     assert np.array_equal(canon(jn.jn_hash(ctx, R, S)), canon(O.hash_join(r.numpy(), s.numpy())))
     # the same size class reuses the cached choice
     r2 = datagen.uniform_keys(300001, 0, 1 << 20, 202, 0)
