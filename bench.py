@@ -170,6 +170,7 @@ def algorithmic_bytes(kind, info, nr, ns, m, ksize):
             "scatter": 2 * 12 * (nr + ns),
             "theta_count": 12 * (nr + ns),
             "theta_emit": 12 * (nr + ns) + 8 * m,
+            "theta_gather": 12 * (nr + ns) + 8 * m,
         }
     return {}
 

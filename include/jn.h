@@ -203,6 +203,9 @@ jn_status jn_aggregate(jn_ctx* ctx, int32_t algo, const jn_table* R, const jn_ta
  *                  (one allocation, after the count pass) and stores the
  *                  pointer in *out; release it with jn_free.  capacity is ignored.
  *   *out != NULL : a caller buffer of `capacity` pairs, device or host memory.
+ *                  The kernels write 8-byte aligned device buffers (and, with
+ *                  host_io bit 1, aligned page-locked host buffers) in place;
+ *                  any other buffer is filled by a copy.
  *                  If the result has more pairs than capacity the call returns
  *                  JN_ERR_CAPACITY with *n_out = the required count and writes
  *                  nothing.  A host buffer is filled by a copy before return.
@@ -289,7 +292,8 @@ jn_status jn_batch(jn_ctx* ctx, int32_t count, const jn_join* joins, jn_pair** o
  *     call uses that device's array); anything else returns JN_ERR_INVALID.
  *     The first call on a device looks up the array's device address.
  *   - Columns must be device memory; the output is a caller buffer of
- *     `capacity` pairs in device memory.  When the result has more pairs,
+ *     `capacity` pairs in device memory, 8-byte aligned (JN_ERR_INVALID
+ *     otherwise).  When the result has more pairs,
  *     JN_ERR_CAPACITY is returned with *n_out = the required count and
  *     nothing is written.
  *   - Work is issued on `stream` (a cudaStream_t, NULL = legacy default).

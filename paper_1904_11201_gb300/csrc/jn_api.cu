@@ -49,11 +49,14 @@ jn_status out_prepare(jn_ctx* c, Scratch& s, uint64_t m, OutPlan& plan) {
         *plan.n_out = m;
         return fail(c, JN_ERR_CAPACITY, "output buffer holds fewer pairs than the result");
     }
-    if (m == 0 || is_device_pointer(user)) {
+    // the kernels store a pair as one 8-byte word: a caller buffer off an
+    // 8-byte boundary is filled by a copy from an aligned scratch buffer
+    const bool aligned = ((uintptr_t)user & 7) == 0;
+    if (m == 0 || (aligned && is_device_pointer(user))) {
         plan.dev = user;
         return JN_OK;
     }
-    if (mapped) {  // page-locked host memory: the kernels write the pairs in place
+    if (mapped && aligned) {  // page-locked host memory: the kernels write the pairs in place
         plan.dev = const_cast<jn_pair*>(mapped);
         plan.mapped = true;
         return JN_OK;
@@ -66,7 +69,7 @@ jn_status out_finish(jn_ctx* c, uint64_t m, OutPlan& plan) {
     if (plan.mapped && m > 0) JN_CUDA(c, cudaStreamSynchronize(c->stream));  // pairs visible to the host
     if (plan.host_copy && m > 0) {
         if (!plan.copied)
-            JN_CUDA(c, cudaMemcpyAsync(*plan.user_out, plan.dev, m * sizeof(jn_pair), cudaMemcpyDeviceToHost,
+            JN_CUDA(c, cudaMemcpyAsync(*plan.user_out, plan.dev, m * sizeof(jn_pair), cudaMemcpyDefault,
                                        c->stream));
         JN_CUDA(c, cudaStreamSynchronize(c->stream));
     }
@@ -277,7 +280,8 @@ static jn_status batch_typed(jn_ctx* c, int count, const jn_join* joins, jn_pair
     plan.capacity = capacity;
     plan.n_out = n_out;
     JN_TRY(out_prepare(c, s, te + tb, plan));
-    if (plan.host_copy) return fail(c, JN_ERR_INVALID, "batch outputs must be device memory");
+    if (plan.host_copy && !is_device_pointer(*out))
+        return fail(c, JN_ERR_INVALID, "batch outputs must be device memory");
     if (he) JN_TRY(he->emit(c, plan.dev));
     if (be) JN_TRY(be->emit(c, plan.dev + te));
     for (size_t j = 0; j < eq.size(); j++) {

@@ -42,6 +42,7 @@ enum KernelId {
     K_CHUNK_HIST,
     K_REGION1,
     K_REGION2,
+    K_THETA_GATHER,
     K_COUNT_IDS
 };
 
@@ -276,6 +277,13 @@ __device__ __forceinline__ void warp_add_to(unsigned long long* dst, unsigned lo
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
     if ((threadIdx.x & 31) == 0 && v) atomicAdd(dst, v);
+}
+
+// Stores one result pair as a single 8-byte word.  Every pair buffer a kernel
+// writes is 8-byte aligned: library allocations and scratch are, and a caller
+// buffer off that boundary is filled by a copy from aligned scratch.
+__device__ __forceinline__ void st_pair(jn_pair* p, int32_t r, int32_t s) {
+    *reinterpret_cast<int2*>(p) = make_int2(r, s);
 }
 
 // Membership of x in [lo, hi] for signed integers, by one unsigned compare:

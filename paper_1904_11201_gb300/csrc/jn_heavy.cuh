@@ -308,10 +308,7 @@ k_cartesian(const R* __restrict__ rr, const uint64_t* __restrict__ roff, const R
         uint64_t si = q / nr, ri = q - si * nr;
         const uint64_t step_s = blockDim.x / nr, step_r = blockDim.x - step_s * nr;
         for (; q < q1; q += blockDim.x) {
-            jn_pair v;
-            v.r = rr[roff[h] + ri].pay;
-            v.s = sr[soff[h] + si].pay;
-            out[ob + q] = v;
+            st_pair(out + ob + q, rr[roff[h] + ri].pay, sr[soff[h] + si].pay);
             ri += step_r;
             si += step_s;
             if (ri >= nr) {

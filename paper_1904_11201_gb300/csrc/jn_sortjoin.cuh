@@ -299,7 +299,7 @@ k_sort_join(const Row<K, false>* __restrict__ rrows, const Row<K, false>* __rest
                 // short runs by their lane, long runs by the whole warp
                 const bool longr = m > 4;
                 if (!longr)
-                    for (uint32_t e = 0; e < m; e++) out[o + e] = jn_pair{s_pay[lo + e], spay};
+                    for (uint32_t e = 0; e < m; e++) st_pair(out + o + e, s_pay[lo + e], spay);
                 for (unsigned lanes = __ballot_sync(0xffffffffu, longr); lanes; lanes &= lanes - 1) {
                     const int src = __ffs(lanes) - 1;
                     const uint32_t bm = __shfl_sync(0xffffffffu, m, src);
@@ -307,7 +307,7 @@ k_sort_join(const Row<K, false>* __restrict__ rrows, const Row<K, false>* __rest
                     const int32_t bp = __shfl_sync(0xffffffffu, spay, src);
                     const uint64_t bo = __shfl_sync(0xffffffffu, o, src);
                     for (uint32_t e = lane; e < bm; e += 32)
-                        out[bo + e] = jn_pair{s_pay[bl + e], bp};
+                        st_pair(out + bo + e, s_pay[bl + e], bp);
                 }
             } else {
                 acc += m;

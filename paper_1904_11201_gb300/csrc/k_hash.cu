@@ -512,14 +512,14 @@ k_hash_join(const Row<K, false>* __restrict__ rrows, const Row<K, false>* __rest
                         // whole warp, 32 pairs at a time
                         const bool longr = m[u] > 4;
                         if (!longr)
-                            for (uint32_t i = 0; i < m[u]; i++) out[o + i] = jn_pair{s_pay[beg[u] + i], x[u].pay};
+                            for (uint32_t i = 0; i < m[u]; i++) st_pair(out + o + i, s_pay[beg[u] + i], x[u].pay);
                         for (unsigned lanes = __ballot_sync(0xffffffffu, longr); lanes; lanes &= lanes - 1) {
                             const int src = __ffs(lanes) - 1;
                             const uint32_t bm = __shfl_sync(0xffffffffu, m[u], src);
                             const uint32_t bb = __shfl_sync(0xffffffffu, beg[u], src);
                             const int32_t bp = __shfl_sync(0xffffffffu, x[u].pay, src);
                             const uint64_t bo = __shfl_sync(0xffffffffu, o, src);
-                            for (uint32_t i = lane; i < bm; i += 32) out[bo + i] = jn_pair{s_pay[bb + i], bp};
+                            for (uint32_t i = lane; i < bm; i += 32) st_pair(out + bo + i, s_pay[bb + i], bp);
                         }
                     }
                 } else {
@@ -1126,7 +1126,7 @@ jn_status run_hash(jn_ctx* c, const Cols<K>& R, const Cols<K>& S, int mode, OutP
         cudaStreamWaitEvent(c->copy_stream, e, 0);
         cudaEventDestroy(e);
         JN_CUDA(c, cudaMemcpyAsync(*plan->user_out + lo, plan->dev + lo, (hi - lo) * sizeof(jn_pair),
-                                   cudaMemcpyDeviceToHost, c->copy_stream));
+                                   cudaMemcpyDefault, c->copy_stream));
         return JN_OK;
     };
     if (normal > 0) {

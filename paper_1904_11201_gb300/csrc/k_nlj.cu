@@ -113,10 +113,7 @@ k_nlj(const K* __restrict__ rk, const K* __restrict__ rk2, const int32_t* __rest
                     for (int j = 0; j < NLJ_SPT; j++) {
                         if ((mask >> j) & 1u) {
                             const uint32_t slot = atomicAdd(&s_cur, 1u);
-                            jn_pair q;
-                            q.r = s_p[i];
-                            q.s = spay[j];
-                            out[tile_off[tile] + slot] = q;
+                            st_pair(out + tile_off[tile] + slot, s_p[i], spay[j]);
                         }
                     }
                 }
@@ -357,6 +354,7 @@ extern "C" jn_status jn_nested_loop_noalloc(const jn_table* R, const jn_table* S
     for (const void* c : cols)
         if (c && pointer_device(c) != dev) return JN_ERR_INVALID;
     if (capacity > 0 && pointer_device(out) != dev) return JN_ERR_INVALID;
+    if (((uintptr_t)out & 7) != 0) return JN_ERR_INVALID;  // pairs are stored as 8-byte words
     if (stream) {
         int sdev = -1;
         if (cudaStreamGetDevice((cudaStream_t)stream, &sdev) != cudaSuccess) {

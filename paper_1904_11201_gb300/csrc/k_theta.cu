@@ -23,30 +23,75 @@
 namespace jnx {
 
 constexpr int TH_T = 256;
-constexpr int TH_RCAP = 4096;   // R rows per shared-memory chunk
+#ifndef JN_TH_RCAP
+#define JN_TH_RCAP 4096
+#endif
+constexpr int TH_RCAP = JN_TH_RCAP;   // R rows per shared-memory chunk
 constexpr int TH_SCH = 4096;    // S rows per work item
+constexpr int TH_KPAD = 4;      // staged rows of padding read by the unrolled candidate scan
 constexpr int TH_NFB = 2048;    // fine k-buckets per window
 constexpr uint64_t CE_CHUNK = 1u << 16;  // cross-product pairs per work item
 
+// Dynamic shared memory of the theta join kernel: the staged R rows (k and a,
+// then payloads) and the fine-bucket offsets.
 template <typename K>
-__global__ void k_minmax(const K* __restrict__ col, int64_t n, long long* __restrict__ mm) {
+static size_t theta_smem(int) {
+    return (size_t)(TH_RCAP + TH_KPAD) * 2 * sizeof(K) + (size_t)TH_RCAP * 4 + sizeof(uint32_t) * TH_NFB;
+}
+
+// Minimum and maximum of a column into mm[0], mm[1] (atomics, one per block).
+// The body is read in 16-byte words, four in flight per thread; the elements
+// before the first 16-byte boundary and after the last whole word are read
+// one by one.
+template <typename K>
+__global__ void __launch_bounds__(512) k_minmax(const K* __restrict__ col, int64_t n, long long* __restrict__ mm) {
+    constexpr int PER = 16 / sizeof(K);
+    __shared__ long long s_lo[16], s_hi[16];
     long long lo = LLONG_MAX, hi = LLONG_MIN;
-    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
-         i += (int64_t)gridDim.x * blockDim.x) {
-        long long v = (long long)col[i];
+    auto take = [&](long long v) {
         lo = v < lo ? v : lo;
         hi = v > hi ? v : hi;
+    };
+    const int64_t tid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    const int64_t head = min(n, (int64_t)(((16 - ((uintptr_t)col & 15)) & 15) / sizeof(K)));
+    const int64_t nv = (n - head) / PER;
+    if (tid < head) take((long long)col[tid]);
+    const uint4* v = reinterpret_cast<const uint4*>(col + head);
+#pragma unroll 4
+    for (int64_t i = tid; i < nv; i += stride) {
+        const uint4 w = __ldg(v + i);
+        if (sizeof(K) == 4) {
+            take((int32_t)w.x);
+            take((int32_t)w.y);
+            take((int32_t)w.z);
+            take((int32_t)w.w);
+        } else {
+            take((long long)(((uint64_t)w.y << 32) | w.x));
+            take((long long)(((uint64_t)w.w << 32) | w.z));
+        }
     }
+    for (int64_t i = head + nv * PER + tid; i < n; i += stride) take((long long)col[i]);
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) {
-        long long a = __shfl_xor_sync(0xffffffffu, lo, o);
-        long long b = __shfl_xor_sync(0xffffffffu, hi, o);
-        lo = a < lo ? a : lo;
-        hi = b > hi ? b : hi;
+        take(__shfl_xor_sync(0xffffffffu, lo, o));
+        take(__shfl_xor_sync(0xffffffffu, hi, o));
     }
+    const int w = threadIdx.x >> 5;
     if ((threadIdx.x & 31) == 0) {
-        atomicMin(&mm[0], lo);
-        atomicMax(&mm[1], hi);
+        s_lo[w] = lo;
+        s_hi[w] = hi;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        for (int k = 1; k < (int)(blockDim.x >> 5); k++) {
+            take(s_lo[k]);
+            take(s_hi[k]);
+        }
+        if (lo <= hi) {
+            atomicMin(&mm[0], lo);
+            atomicMax(&mm[1], hi);
+        }
     }
 }
 
@@ -161,10 +206,127 @@ __device__ __forceinline__ void theta_emit_scan(const KA<K>* s_ka, const int32_t
         bool ok = PLAIN ? in_range(t.a, ia.lo, ia.span) : iv_test(ia, t.a);
         if (BAND) ok &= in_range(t.k, ib.lo, ib.span);
         if (ok) {
-            jn_pair q;
-            q.r = s_p[e];
-            q.s = spay;
-            *out++ = q;
+            st_pair(out++, s_p[e], spay);
+        }
+    }
+}
+
+// Tests one S row against the staged candidates [lo, hi), four shared loads
+// in flight (the loads past hi read the padding behind the staged rows and
+// are discarded).  Returns the matches; *mask gets the matches among the
+// first 32 candidates as bits, *fsum (AGG) the sum of f over the matches.
+// PLAIN: the a-interval is not inverted, so its test is the bare range check.
+template <bool PLAIN, bool AGG, typename K, bool BAND>
+__device__ __forceinline__ uint32_t theta_scan(const KA<K>* s_ka, const int32_t* s_p, uint32_t lo, uint32_t hi,
+                                               const Interval<K>& ia, const Interval<K>& ib, uint32_t* mask,
+                                               unsigned long long* fsum) {
+    uint32_t m = 0, mk = 0, bit = 1;
+    for (uint32_t e = lo; e < hi; e += 4) {
+        KA<K> t[4];
+#pragma unroll
+        for (int u = 0; u < 4; u++) t[u] = s_ka[e + u];
+#pragma unroll
+        for (int u = 0; u < 4; u++) {
+            bool ok = PLAIN ? in_range(t[u].a, ia.lo, ia.span) : iv_test(ia, t[u].a);
+            if (BAND) ok &= in_range(t[u].k, ib.lo, ib.span);
+            ok &= e + u < hi;
+            m += ok;
+            mk |= ok ? bit : 0u;
+            bit <<= 1;
+            if (AGG && ok) *fsum += chk_f(s_p[e + u]);
+        }
+    }
+    *mask = mk;
+    return m;
+}
+
+// What the count pass of a band join leaves for a gathering emit pass.  For
+// S row j of item it, rows[it * TH_SCH + j] = (mask, at): the row's matches
+// among its first 32 candidates as bits, and at = (offset of its first pair
+// within the item's output << 13) | (staged position of its first candidate),
+// or TH_WIDE when the row has more than 32 candidates.  pay[it * TH_RCAP ..]
+// holds the item's staged R payloads in staged order.  sdesc[it] =
+// (first S row << 14) | (S rows << 1) | wide, wide when any of its rows is;
+// *any_wide is set when some item is wide.  Wide items are emitted by the
+// join kernel itself, the others by k_theta_gather.
+struct ThetaRec {
+    uint2* rows;
+    int32_t* pay;
+    uint64_t* sdesc;
+    unsigned int* any_wide;
+};
+constexpr uint32_t TH_WIDE = 0xFFFFFFFFu;
+static_assert(TH_SCH == 4096 && TH_RCAP < 8192, "record fields: 12 bits of S row, 13 of staged position");
+
+constexpr int TH_GSTG = 256;  // pairs a gather warp stages before one coalesced store
+
+// Emit pass of the band items that are not wide, one block per item: the
+// item's staged payloads are loaded into shared memory, and each warp takes
+// the 32 S rows one warp of the count pass took (same rows per round and
+// warp), whose pairs are one contiguous run of the output.  The warp gathers
+// the run from the rows' records into shared memory and stores it coalesced
+// (a run longer than TH_GSTG pairs is written lane by lane).
+template <typename K>
+__global__ void __launch_bounds__(TH_T)
+k_theta_gather(const Row<K, true>* __restrict__ srows, const uint64_t* __restrict__ nitems_p,
+               const uint64_t* __restrict__ item_off, ThetaRec rec, jn_pair* __restrict__ out) {
+    __shared__ __align__(16) int32_t s_pay[TH_RCAP];
+    __shared__ __align__(16) int2 s_stg[TH_T / 32][TH_GSTG];
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    const uint64_t nitems = *nitems_p;
+    for (uint64_t it = blockIdx.x; it < nitems; it += gridDim.x) {
+        const uint64_t d = rec.sdesc[it];
+        if (d & 1) continue;  // wide: the join kernel emits it
+        const int sn = (int)((d >> 1) & 8191);
+        const uint64_t sbeg = d >> 14;
+        __syncthreads();  // the previous item's payloads are no longer read
+        const int4* src = reinterpret_cast<const int4*>(rec.pay + it * TH_RCAP);
+        for (int i = threadIdx.x; i < TH_RCAP / 4; i += TH_T) reinterpret_cast<int4*>(s_pay)[i] = src[i];
+        __syncthreads();
+        const uint64_t obase = item_off[it];
+        // a row's record and S payload load one round ahead of their use
+        uint2 rn = make_uint2(0u, 0u);
+        int32_t pn = 0;
+        if ((int)threadIdx.x < sn) {
+            rn = rec.rows[it * TH_SCH + threadIdx.x];
+            pn = srows[sbeg + threadIdx.x].pay;
+        }
+        for (int r0 = 0; r0 < sn; r0 += TH_T) {
+            const int j = r0 + threadIdx.x;
+            uint32_t mask = rn.x;
+            const uint32_t at = rn.y;
+            const int32_t spay = pn;
+            if (j + TH_T < sn) {
+                rn = rec.rows[it * TH_SCH + j + TH_T];
+                pn = srows[sbeg + j + TH_T].pay;
+            } else {
+                rn = make_uint2(0u, 0u);
+            }
+            const uint32_t m = __popc(mask);
+            const uint32_t incl = warp_incl_scan(m);
+            const uint32_t wt = __shfl_sync(0xffffffffu, incl, 31);
+            if (wt == 0) continue;  // lane 0 holds a row whenever the warp has pairs
+            const uint32_t run = __shfl_sync(0xffffffffu, (at >> 13) - (incl - m), 0);
+            jn_pair* g = out + obase + run;
+            const int32_t* rp = s_pay + (at & 8191);
+            if (wt <= (uint32_t)TH_GSTG) {
+                uint32_t q = incl - m;
+                while (mask) {
+                    const int e = __ffs(mask) - 1;
+                    mask &= mask - 1;
+                    s_stg[w][q++] = make_int2(rp[e], spay);
+                }
+                __syncwarp();
+                for (uint32_t q2 = lane; q2 < wt; q2 += 32) st_pair(g + q2, s_stg[w][q2].x, s_stg[w][q2].y);
+                __syncwarp();
+            } else {
+                jn_pair* o = g + (incl - m);
+                while (mask) {
+                    const int e = __ffs(mask) - 1;
+                    mask &= mask - 1;
+                    st_pair(o++, rp[e], spay);
+                }
+            }
         }
     }
 }
@@ -175,28 +337,35 @@ k_theta_join(const Row<K, BAND>* __restrict__ rrows, const uint64_t* __restrict_
              const Row<K, BAND>* __restrict__ srows, const uint64_t* __restrict__ soff, ThetaSet ts, int Ptot,
              const uint64_t* __restrict__ item_prefix, unsigned long long* __restrict__ item_val,
              unsigned long long* __restrict__ chk, const uint64_t* __restrict__ item_off, jn_pair* __restrict__ out,
-             unsigned int* __restrict__ work) {
+             unsigned int* __restrict__ work, ThetaRec rec) {
     extern __shared__ __align__(16) unsigned char smem[];
     // the staged R rows' k and a side by side, so one load gives both
     KA<K>* s_ka = reinterpret_cast<KA<K>*>(smem);
-    int32_t* s_p = reinterpret_cast<int32_t*>(s_ka + TH_RCAP);
+    int32_t* s_p = reinterpret_cast<int32_t*>(s_ka + TH_RCAP + TH_KPAD);
     uint32_t* s_off = reinterpret_cast<uint32_t*>(s_p + TH_RCAP);
     __shared__ unsigned long long tmp64[33];
     __shared__ uint32_t tmp32[33];
     __shared__ unsigned int s_item;
-    __shared__ uint32_t s_cursor, s_rows;
+    __shared__ uint32_t s_cursor, s_rows, s_wide;
 
     const uint64_t nitems = item_prefix[Ptot];
     const int lane = threadIdx.x & 31;
+    // count pass of a band join followed by a gathering emit: record the rows
+    const bool record = BAND && MODE == MODE_COUNT && rec.rows != nullptr;
     while (true) {
         if (threadIdx.x == 0) {
             s_item = atomicAdd(work, 1u);
             s_cursor = 0;
             s_rows = 0;
+            s_wide = 0;
         }
         __syncthreads();
         const uint64_t it = s_item;
         if (it >= nitems) break;
+        if (MODE == MODE_EMIT && rec.sdesc != nullptr && !(rec.sdesc[it] & 1)) {
+            __syncthreads();  // a gathered item: k_theta_gather writes its pairs
+            continue;
+        }
         const int p = find_segment(item_prefix, Ptot, it);
         const int inst = p >> ts.lg, y = p & ((1 << ts.lg) - 1), G = ts.groups[inst];
         const RangeParams P = ts.prm[inst];
@@ -267,13 +436,18 @@ k_theta_join(const Row<K, BAND>* __restrict__ rrows, const uint64_t* __restrict_
 
         unsigned long long acc = 0, csum = 0;
         const int rounds = (sn + TH_T - 1) / TH_T;
+        // S rows stream through registers one round ahead: the next round's
+        // row loads while this round's candidates are scanned
+        Row<K, BAND> xn{};
+        if ((int)threadIdx.x < sn) xn = srows[sbeg + threadIdx.x];
         for (int r = 0; r < rounds; r++) {
             const int j = r * TH_T + threadIdx.x;
+            const Row<K, BAND> x = xn;
+            if (j + TH_T < sn) xn = srows[sbeg + j + TH_T];
             uint32_t lo = 0, hi = 0;
             Interval<K> ia, ib;
             int32_t pay = 0;
             if (j < sn) {
-                const Row<K, BAND> x = srows[sbeg + j];
                 const K a = col_a<K, BAND>(x);
                 pay = x.pay;
                 ia = op_interval<K>(op, a);
@@ -295,29 +469,16 @@ k_theta_join(const Row<K, BAND>* __restrict__ rrows, const uint64_t* __restrict_
             }
             uint32_t m = 0;
             unsigned long long fs_sum = 0;
-            // The emit pass's two scans take the plain test in a warp without
-            // inverted intervals (!=, empty sets); the count pass keeps the
-            // general test, which measured faster there.
-            const bool plain = MODE == MODE_EMIT && !__any_sync(0xffffffffu, j < sn && ia.inv);
-            if (MODE == MODE_EMIT && plain) {
-                for (uint32_t e = lo; e < hi; e++) {
-                    const KA<K> t = s_ka[e];
-                    bool ok = in_range(t.a, ia.lo, ia.span);
-                    if (BAND) ok &= in_range(t.k, ib.lo, ib.span);
-                    m += ok;
-                }
-            } else {
-                for (uint32_t e = lo; e < hi; e++) {
-                    const KA<K> t = s_ka[e];
-                    bool ok = iv_test(ia, t.a);
-                    if (BAND) ok = ok && iv_test(ib, t.k);
-                    if (ok) {
-                        m++;
-                        if (MODE == MODE_AGG) fs_sum += chk_f(s_p[e]);
-                    }
-                }
-            }
             if (MODE == MODE_EMIT) {
+                // one scan: the matches among the first 32 candidates as a
+                // mask, so the pairs are written without testing again; a
+                // row with more candidates tests them again as it writes.
+                // A warp without inverted intervals (!=, empty sets) takes
+                // the bare range test.
+                const bool plain = !__any_sync(0xffffffffu, j < sn && ia.inv);
+                uint32_t mask = 0;
+                m = plain ? theta_scan<true, false, K, BAND>(s_ka, s_p, lo, hi, ia, ib, &mask, &fs_sum)
+                          : theta_scan<false, false, K, BAND>(s_ka, s_p, lo, hi, ia, ib, &mask, &fs_sum);
                 const uint32_t incl = warp_incl_scan(m);
                 const uint32_t wt = __shfl_sync(0xffffffffu, incl, 31);
                 uint32_t base = 0;
@@ -325,14 +486,52 @@ k_theta_join(const Row<K, BAND>* __restrict__ rrows, const uint64_t* __restrict_
                 base = __shfl_sync(0xffffffffu, base, 0);
                 if (m) {
                     jn_pair* o = out + item_off[it] + base + (incl - m);
-                    if (plain)
+                    if (hi - lo <= 32) {
+                        while (mask) {
+                            const int e = __ffs(mask) - 1;
+                            mask &= mask - 1;
+                            st_pair(o++, s_p[lo + e], pay);
+                        }
+                    } else if (plain) {
                         theta_emit_scan<true, K, BAND>(s_ka, s_p, lo, hi, ia, ib, o, pay);
-                    else
+                    } else {
                         theta_emit_scan<false, K, BAND>(s_ka, s_p, lo, hi, ia, ib, o, pay);
+                    }
                 }
             } else {
+                const bool plain = !__any_sync(0xffffffffu, j < sn && ia.inv);
+                uint32_t mask;
+                m = plain ? theta_scan<true, MODE == MODE_AGG, K, BAND>(s_ka, s_p, lo, hi, ia, ib, &mask, &fs_sum)
+                          : theta_scan<false, MODE == MODE_AGG, K, BAND>(s_ka, s_p, lo, hi, ia, ib, &mask, &fs_sum);
                 acc += m;
                 if (MODE == MODE_AGG && m) csum += fs_sum * chk_g(pay);
+                if (record) {
+                    // the row's pairs start where the warp's running cursor
+                    // puts them; the emit pass writes them there
+                    const uint32_t incl = warp_incl_scan(m);
+                    const uint32_t wt = __shfl_sync(0xffffffffu, incl, 31);
+                    uint32_t base = 0;
+                    if (lane == 0 && wt) base = atomicAdd(&s_cursor, wt);
+                    base = __shfl_sync(0xffffffffu, base, 0);
+                    if (j < sn) {
+                        const bool narrow = hi - lo <= 32;
+                        rec.rows[it * TH_SCH + j] =
+                            make_uint2(mask, narrow ? ((base + incl - m) << 13) | lo : TH_WIDE);
+                        if (!narrow) s_wide = 1;
+                    }
+                }
+            }
+        }
+        if (record) {
+            // a narrow item's offsets fit (at most TH_SCH * 32 pairs); its
+            // staged payloads are what its records point into
+            __syncthreads();
+            const bool wide = s_wide != 0;
+            if (!wide)
+                for (int i = threadIdx.x; i < rn; i += TH_T) rec.pay[it * TH_RCAP + i] = s_p[i];
+            if (threadIdx.x == 0) {
+                rec.sdesc[it] = (sbeg << 14) | ((uint64_t)sn << 1) | (wide ? 1u : 0u);
+                if (wide) atomicOr(rec.any_wide, 1u);
             }
         }
         if (MODE != MODE_EMIT) {
@@ -426,10 +625,7 @@ k_cross_emit(const R* __restrict__ rrows, const uint64_t* __restrict__ roff, con
         for (uint64_t q = q0 + threadIdx.x; q < q1; q += blockDim.x) {
             const uint64_t si = q / len, ri = q - si * len;
             const uint64_t r = ri < l0 ? b0 + ri : b1 + (ri - l0);
-            jn_pair v;
-            v.r = rrows[r].pay;
-            v.s = srows[soff[y] + si].pay;
-            out[obase + q] = v;
+            st_pair(out + obase + q, rrows[r].pay, srows[soff[y] + si].pay);
         }
     }
 }
@@ -546,25 +742,36 @@ static jn_status run_theta_t(jn_ctx* c, const Cols<K>& R, const Cols<K>& S, int 
     JN_TRY(s.get(&ioff, nitems + 1));
     JN_TRY(s.get(&chk, 1));
     JN_TRY(zero(c, chk, 8));
-    const size_t smj = (size_t)TH_RCAP * (2 * sizeof(K) + 4) + sizeof(uint32_t) * TH_NFB;
     const int cm = mode == MODE_AGG ? MODE_AGG : MODE_COUNT;
     auto pick = [&](int m) {
         if (m == MODE_EMIT) return k_theta_join<K, MODE_EMIT, B>;
         if (m == MODE_AGG) return k_theta_join<K, MODE_AGG, B>;
         return k_theta_join<K, MODE_COUNT, B>;
     };
-    auto grid_of = [&](const void* fn) {
+    auto grid_of = [&](const void* fn, size_t smj) {
         int per = 0;
         ensure_smem(fn, smj);
         cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, fn, TH_T, smj);
         return max(per, 1) * c->num_sms;
     };
+    // a band join that emits records every S row's matches in the count
+    // pass (a few bytes per row and staged R row), so the emit pass gathers
+    // them instead of staging and testing again
+    ThetaRec rec{nullptr, nullptr, nullptr, nullptr};
+    if (B && mode == MODE_EMIT && nitems && nitems <= (uint64_t)(4ull << 30) / (TH_SCH * 8 + TH_RCAP * 4)) {
+        JN_TRY(s.get(&rec.rows, nitems * TH_SCH));
+        JN_TRY(s.get(&rec.pay, nitems * TH_RCAP));
+        JN_TRY(s.get(&rec.sdesc, nitems));
+        rec.any_wide = reinterpret_cast<unsigned int*>(d_small + 2);
+        JN_TRY(zero(c, d_small + 2, 8));
+    }
     if (nitems) {
         auto kc = pick(cm);
         JN_TRY(zero(c, work, 4));
-        JN_TRY(launch(c, K_THETA_COUNT, kc, dim3(grid_of((const void*)kc)), dim3(TH_T), smj, (const RW*)rrows,
+        JN_TRY(launch(c, K_THETA_COUNT, kc, dim3(grid_of((const void*)kc, theta_smem<K>(cm))), dim3(TH_T),
+                      theta_smem<K>(cm), (const RW*)rrows,
                       (const uint64_t*)roff, (const RW*)srows, (const uint64_t*)soff, ts, G, (const uint64_t*)ipre,
-                      ival, chk, (const uint64_t*)nullptr, (jn_pair*)nullptr, work));
+                      ival, chk, (const uint64_t*)nullptr, (jn_pair*)nullptr, work, rec));
     }
     JN_TRY(scan_u64(c, reinterpret_cast<const uint64_t*>(ival), ioff, (int64_t)nitems));
     if (has_cross && mode == MODE_AGG) {
@@ -581,7 +788,8 @@ static jn_status run_theta_t(jn_ctx* c, const Cols<K>& R, const Cols<K>& S, int 
     JN_CUDA(c, cudaMemcpyAsync(d_small + 1, chk, 8, cudaMemcpyDeviceToDevice, c->stream));
     if (has_cross) JN_CUDA(c, cudaMemcpyAsync(d_small + 2, coff + G, 8, cudaMemcpyDeviceToDevice, c->stream));
     uint64_t h[3] = {0, 0, 0};
-    JN_TRY(read_back(c, d_small, h, has_cross ? 3 : 2));
+    JN_TRY(read_back(c, d_small, h, (has_cross || rec.rows) ? 3 : 2));
+    const bool any_wide = rec.rows && (h[2] & 0xffffffffu) != 0;
     const uint64_t diag = h[0], crossn = has_cross ? h[2] : 0;
     const uint64_t total = diag + crossn;
     res->count = total;
@@ -595,13 +803,21 @@ static jn_status run_theta_t(jn_ctx* c, const Cols<K>& R, const Cols<K>& S, int 
     info.cartesian_bound = compared + crossn;  // cross regions are written whole
     if (mode != MODE_EMIT) return JN_OK;
     JN_TRY(out_prepare(c, s, total, *plan));
-    if (diag) {
+    if constexpr (B) {
+        if (diag && rec.rows)
+            JN_TRY(launch(c, K_THETA_GATHER, k_theta_gather<K>,
+                          dim3((unsigned)min(nitems, (uint64_t)8 * c->num_sms)), dim3(TH_T), 0, (const RW*)srows,
+                          (const uint64_t*)(ipre + G), (const uint64_t*)ioff, rec, plan->dev));
+    }
+    if (diag && (!rec.rows || any_wide)) {
+        // every item, or (after the gather) the wide ones
         auto ke = pick(MODE_EMIT);
         JN_TRY(zero(c, work, 4));
-        JN_TRY(launch(c, K_THETA_EMIT, ke, dim3(grid_of((const void*)ke)), dim3(TH_T), smj, (const RW*)rrows,
+        JN_TRY(launch(c, K_THETA_EMIT, ke, dim3(grid_of((const void*)ke, theta_smem<K>(MODE_EMIT))), dim3(TH_T),
+                      theta_smem<K>(MODE_EMIT), (const RW*)rrows,
                       (const uint64_t*)roff, (const RW*)srows, (const uint64_t*)soff, ts, G, (const uint64_t*)ipre,
                       (unsigned long long*)nullptr, (unsigned long long*)nullptr, (const uint64_t*)ioff, plan->dev,
-                      work));
+                      work, rec));
     }
     if (crossn) {
         JN_TRY(zero(c, work, 4));
@@ -814,7 +1030,7 @@ struct BandBatchRun : BatchRun {
         JN_CUDA(c, cudaMemcpyAsync(h_groups, groups.data(), sizeof(int) * m, cudaMemcpyHostToDevice, c->stream));
         JN_CUDA(c, cudaStreamSynchronize(c->stream));  // the host vectors go out of scope below
         ts = ThetaSet{prm, d_band, d_op, d_groups, 10};
-        smj = (size_t)TH_RCAP * (2 * sizeof(K) + 4) + sizeof(uint32_t) * TH_NFB;
+        smj = theta_smem<K>(MODE_COUNT);
 
         // ---- phase 1a: ranges, range partition and work items ----
         {
@@ -893,7 +1109,8 @@ struct BandBatchRun : BatchRun {
                     if ((st = launch(c, K_THETA_COUNT, kc, dim3(max(per, 1) * c->num_sms), dim3(TH_T), smj,
                                      (const RW*)prow, (const uint64_t*)start, (const RW*)prow,
                                      (const uint64_t*)(start + P), ts, (int)P, (const uint64_t*)ipre, ival, chk,
-                                     (const uint64_t*)nullptr, (jn_pair*)nullptr, work)) != JN_OK)
+                                     (const uint64_t*)nullptr, (jn_pair*)nullptr, work,
+                                     ThetaRec{nullptr, nullptr, nullptr, nullptr})) != JN_OK)
                         break;
                 }
                 if ((st = scan_u64(c, reinterpret_cast<const uint64_t*>(ival), ioff, (int64_t)nitems)) != JN_OK) break;
@@ -923,13 +1140,14 @@ struct BandBatchRun : BatchRun {
         jn_status st = zero(c, work, 4);
         if (st == JN_OK) {
             auto ke = k_theta_join<K, MODE_EMIT, true>;
-            ensure_smem((const void*)ke, smj);
+            const size_t sme = theta_smem<K>(MODE_EMIT);
+            ensure_smem((const void*)ke, sme);
             int per = 0;
-            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, ke, TH_T, smj);
-            st = launch(c, K_THETA_EMIT, ke, dim3(max(per, 1) * c->num_sms), dim3(TH_T), smj, (const RW*)prow,
+            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, ke, TH_T, sme);
+            st = launch(c, K_THETA_EMIT, ke, dim3(max(per, 1) * c->num_sms), dim3(TH_T), sme, (const RW*)prow,
                         (const uint64_t*)start, (const RW*)prow, (const uint64_t*)(start + P), ts, (int)P,
                         (const uint64_t*)ipre, (unsigned long long*)nullptr, (unsigned long long*)nullptr,
-                        (const uint64_t*)ioff, out, work);
+                        (const uint64_t*)ioff, out, work, ThetaRec{nullptr, nullptr, nullptr, nullptr});
         }
         if (st != JN_OK) {
             gp.abort();

@@ -203,6 +203,40 @@ def test_table_rows_rejected(ctx):
             ctx.set_tuning(table_rows=0)
 
 
+def test_output_buffer_off_8_byte_boundary(ctx):
+    # the kernels store a pair as one 8-byte word: a caller device buffer 4
+    # bytes off that boundary is filled by a copy, for every join and the batch
+    r = keys(20000, 0, 5000, 17, 0)
+    s = keys(30000, 0, 5000, 17, 1)
+    R, S = jn.table(r.to(DEV)), jn.table(s.to(DEV))
+    exp = canon(O.hash_join(r.numpy(), s.numpy()))
+    m = exp.shape[0]
+    flat = torch.full((2 * m + 3,), -7, dtype=torch.int32, device=DEV)
+    out = flat[1:2 * m + 1].view(m, 2)
+    assert out.data_ptr() % 8 == 4
+    for fn in (jn.jn_hash, jn.jn_sort_merge):
+        flat.fill_(-7)
+        got = fn(ctx, R, S, out=out)
+        assert np.array_equal(canon(got), exp)
+        assert flat[0].item() == -7 and flat[2 * m + 1].item() == -7  # nothing written outside
+    ra, rk = datagen.band_columns(3000, 12, seed=18, stream=0)
+    sa, sk = datagen.band_columns(5000, 12, seed=18, stream=1)
+    Rb, Sb = jn.table(ra.to(DEV), rk.to(DEV)), jn.table(sa.to(DEV), sk.to(DEV))
+    expb = canon(O.band_join_sorted(ra.numpy(), rk.numpy(), sa.numpy(), sk.numpy(), O.LT, 5))
+    mb = expb.shape[0]
+    fb = torch.full((2 * mb + 3,), -7, dtype=torch.int32, device=DEV)
+    outb = fb[1:2 * mb + 1].view(mb, 2)
+    assert np.array_equal(canon(jn.jn_theta(ctx, Rb, Sb, jn.JN_LT, 5, out=outb)), expb)
+    assert np.array_equal(canon(jn.jn_nested_loop(ctx, Rb, Sb, jn.pred(jn.JN_LT, jn.JN_ANY, 5), out=outb)), expb)
+    assert fb[0].item() == -7 and fb[2 * mb + 1].item() == -7
+    pairs, first, cnt = jn.jn_batch(ctx, [(R, S, jn.JN_EQ, -1), (Rb, Sb, jn.JN_LT, 5)],
+                                    out=torch.empty((2 * (m + mb) + 1,), dtype=torch.int32,
+                                                    device=DEV)[1:].view(m + mb, 2))
+    assert cnt == [m, mb]
+    assert np.array_equal(canon(pairs[first[0]:first[0] + m]), exp)
+    assert np.array_equal(canon(pairs[first[1]:first[1] + mb]), expb)
+
+
 @pytest.mark.parametrize("dt", [torch.int32, torch.int64])
 @pytest.mark.parametrize("pre", [0, 2, 3])
 def test_region_path_many_chunks_ragged(ctx, dt, pre):
@@ -401,6 +435,35 @@ def test_band_join_widths_and_groups(ctx, band, groups):
     finally:
         ctx.set_tuning(theta_groups=0)
     assert np.array_equal(canon(got), exp)
+
+
+@pytest.mark.parametrize("dt", [torch.int32, torch.int64])
+@pytest.mark.parametrize("op", [jn.JN_LT, jn.JN_NE])
+def test_band_join_narrow_and_wide_items(ctx, dt, op):
+    # sparse R keys leave every S row a handful of candidates (its matches
+    # are recorded by the count pass and gathered), except near a dense
+    # cluster of R keys, where S rows have hundreds (those items are emitted
+    # by testing again); several S chunks per group and a ragged last one
+    nr, ns = 60000, 300000
+    ra = keys(nr, 0, 1000, 23, 0, dt)
+    rk = keys(nr, 0, 1 << 22, 23, 1, dt)
+    rk[:3000] = keys(3000, 2000000, 2000040, 23, 2, dt)
+    sa = keys(ns, 0, 1000, 23, 3, dt)
+    sk = keys(ns, 0, 1 << 22, 23, 4, dt)
+    sk[:5000] = keys(5000, 1999990, 2000050, 23, 5, dt)
+    band = 20
+    exp = canon(O.band_join_sorted(ra.numpy(), rk.numpy(), sa.numpy(), sk.numpy(), op, band))
+    R = jn.table(ra.to(DEV), rk.to(DEV))
+    S = jn.table(sa.to(DEV), sk.to(DEV))
+    for groups in (0, 6, 10):
+        ctx.set_tuning(theta_groups=groups)
+        try:
+            got = jn.jn_theta(ctx, R, S, op, band)
+            cnt = jn.jn_count(ctx, jn.JN_ALGO_THETA, R, S, jn.pred(op, jn.JN_ANY, band))
+        finally:
+            ctx.set_tuning(theta_groups=0)
+        assert cnt == exp.shape[0]
+        assert np.array_equal(canon(got), exp)
 
 
 @pytest.mark.parametrize("op", [jn.JN_LT, jn.JN_LE, jn.JN_GT, jn.JN_GE, jn.JN_EQ, jn.JN_NE, jn.JN_ANY])
