@@ -528,15 +528,30 @@ def serve_main(args, world, rank, local, dev, stream, jn, ctx):
     # one at a time, through the library on one context, admitted by the same budget
     ctx.set_memory_limit(budget)
 
+    def note(msg):
+        if args.verbose:
+            print("[serve %.1fs] %s" % (time.perf_counter() - t_start, msg), file=sys.stderr, flush=True)
+
+    t_start = time.perf_counter()
+    note("pool of %d tables ready" % len(pool))
+
     def one(q):
+        t = time.perf_counter()
         try:
             if q["kind"] == "equi":
-                return jn.jn_hash(ctx, eq_t[q["r"]], eq_t[q["s"]]).shape[0]
-            return jn.jn_theta(ctx, bd_t[q["r"]], bd_t[q["s"]], q["op"], q["band"]).shape[0]
+                m = jn.jn_hash(ctx, eq_t[q["r"]], eq_t[q["s"]]).shape[0]
+            else:
+                m = jn.jn_theta(ctx, bd_t[q["r"]], bd_t[q["s"]], q["op"], q["band"]).shape[0]
         except jn.JoinError as e:
             if e.status != jn.JN_ERR_OOM:
                 raise
-            return -1
+            m = -1
+        dt = time.perf_counter() - t
+        if dt > 1.0:
+            note("slow request %s: %d x %d rows, theta %.2f / %.2f, %.1f s, %d pairs"
+                 % (q["kind"], pool[q["r"]]["rows"], pool[q["s"]]["rows"], pool[q["r"]]["theta"],
+                    pool[q["s"]]["theta"], dt, m))
+        return m
 
     for q in reqs[:16]:
         one(q)
@@ -545,12 +560,14 @@ def serve_main(args, world, rank, local, dev, stream, jn, ctx):
     m_of = [one(q) for q in reqs]
     torch.cuda.synchronize()
     t_one = time.perf_counter() - t0
+    note("one at a time: %d requests in %.1f s" % (n_req, t_one))
     ctx.set_memory_limit(0)
     rows = [pool[q["r"]]["rows"] + pool[q["s"]]["rows"] for q in reqs]
     units = sum(rows[i] + m_of[i] for i in range(n_req) if m_of[i] >= 0)
     cap_rps = n_req / t_one
 
     srv = jn.Server(local, slots=args.serve_slots, coalesce_rows=1 << 18, max_batch=64,
+                    small_slots=args.serve_small_slots,
                     memory_budget=budget, graphs=False)
     handles = {i: srv.register(eq_t[i]) for i in resident}
 
@@ -574,16 +591,34 @@ def serve_main(args, world, rank, local, dev, stream, jn, ctx):
         lat = [0.0] * count
         status = [0] * count
         got_m = [0] * count
+        run = [0.0] * count
 
         def waiter():
-            for i in range(count):
-                while tickets[i] is None:
-                    time.sleep(0.0002)
-                res = srv.wait(tickets[i])
+            # results are collected and released in completion order, so
+            # held outputs never wait on an earlier, slower request
+            while tickets[0] is None:
+                time.sleep(0.0002)
+            t0 = tickets[0]  # this stream's tickets are consecutive
+            for _ in range(count):
+                got = None
+                while got is None:
+                    try:
+                        got = srv.wait_any(1000)
+                        if got is None:
+                            st = srv.stats()
+                            note("waiting 1 s for a completion: %d of %d collected, %d queued, %d MB held"
+                                 % (_, count, st["queued"], st["held_bytes"] >> 20))
+                    except jn.JoinError as e:  # every result so far collected: more to come
+                        if e.status != jn.JN_ERR_INVALID:
+                            raise
+                        time.sleep(0.0002)
+                t, res = got
+                i = t - t0
                 status[i] = res["status"]
                 lat[i] = res["total_ms"]
+                run[i] = res["run_ms"]
                 got_m[i] = res["pairs"]
-                srv.release(tickets[i])
+                srv.release(t)
 
         th = threading.Thread(target=waiter)
         th.start()
@@ -599,9 +634,22 @@ def serve_main(args, world, rank, local, dev, stream, jn, ctx):
         ls = sorted(lat[i] for i in ok)
         pct = (lambda p: ls[min(len(ls) - 1, int(p * len(ls)))] if ls else None)
         refused = [i for i in range(count) if status[i] == jn.JN_ERR_OOM]
+        rs = sorted(run[i] for i in ok)
+        run_pct = (lambda p: rs[min(len(rs) - 1, int(p * len(rs)))] if rs else None)
+        # slowdown: latency over the request's own run time (queueing it saw)
+        sds = sorted(lat[i] / max(run[i], 1e-3) for i in ok)
+        sd_pct = (lambda p: sds[min(len(sds) - 1, int(p * len(sds)))] if sds else None)
+        by_class = {}
+        for name, sel in (("small", lambda i: rows[i] < (1 << 18)), ("large", lambda i: rows[i] >= (1 << 18))):
+            lc = sorted(lat[i] for i in ok if sel(i))
+            if lc:
+                by_class[name] = {"n": len(lc), "p50_ms": lc[len(lc) // 2],
+                                  "p99_ms": lc[min(len(lc) - 1, int(0.99 * len(lc)))]}
         return {"offered_req_s": rate, "achieved_req_s": len(ok) / wall, "wall_s": wall, "ok": len(ok),
                 "refused_oom": len(refused), "failed": count - len(ok) - len(refused),
-                "p50_ms": pct(0.5), "p99_ms": pct(0.99),
+                "p50_ms": pct(0.5), "p99_ms": pct(0.99), "by_size": by_class,
+                "run_p50_ms": run_pct(0.5), "run_p99_ms": run_pct(0.99),
+                "slowdown_p50": sd_pct(0.5), "slowdown_p99": sd_pct(0.99),
                 "tuples_per_s": sum(rows[i] + got_m[i] for i in ok) / wall,
                 "results_match": all(got_m[i] == m_of[i] for i in ok)
                 and all(m_of[i] < 0 for i in refused)}
@@ -609,9 +657,14 @@ def serve_main(args, world, rank, local, dev, stream, jn, ctx):
     clk = ClockSampler(local)
     clk.start()
     run_stream(None, min(n_req, 500))  # warm-up: worker contexts, pools
+    note("server warm-up done")
     tw0 = time.time()
     sat = run_stream(None, n_req)
-    rates = [dict(run_stream(f * cap_rps, n_req), fraction=f) for f in (0.5, 0.8, 0.95)]
+    note("saturation: %.1f req/s" % sat["achieved_req_s"])
+    rates = []
+    for f in (0.5, 0.8, 0.95):
+        rates.append(dict(run_stream(f * cap_rps, n_req), fraction=f))
+        note("Poisson at %.2f of one-at-a-time: p50 %.2f ms, p99 %.2f ms" % (f, rates[-1]["p50_ms"], rates[-1]["p99_ms"]))
     clk.mark(tw0, time.time())
     clocks = clk.stop()
     st = srv.stats()
@@ -626,7 +679,8 @@ def serve_main(args, world, rank, local, dev, stream, jn, ctx):
                                        " tables of %d-%d rows, int32/int64 50/50, Zipf(theta ~ U[0,1]) keys over "
                                        "2^28 ranks, half the requests on resident tables by handle"
                                        % (n_req, 10000, pool_hi(small)),
-                           "pool_tables": len(pool), "slots": args.serve_slots, "coalesce_rows": 1 << 18,
+                           "pool_tables": len(pool), "slots": args.serve_slots, "small_slots": args.serve_small_slots,
+                           "coalesce_rows": 1 << 18,
                            "memory_budget": budget, "resident_requests": sum(q["resident"] for q in reqs),
                            "l2": "tables up to 64M rows; no flush between requests",
                            "parallelism": "replicas" if world > 1 else "1 GPU"},
@@ -818,6 +872,9 @@ def main():
                     help="time the join at every partition-bit (hash) or group (band) count; one JSON line")
     ap.add_argument("--serve-requests", type=int, default=10000, help="serve workload: requests per stream")
     ap.add_argument("--serve-slots", type=int, default=4, help="serve workload: server worker slots")
+    ap.add_argument("--serve-small-slots", type=int, default=1,
+                    help="serve workload: slots that take only small requests (a lane for them)")
+    ap.add_argument("--verbose", action="store_true", help="progress lines on stderr")
     args = ap.parse_args()
     world, rank, local = dist_setup(args)
     if args.impl == "reference":

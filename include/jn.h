@@ -339,7 +339,8 @@ jn_status jn_autotune_batch(jn_ctx* ctx, int32_t count, const jn_join* joins, jn
  * Small requests (|R| + |S| < coalesce_rows) waiting at the same time are
  * run together as one jn_batch (at most max_batch of them); larger requests
  * run alone after an exact count pass and wait until their scratch estimate
- * plus exact output fits memory_budget next to the outputs still held.
+ * plus exact output fits memory_budget next to the outputs still held, as
+ * long as another request is running (see jn_server_wait_any).
  * Tables registered with the server stay resident on the device.  The paper
  * has no serving layer; this is the request loop around its join method. */
 typedef struct jn_server jn_server;
@@ -350,6 +351,14 @@ typedef struct {
     int32_t max_batch;       /* requests per coalesced batch, >= 1                  */
     int32_t graphs;          /* 1: batches replay their phases as CUDA graphs       */
     uint64_t memory_budget;  /* device bytes for scratch and held outputs           */
+    int32_t small_slots;     /* of the slots, how many serve only requests below
+                                coalesce_rows (a lane a small request never waits in
+                                behind a large one); 0..slots-1                     */
+    int32_t hold_wait_ms;    /* a request that does not fit next to the results the
+                                client holds, while no other request runs, waits this
+                                long (ms, >= 0) for a release, then is refused
+                                (JN_ERR_OOM): bounded, so a client that releases in
+                                submission order cannot deadlock the server          */
 } jn_server_config;
 
 typedef struct {
@@ -386,6 +395,13 @@ jn_status jn_server_register(jn_server* s, const jn_table* t, int32_t* handle);
 jn_status jn_server_unregister(jn_server* s, int32_t handle);
 jn_status jn_server_submit(jn_server* s, const jn_request* req, uint64_t* ticket);
 jn_status jn_server_wait(jn_server* s, uint64_t ticket, jn_result* res);  /* blocks */
+/* Returns the oldest completed request whose result no wait has returned yet
+ * (its ticket and result): blocks up to timeout_ms (< 0: no limit), then
+ * JN_ERR_TIMEOUT; JN_ERR_INVALID when every submitted request's result has
+ * been returned.  Releasing results in completion order keeps held outputs
+ * from filling the budget: a request that cannot fit next to held results
+ * while no other request runs is refused with JN_ERR_OOM, not left waiting. */
+jn_status jn_server_wait_any(jn_server* s, uint64_t* ticket, jn_result* res, int64_t timeout_ms);
 jn_status jn_server_release(jn_server* s, uint64_t ticket);  /* frees the pairs of a done request */
 jn_status jn_server_stats_get(jn_server* s, jn_server_stats* out);
 

@@ -7,7 +7,9 @@
 // others run is admitted as soon as a slot and memory allow, not after the
 // current group ends).  A worker that finds small requests at the head of the
 // queue takes up to max_batch of them and runs them as one jn_batch (one
-// launch sequence for the group); a large request runs alone.  Admission is
+// launch sequence for the group); a large request runs alone.  The first
+// small_slots workers take small requests only, so a small request has a
+// lane where it never waits behind a large join.  Admission is
 // by device memory: a request reserves its scratch estimate, and the join's
 // own exact count pass, through the context's admission hook, reserves the
 // exact output bytes before the output is allocated.  A run that does not fit
@@ -46,6 +48,7 @@ struct Job {
     jn_request req{};
     Clock::time_point submitted, started, finished;
     bool done = false;
+    bool collected = false;  // its result was returned by a wait
     jn_status status = JN_OK;
     uint64_t pairs = 0;
     jn_pair* out = nullptr;
@@ -72,6 +75,9 @@ struct jn_server {
     int32_t next_handle = 1;
     uint64_t next_ticket = 1;
     uint64_t mem_held = 0;  // bytes of outputs not yet released + scratch reserved by running requests
+    int running = 0;        // requests holding a reservation (their end frees their scratch)
+    uint64_t queued_small = 0;  // queued requests below coalesce_rows
+    std::deque<uint64_t> done_order;  // tickets in completion order, for jn_server_wait_any
     bool stop = false;
     std::vector<std::thread> workers;
     jn_server_stats stats{};
@@ -118,25 +124,45 @@ void finish(jn_server* s, const std::shared_ptr<Job>& j, jn_status st, uint64_t 
     j->buf = buf;
     if (err) j->err = err;
     j->done = true;
+    s->done_order.push_back(j->ticket);
     s->stats.completed++;
     if (st != JN_OK) s->stats.failed++;
     s->cv_done.notify_all();
 }
 
-// Waits until `bytes` more fit the budget (false: they never can).
+// Reserves `bytes` of the budget for a run (false: refused).  While another
+// request runs it waits for it (its end frees scratch).  With nothing
+// running, only the client can free memory, by releasing results it holds:
+// the request waits at most hold_wait_ms (summed over such stretches) and is
+// then refused, since that release may itself wait on this request.
 bool reserve(jn_server* s, uint64_t bytes) {
     std::unique_lock<std::mutex> lk(s->mu);
     if (bytes > s->cfg.memory_budget) return false;
-    s->cv_mem.wait(lk, [&] { return s->stop || s->mem_held + bytes <= s->cfg.memory_budget; });
-    if (s->stop) return false;
+    auto fits = [&] { return s->stop || s->mem_held + bytes <= s->cfg.memory_budget; };
+    auto idle_left = std::chrono::milliseconds(s->cfg.hold_wait_ms);
+    while (!fits()) {
+        if (s->running > 0) {
+            s->cv_mem.wait(lk);
+            continue;
+        }
+        if (idle_left.count() <= 0) break;
+        const auto t0 = Clock::now();
+        s->cv_mem.wait_for(lk, idle_left);
+        idle_left -= std::chrono::duration_cast<std::chrono::milliseconds>(Clock::now() - t0) +
+                     std::chrono::milliseconds(1);
+    }
+    if (s->stop || s->mem_held + bytes > s->cfg.memory_budget) return false;
     s->mem_held += bytes;
+    s->running++;
     if (s->mem_held > s->stats.peak_bytes) s->stats.peak_bytes = s->mem_held;
     return true;
 }
 
+// Ends a run's reservation, returning `bytes` to the budget.
 void unreserve(jn_server* s, uint64_t bytes) {
     std::lock_guard<std::mutex> g(s->mu);
     s->mem_held -= bytes;
+    s->running--;
     s->cv_mem.notify_all();
 }
 
@@ -302,7 +328,15 @@ void run_group(jn_server* s, jn_ctx* ctx, Admit* a, cudaStream_t stream, std::ve
 void worker_main(jn_server* s, int slot) {
     cudaSetDevice(s->device);
     cudaStream_t stream = nullptr;
-    cudaStreamCreateWithFlags(&stream, cudaStreamNonBlocking);
+    if (slot < s->cfg.small_slots) {
+        // the small-request lane's stream has the highest priority: its
+        // blocks go first as SMs free up, ahead of the large joins' kernels
+        int least = 0, greatest = 0;
+        cudaDeviceGetStreamPriorityRange(&least, &greatest);
+        cudaStreamCreateWithPriority(&stream, cudaStreamNonBlocking, greatest);
+    } else {
+        cudaStreamCreateWithFlags(&stream, cudaStreamNonBlocking);
+    }
     jn_ctx* ctx = nullptr;
     if (jn_create(&ctx, s->device, stream) != JN_OK) {
         cudaStreamDestroy(stream);
@@ -316,23 +350,32 @@ void worker_main(jn_server* s, int slot) {
     adm.s = s;
     adm.ctx = ctx;
     jn_set_admission(ctx, admit_hook, &adm);
-    (void)slot;
+    // the first small_slots workers form the small-request lane: they take
+    // only requests below coalesce_rows, so those never queue behind a large
+    // join; the other workers take the queue in order
+    const bool small_lane = slot < s->cfg.small_slots;
+    const uint64_t small_rows = (uint64_t)s->cfg.coalesce_rows;
     while (true) {
         std::vector<std::shared_ptr<Job>> take;
         {
             std::unique_lock<std::mutex> lk(s->mu);
-            s->cv_work.wait(lk, [&] { return s->stop || !s->queue.empty(); });
+            s->cv_work.wait(lk, [&] { return s->stop || (small_lane ? s->queued_small > 0 : !s->queue.empty()); });
             if (s->stop && s->queue.empty()) break;
-            auto head = s->queue.front();
-            s->queue.pop_front();
+            if (s->stop && small_lane && s->queued_small == 0) break;
+            auto hit = s->queue.begin();
+            if (small_lane)
+                while (rows_of((*hit)->req) >= small_rows) ++hit;  // queued_small > 0: one exists
+            auto head = *hit;
+            s->queue.erase(hit);
             take.push_back(head);
-            if (rows_of(head->req) < (uint64_t)s->cfg.coalesce_rows) {
+            if (rows_of(head->req) < small_rows) {
+                s->queued_small--;
                 // coalesce the small requests waiting now
                 for (auto it = s->queue.begin(); it != s->queue.end() && (int)take.size() < s->cfg.max_batch;) {
-                    if (rows_of((*it)->req) < (uint64_t)s->cfg.coalesce_rows &&
-                        (*it)->req.R.key_type == head->req.R.key_type) {
+                    if (rows_of((*it)->req) < small_rows && (*it)->req.R.key_type == head->req.R.key_type) {
                         take.push_back(*it);
                         it = s->queue.erase(it);
+                        s->queued_small--;
                     } else {
                         ++it;
                     }
@@ -353,7 +396,8 @@ void worker_main(jn_server* s, int slot) {
 extern "C" {
 
 jn_status jn_server_create(jn_server** out, int device, const jn_server_config* cfg) {
-    if (!out || !cfg || cfg->slots < 1 || cfg->slots > 16 || cfg->max_batch < 1)
+    if (!out || !cfg || cfg->slots < 1 || cfg->slots > 16 || cfg->max_batch < 1 || cfg->small_slots < 0 ||
+        cfg->small_slots >= cfg->slots || cfg->hold_wait_ms < 0)
         return JN_ERR_INVALID;
     int ndev = 0;
     if (cudaGetDeviceCount(&ndev) != cudaSuccess || device < 0 || device >= ndev) {
@@ -469,11 +513,25 @@ jn_status jn_server_submit(jn_server* s, const jn_request* req, uint64_t* ticket
         j->submitted = Clock::now();
         s->jobs[j->ticket] = j;
         s->queue.push_back(j);
+        if (rows_of(j->req) < (uint64_t)s->cfg.coalesce_rows) s->queued_small++;
         s->stats.submitted++;
         *ticket = j->ticket;
     }
-    s->cv_work.notify_one();
+    s->cv_work.notify_all();  // a small-lane worker may not take this request
     return JN_OK;
+}
+
+static void fill_result(Job& j, jn_result* res) {
+    j.collected = true;
+    memset(res, 0, sizeof(*res));
+    res->status = j.status;
+    res->pairs = j.pairs;
+    res->out = j.out;
+    using ms = std::chrono::duration<double, std::milli>;
+    res->queue_ms = ms(j.started - j.submitted).count();
+    res->run_ms = ms(j.finished - j.started).count();
+    res->total_ms = ms(j.finished - j.submitted).count();
+    if (j.started.time_since_epoch().count() == 0) res->queue_ms = res->run_ms = 0;
 }
 
 jn_status jn_server_wait(jn_server* s, uint64_t ticket, jn_result* res) {
@@ -483,15 +541,39 @@ jn_status jn_server_wait(jn_server* s, uint64_t ticket, jn_result* res) {
     if (it == s->jobs.end()) return JN_ERR_INVALID;
     auto j = it->second;
     s->cv_done.wait(lk, [&] { return j->done; });
-    memset(res, 0, sizeof(*res));
-    res->status = j->status;
-    res->pairs = j->pairs;
-    res->out = j->out;
-    using ms = std::chrono::duration<double, std::milli>;
-    res->queue_ms = ms(j->started - j->submitted).count();
-    res->run_ms = ms(j->finished - j->started).count();
-    res->total_ms = ms(j->finished - j->submitted).count();
-    if (j->started.time_since_epoch().count() == 0) res->queue_ms = res->run_ms = 0;
+    fill_result(*j, res);
+    return JN_OK;
+}
+
+jn_status jn_server_wait_any(jn_server* s, uint64_t* ticket, jn_result* res, int64_t timeout_ms) {
+    if (!s || !ticket || !res) return JN_ERR_INVALID;
+    std::unique_lock<std::mutex> lk(s->mu);
+    // the oldest completion whose result no wait has returned yet
+    auto ready = [&]() -> std::shared_ptr<Job> {
+        while (!s->done_order.empty()) {
+            auto it = s->jobs.find(s->done_order.front());
+            if (it != s->jobs.end() && !it->second->collected) return it->second;
+            s->done_order.pop_front();  // released, or returned by jn_server_wait
+        }
+        return nullptr;
+    };
+    auto pending = [&] {  // requests whose result is still to be returned
+        for (auto& kv : s->jobs)
+            if (!kv.second->collected) return true;
+        return false;
+    };
+    std::shared_ptr<Job> j = ready();
+    if (!j) {
+        if (!pending()) return JN_ERR_INVALID;  // nothing submitted is outstanding
+        auto pred = [&] { return (j = ready()) != nullptr; };
+        if (timeout_ms < 0)
+            s->cv_done.wait(lk, pred);
+        else if (!s->cv_done.wait_for(lk, std::chrono::milliseconds(timeout_ms), pred))
+            return JN_ERR_TIMEOUT;
+    }
+    s->done_order.pop_front();
+    *ticket = j->ticket;
+    fill_result(*j, res);
     return JN_OK;
 }
 

@@ -72,11 +72,15 @@ __global__ void __launch_bounds__(512) k_minmax(const K* __restrict__ col, int64
         }
     }
     for (int64_t i = head + nv * PER + tid; i < n; i += stride) take((long long)col[i]);
+    // minima combine with minima and maxima with maxima: a thread without
+    // elements holds the empty range (LLONG_MAX, LLONG_MIN)
+    auto merge = [&](long long l, long long h) {
+        lo = l < lo ? l : lo;
+        hi = h > hi ? h : hi;
+    };
 #pragma unroll
-    for (int o = 16; o > 0; o >>= 1) {
-        take(__shfl_xor_sync(0xffffffffu, lo, o));
-        take(__shfl_xor_sync(0xffffffffu, hi, o));
-    }
+    for (int o = 16; o > 0; o >>= 1)
+        merge(__shfl_xor_sync(0xffffffffu, lo, o), __shfl_xor_sync(0xffffffffu, hi, o));
     const int w = threadIdx.x >> 5;
     if ((threadIdx.x & 31) == 0) {
         s_lo[w] = lo;
@@ -84,10 +88,7 @@ __global__ void __launch_bounds__(512) k_minmax(const K* __restrict__ col, int64
     }
     __syncthreads();
     if (threadIdx.x == 0) {
-        for (int k = 1; k < (int)(blockDim.x >> 5); k++) {
-            take(s_lo[k]);
-            take(s_hi[k]);
-        }
+        for (int k = 1; k < (int)(blockDim.x >> 5); k++) merge(s_lo[k], s_hi[k]);
         if (lo <= hi) {
             atomicMin(&mm[0], lo);
             atomicMax(&mm[1], hi);

@@ -60,7 +60,8 @@ class Join(ctypes.Structure):
 
 class ServerConfig(ctypes.Structure):
     _fields_ = [("slots", ctypes.c_int32), ("coalesce_rows", ctypes.c_int32), ("max_batch", ctypes.c_int32),
-                ("graphs", ctypes.c_int32), ("memory_budget", ctypes.c_uint64)]
+                ("graphs", ctypes.c_int32), ("memory_budget", ctypes.c_uint64), ("small_slots", ctypes.c_int32),
+                ("hold_wait_ms", ctypes.c_int32)]
 
 
 class Request(ctypes.Structure):
@@ -147,6 +148,8 @@ _SIGS = {
     "jn_server_unregister": (ctypes.c_int, [_P, ctypes.c_int32]),
     "jn_server_submit": (ctypes.c_int, [_P, ctypes.POINTER(Request), ctypes.POINTER(ctypes.c_uint64)]),
     "jn_server_wait": (ctypes.c_int, [_P, ctypes.c_uint64, ctypes.POINTER(Result)]),
+    "jn_server_wait_any": (ctypes.c_int, [_P, ctypes.POINTER(ctypes.c_uint64), ctypes.POINTER(Result),
+                                          ctypes.c_int64]),
     "jn_server_release": (ctypes.c_int, [_P, ctypes.c_uint64]),
     "jn_server_stats_get": (ctypes.c_int, [_P, ctypes.POINTER(ServerStats)]),
     "jn_set_profiling": (ctypes.c_int, [_P, ctypes.c_int32]),
@@ -408,9 +411,10 @@ class Server:
     """jn_server: a request loop over the library (see jn.h, serving)."""
 
     def __init__(self, device=0, slots=4, coalesce_rows=1 << 18, max_batch=64, memory_budget=64 << 30,
-                 graphs=False):
+                 graphs=False, small_slots=0, hold_wait_ms=2000):
         lib = load()
-        cfg = ServerConfig(slots, coalesce_rows, max_batch, 1 if graphs else 0, memory_budget)
+        cfg = ServerConfig(slots, coalesce_rows, max_batch, 1 if graphs else 0, memory_budget, small_slots,
+                           hold_wait_ms)
         h = _P()
         st = lib.jn_server_create(ctypes.byref(h), device, ctypes.byref(cfg))
         if st != JN_OK:
@@ -458,13 +462,29 @@ class Server:
         self._keep[int(tk.value)] = (R, S)  # columns stay alive until the request is released
         return int(tk.value)
 
+    @staticmethod
+    def _res(r) -> dict:
+        return {"status": r.status, "pairs": int(r.pairs), "out": r.out, "queue_ms": r.queue_ms,
+                "run_ms": r.run_ms, "total_ms": r.total_ms}
+
     def wait(self, ticket: int) -> dict:
         r = Result()
         st = load().jn_server_wait(self.handle, ticket, ctypes.byref(r))
         if st != JN_OK:
             raise JoinError(st, "jn_server_wait failed")
-        return {"status": r.status, "pairs": int(r.pairs), "out": r.out, "queue_ms": r.queue_ms,
-                "run_ms": r.run_ms, "total_ms": r.total_ms}
+        return self._res(r)
+
+    def wait_any(self, timeout_ms: int = -1):
+        """(ticket, result) of the oldest completion not yet returned by a wait;
+        None on timeout."""
+        r = Result()
+        t = ctypes.c_uint64()
+        st = load().jn_server_wait_any(self.handle, ctypes.byref(t), ctypes.byref(r), timeout_ms)
+        if st == JN_ERR_TIMEOUT:
+            return None
+        if st != JN_OK:
+            raise JoinError(st, "jn_server_wait_any failed")
+        return int(t.value), self._res(r)
 
     def pairs(self, res: dict):
         """Copies a finished request's pairs into a new CUDA tensor."""

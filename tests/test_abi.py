@@ -47,6 +47,13 @@ def test_library_loads_and_answers_without_gpu(lib_path):
     assert lib.jn_sort_merge(None, None, None, None, 0, None) == jn.JN_ERR_INVALID
     assert lib.jn_selftest_wait(None, 1, 0, None) == jn.JN_ERR_INVALID
     assert lib.jn_autotune(None, jn.JN_ALGO_SORT, None, None, None, None) == jn.JN_ERR_INVALID
+    assert lib.jn_server_wait_any(None, None, None, 0) == jn.JN_ERR_INVALID
+    # a server configuration is checked before any device is touched: the
+    # small-request lane must leave at least one slot for large requests
+    srv = ctypes.c_void_p()
+    for slots, small, hold in ((4, 4, 0), (4, -1, 0), (1, 1, 0), (2, 0, -1)):
+        cfg = jn.ServerConfig(slots, 1 << 18, 8, 0, 1 << 30, small, hold)
+        assert lib.jn_server_create(ctypes.byref(srv), 0, ctypes.byref(cfg)) == jn.JN_ERR_INVALID
     h = ctypes.c_void_p()
     st = lib.jn_create(ctypes.byref(h), 0, None)
     # no GPU in this container: creation must fail cleanly, not crash

@@ -74,7 +74,7 @@ def test_server_defers_until_memory_is_released():
     r = datagen.uniform_keys(3000, 0, 2, 303, 0)   # about 4.5M pairs: 36 MB of output
     s = datagen.uniform_keys(3000, 0, 2, 303, 1)
     m = O.hash_join(r.numpy(), s.numpy(), count_only=True)
-    srv = jn.Server(0, slots=2, coalesce_rows=0, max_batch=1, memory_budget=64 << 20)
+    srv = jn.Server(0, slots=2, coalesce_rows=0, max_batch=1, memory_budget=64 << 20, hold_wait_ms=20000)
     try:
         R, S = jn.table(r.to(DEV)), jn.table(s.to(DEV))
         torch.cuda.synchronize()

@@ -438,6 +438,26 @@ def test_band_join_widths_and_groups(ctx, band, groups):
 
 
 @pytest.mark.parametrize("dt", [torch.int32, torch.int64])
+@pytest.mark.parametrize("n", [1, 7, 1000, 300001])
+def test_band_groups_follow_the_key_range(ctx, dt, n):
+    # the groups cut [min k, max k] over both tables: with correct extremes a
+    # narrow band compares each S group with about three R groups, far fewer
+    # than |R| * |S| pairs; column lengths leave most threads of the min/max
+    # reduction without elements, and the columns start off a 16-byte boundary
+    nr, ns = n, 2 * n + 5
+    ra, rk = keys(nr + 1, 0, 100, 29, 0, dt), keys(nr + 1, -(1 << 30), 1 << 30, 29, 1, dt)
+    sa, sk = keys(ns, 0, 100, 29, 2, dt), keys(ns, -(1 << 30), 1 << 30, 29, 3, dt)
+    R = jn.table(ra[1:].to(DEV), rk[1:].to(DEV))
+    S = jn.table(sa.to(DEV), sk.to(DEV))
+    exp = canon(O.band_join_sorted(ra[1:].numpy(), rk[1:].numpy(), sa.numpy(), sk.numpy(), O.LT, 7))
+    assert np.array_equal(canon(jn.jn_theta(ctx, R, S, jn.JN_LT, 7)), exp)
+    info = ctx.run_info()
+    assert info["partitions"] >= 4
+    if n >= 1000:
+        assert info["cartesian_bound"] <= nr * ns * 8 // info["partitions"]
+
+
+@pytest.mark.parametrize("dt", [torch.int32, torch.int64])
 @pytest.mark.parametrize("op", [jn.JN_LT, jn.JN_NE])
 def test_band_join_narrow_and_wide_items(ctx, dt, op):
     # sparse R keys leave every S row a handful of candidates (its matches

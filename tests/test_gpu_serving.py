@@ -112,3 +112,64 @@ def test_admission_refuses_what_never_fits():
         srv.release(t_small)
     finally:
         srv.close()
+
+
+@pytest.mark.parametrize("hold_ms", [0, 300])
+def test_held_results_refuse_after_a_bounded_wait(hold_ms):
+    # the client keeps the first result while it waits for the second, which
+    # fits the budget only once that result is released: with nothing else
+    # running the server waits hold_wait_ms for a release, then refuses it
+    # (JN_ERR_OOM) instead of waiting for a release that waits on it;
+    # released results let the same request through
+    import time
+    srv = jn.Server(0, slots=1, coalesce_rows=0, max_batch=1, memory_budget=40 << 20, hold_wait_ms=hold_ms)
+    try:
+        r = datagen.uniform_keys(2000, 0, 2, 3, 0)  # ~2M pairs: 16 MB of output each
+        s = datagen.uniform_keys(2000, 0, 2, 3, 1)
+        R, S = jn.table(r.to(DEV)), jn.table(s.to(DEV))
+        exp = O.hash_join(r.numpy(), s.numpy(), count_only=True)
+        torch.cuda.synchronize()
+        t1 = srv.submit(R, S)
+        first = srv.wait(t1)
+        assert first["status"] == jn.JN_OK and first["pairs"] == exp
+        t0 = time.perf_counter()
+        t2 = srv.submit(R, S)
+        second = srv.wait(t2)  # returns: refused, not a hang
+        assert second["status"] == jn.JN_ERR_OOM
+        assert time.perf_counter() - t0 >= hold_ms * 1e-3
+        srv.release(t2)
+        srv.release(t1)
+        t3 = srv.submit(R, S)
+        third = srv.wait(t3)
+        assert third["status"] == jn.JN_OK and third["pairs"] == exp
+        srv.release(t3)
+    finally:
+        srv.close()
+
+
+@pytest.mark.parametrize("small_slots", [0, 1, 2])
+def test_wait_any_returns_completions_once(small_slots):
+    # with a small-request lane of 1 or 2 of the 3 slots, small and large
+    # requests both complete, each exactly once
+    srv = jn.Server(0, slots=3, coalesce_rows=1 << 12, max_batch=8, memory_budget=1 << 30,
+                    small_slots=small_slots)
+    try:
+        tabs = []
+        for i in range(12):
+            r = datagen.uniform_keys(500 + 3000 * i, 0, 4000, 40 + i, 0)
+            s = datagen.uniform_keys(800 + 2000 * i, 0, 4000, 40 + i, 1)
+            tabs.append((r, s, jn.table(r.to(DEV)), jn.table(s.to(DEV))))
+        torch.cuda.synchronize()
+        tickets = {srv.submit(R, S): i for i, (_, _, R, S) in enumerate(tabs)}
+        seen = set()
+        for _ in range(len(tickets)):
+            t, res = srv.wait_any(-1)
+            assert t in tickets and t not in seen and res["status"] == jn.JN_OK
+            seen.add(t)
+            r, s, _, _ = tabs[tickets[t]]
+            assert np.array_equal(canon(srv.pairs(res)), canon(O.hash_join(r.numpy(), s.numpy())))
+            srv.release(t)
+        with pytest.raises(jn.JoinError):  # nothing outstanding
+            srv.wait_any(10)
+    finally:
+        srv.close()
