@@ -372,6 +372,15 @@ jn_status jn_create(jn_ctx** out, int device, void* stream) {
         uint64_t keep = UINT64_MAX;
         e = cudaMemPoolSetAttribute(c->pool, cudaMemPoolAttrReleaseThreshold, &keep);
     }
+    if (e == cudaSuccess) {
+        // A block freed on one stream is never handed to an allocation on
+        // another by making that stream wait for the free: contexts on their
+        // own streams (server workers) would otherwise queue behind each
+        // other's joins.  Reuse on the same stream, or of a free already
+        // complete, stays allowed.
+        int no = 0;
+        e = cudaMemPoolSetAttribute(c->pool, cudaMemPoolReuseAllowInternalDependencies, &no);
+    }
     if (e == cudaSuccess) e = cudaMallocHost((void**)&c->h_small, 64 * sizeof(uint64_t));
     if (e == cudaSuccess) e = cudaMalloc((void**)&c->d_err, 256);
     if (e == cudaSuccess) e = cudaMemset(c->d_err, 0, 256);
