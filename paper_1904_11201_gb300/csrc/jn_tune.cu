@@ -1,12 +1,13 @@
 // Autotuner: picks tuning knobs by timing them.
 //
 // The knobs that shape the work without changing the result -- the hash
-// join's partition bits, pre-filter and R rows per shared-memory table, the
-// theta join's group count, the nested loop's R tile, a batch's rows per
-// partition -- are tried on the caller's own inputs (the full join when its
-// pairs fit in memory, else the count and checksum), the fastest is applied
-// to the context, and the choice is cached per (algorithm, key type, log2 |R|, log2 |S|) so a later call for the same size
-// class costs nothing.  This plays the part of the paper's choice of alpha
+// join's partition path and bits, pre-filter and R rows per shared-memory
+// table, the theta join's group count, the nested loop's R tile, a batch's
+// rows per partition -- are tried on the caller's own inputs (the full join
+// when its pairs fit in memory, else the count and checksum), the fastest is
+// applied to the context, and the choice is cached per (algorithm, key type,
+// log2 |R|, log2 |S|) so a later call for the same size class costs nothing.
+// This plays the part of the paper's choice of alpha
 // (Sec. 5.1.4 and 5.2.4 sweep it by hand and report the best range).
 #include <algorithm>
 #include <chrono>
@@ -54,19 +55,25 @@ jn_status jn_autotune(jn_ctx* c, int32_t algo, const jn_table* R, const jn_table
     std::vector<jn_tuning> cands;
     if (algo == JN_ALGO_HASH || algo == JN_ALGO_SORT) {
         const int full = jnx::hash_cap(R->key_type);
-        for (int cap : {full, full / 2})  // R rows per shared-memory table
-            for (int pre : {0, 1, 2, 3}) {  // off, both tables, only S, only R
-                const uint64_t target = (pre == 1 || pre == 3) ? cap : cap / 2;  // R rows per partition
-                int b = jnx::ceil_log2(jnx::ceil_div((uint64_t)R->n + 1, target));
-                for (int d = -1; d <= 1; d++) {
-                    jn_tuning t = base;
-                    t.prefilter = pre;
-                    t.radix_bits = std::max(1, std::min(20, b + d));
-                    t.radix_bits1 = 0;
-                    t.table_rows = cap;
-                    cands.push_back(t);
+        // the region path filters a table only at its second level, after
+        // moving all of it once; the two-pass path drops the rows the
+        // pre-filter rejects in its first pass, which wins when the filter
+        // removes most of a large table
+        for (int path : {2, 1})
+            for (int cap : {full, full / 2})  // R rows per shared-memory table
+                for (int pre : {0, 1, 2, 3}) {  // off, both tables, only S, only R
+                    const uint64_t target = (pre == 1 || pre == 3) ? cap : cap / 2;  // R rows per partition
+                    int b = jnx::ceil_log2(jnx::ceil_div((uint64_t)R->n + 1, target));
+                    for (int d = -1; d <= 1; d++) {
+                        jn_tuning t = base;
+                        t.prefilter = pre;
+                        t.radix_bits = std::max(1, std::min(20, b + d));
+                        t.radix_bits1 = 0;
+                        t.table_rows = cap;
+                        t.hash_path = path;
+                        cands.push_back(t);
+                    }
                 }
-            }
     } else if (algo == JN_ALGO_THETA) {
         for (int g = 2; g <= 10; g += 2) {
             jn_tuning t = base;

@@ -35,6 +35,7 @@ def test_autotune_hash_then_join_equals_oracle(ctx):
     t = jn.jn_autotune(ctx, jn.JN_ALGO_HASH, R, S)
     assert t["prefilter"] in (0, 1, 2, 3) and 1 <= t["radix_bits"] <= 20
     assert t["table_rows"] in (2048, 4096)  # the tuner picks the table size too
+    assert t["hash_path"] in (1, 2)  # and the partition path
     assert ctx.tuning()["radix_bits"] == t["radix_bits"]
     jn.jn_hash(ctx, R, S)
     assert ctx.run_info()["table_rows"] == t["table_rows"]
