@@ -71,6 +71,8 @@ def _load():
         lib.or_theta_regions.argtypes = [P, P, I64, P, P, I64, I, I, I64, P, U64, P, P]
         lib.or_thread_ranges.restype = None
         lib.or_thread_ranges.argtypes = [I64, I64, P, P]
+        lib.or_star_nested_loop.restype = U64
+        lib.or_star_nested_loop.argtypes = [P, P, P, I64, P, P, I64, P, P, I64, I, P, U64]
         _lib = lib
     return _lib
 
@@ -126,6 +128,24 @@ def nested_loop(rkey, skey, rkey2=None, skey2=None, rpay=None, spay=None,
     if count_only:
         return int(lib.or_nested_loop(*args, None, 0))
     return _two_call(lib.or_nested_loop, *args)
+
+
+def star_join(rfk1, rfk2, s1key, s2key, rpay=None, s1pay=None, s2pay=None, count_only=False):
+    """O6: star join of R (two join columns) with S1 on fk1 and S2 on fk2, as
+    three nested loops; (n, 3) int32 triples (r, s1, s2)."""
+    lib = _load()
+    rfk1, rfk2, s1key, s2key = _keys(rfk1), _keys(rfk2), _keys(s1key), _keys(s2key)
+    ks = _ksize(rfk1, rfk2, s1key, s2key)
+    assert len(rfk1) == len(rfk2)
+    rp, p1, p2 = _pay(rpay, len(rfk1)), _pay(s1pay, len(s1key)), _pay(s2pay, len(s2key))
+    args = (_ptr(rfk1), _ptr(rfk2), _ptr(rp), len(rfk1), _ptr(s1key), _ptr(p1), len(s1key),
+            _ptr(s2key), _ptr(p2), len(s2key), ks)
+    total = int(lib.or_star_nested_loop(*args, None, 0))
+    if count_only:
+        return total
+    out = np.empty((max(total, 1), 3), dtype=np.int32)
+    assert lib.or_star_nested_loop(*args, out.ctypes.data, total) == total
+    return out[:total]
 
 
 def hash_join(rkey, skey, rpay=None, spay=None, count_only=False):

@@ -619,3 +619,42 @@ void or_thread_ranges(int64_t n, int64_t threads, int64_t* begin, int64_t* end) 
         end[t] = e;
     }
 }
+
+/* ------------------------------------------------------------------------ *
+ * O6: star join of three tables (the multi-table join that Sec. 6 leaves to
+ * future work, built from Sec. 2.3's definition of a join applied twice):
+ * the centre table R carries two join columns, fk1 (key) and fk2 (key2);
+ * every row m of R, row n1 of S1 and row n2 of S2 with
+ *     R.fk1[m] == S1.key[n1]  AND  R.fk2[m] == S2.key[n2]
+ * yields the triple (pay_R[m], pay_S1[n1], pay_S2[n2]).  Plain nested loops:
+ * R outermost, then S1, then S2.
+ * ------------------------------------------------------------------------ */
+typedef struct {
+    int32_t r;
+    int32_t s1;
+    int32_t s2;
+} or_triple;
+
+uint64_t or_star_nested_loop(const void* rfk1, const void* rfk2, const int32_t* rpay, int64_t nr,
+                             const void* s1key, const int32_t* s1pay, int64_t n1,
+                             const void* s2key, const int32_t* s2pay, int64_t n2,
+                             int ksize, or_triple* out, uint64_t cap) {
+    uint64_t cnt = 0;
+    for (int64_t m = 0; m < nr; m++) {
+        int64_t f1 = key_at(rfk1, ksize, m);
+        int64_t f2 = key_at(rfk2, ksize, m);
+        for (int64_t a = 0; a < n1; a++) {
+            if (key_at(s1key, ksize, a) != f1) continue;
+            for (int64_t b = 0; b < n2; b++) {
+                if (key_at(s2key, ksize, b) != f2) continue;
+                if (out && cnt < cap) {
+                    out[cnt].r = pay_at(rpay, m);
+                    out[cnt].s1 = pay_at(s1pay, a);
+                    out[cnt].s2 = pay_at(s2pay, b);
+                }
+                cnt++;
+            }
+        }
+    }
+    return cnt;
+}

@@ -400,3 +400,82 @@ def test_zipf_ranks_follow_the_law():
     assert np.abs(freq - p).max() < 6 * np.sqrt(p.max() / n)
     keys = datagen.rank_to_key32(torch.arange(1 << 12), 12, seed=0)
     assert len(set(keys.tolist())) == 1 << 12        # the rank -> key map is a bijection
+
+
+# ------------------------------------------------------------- star join (O6)
+
+def _star_brute(f1, f2, k1, k2, rp, p1, p2):
+    """Three tables, every combination tested: the definition, in Python."""
+    out = []
+    for (m, a, b) in itertools.product(range(len(f1)), range(len(k1)), range(len(k2))):
+        if f1[m] == k1[a] and f2[m] == k2[b]:
+            out.append((rp[m], p1[a], p2[b]))
+    return sorted(out)
+
+
+@pytest.mark.parametrize("dtype", [np.int32, np.int64])
+def test_star_join_equals_brute_force(dtype):
+    rng = random.Random(61)
+    for trial in range(30):
+        nr, n1, n2 = rng.randint(0, 12), rng.randint(0, 9), rng.randint(0, 9)
+        lo, hi = (-3, 3) if trial % 2 else (-(2 ** 31), -(2 ** 31) + 4)
+        if dtype == np.int64 and trial % 3 == 0:
+            lo, hi = 2 ** 62, 2 ** 62 + 3
+        f1 = np.array([rng.randint(lo, hi) for _ in range(nr)], dtype=dtype)
+        f2 = np.array([rng.randint(lo, hi) for _ in range(nr)], dtype=dtype)
+        k1 = np.array([rng.randint(lo, hi) for _ in range(n1)], dtype=dtype)
+        k2 = np.array([rng.randint(lo, hi) for _ in range(n2)], dtype=dtype)
+        rp = np.array([rng.randint(-1000, 1000) for _ in range(nr)], dtype=np.int32)
+        p1 = np.array([rng.randint(-1000, 1000) for _ in range(n1)], dtype=np.int32)
+        p2 = np.array([rng.randint(-1000, 1000) for _ in range(n2)], dtype=np.int32)
+        got = sorted(map(tuple, O.star_join(f1, f2, k1, k2, rp, p1, p2).tolist()))
+        assert got == _star_brute(f1, f2, k1, k2, rp, p1, p2)
+        # payloads left out are the row indices
+        got_idx = sorted(map(tuple, O.star_join(f1, f2, k1, k2).tolist()))
+        assert got_idx == _star_brute(f1, f2, k1, k2, range(nr), range(n1), range(n2))
+
+
+def test_star_join_count_closed_form():
+    # |R join S1 join S2| = sum over rows m of R of c1(fk1[m]) * c2(fk2[m]),
+    # c1 and c2 the key histograms of S1 and S2
+    rng = np.random.default_rng(62)
+    f1 = rng.integers(0, 50, 3000).astype(np.int32)
+    f2 = rng.integers(0, 70, 3000).astype(np.int32)
+    k1 = rng.integers(0, 60, 400).astype(np.int32)
+    k2 = rng.integers(0, 40, 500).astype(np.int32)
+    c1 = np.bincount(k1, minlength=100)
+    c2 = np.bincount(k2, minlength=100)
+    expect = int((c1[f1].astype(np.int64) * c2[f2]).sum())
+    assert O.star_join(f1, f2, k1, k2, count_only=True) == expect
+    assert O.star_join(f1, f2, k1, k2).shape == (expect, 3)
+
+
+def test_star_join_reduces_to_two_table_join():
+    # S2 holding every fk2 value exactly once: each (r, s1) pair of R join S1
+    # gains exactly the one S2 row of its fk2, so the triples are the pinned
+    # two-table join's pairs with that row appended
+    rng = np.random.default_rng(63)
+    f1 = rng.integers(0, 30, 500).astype(np.int64)
+    f2 = rng.integers(0, 25, 500).astype(np.int64)
+    k1 = rng.integers(0, 30, 200).astype(np.int64)
+    k2 = rng.permutation(25).astype(np.int64)
+    p2 = (np.arange(25, dtype=np.int32) * 7 + 3)
+    tri = O.star_join(f1, f2, k1, k2, s2pay=p2)
+    pairs = O.hash_join(f1, k1)
+    where = {int(k): i for i, k in enumerate(k2)}
+    exp = sorted((int(r), int(s), int(p2[where[int(f2[r])]])) for r, s in pairs)
+    assert sorted(map(tuple, tri.tolist())) == exp
+
+
+def test_star_join_sides_are_not_interchangeable():
+    # fk1 meets only S1 and fk2 only S2: swapping the dimension tables swaps
+    # the roles, which changes the result unless the columns are swapped too
+    f1 = np.array([1, 1, 2], dtype=np.int32)
+    f2 = np.array([5, 6, 5], dtype=np.int32)
+    k1 = np.array([1, 2, 2], dtype=np.int32)
+    k2 = np.array([5, 5, 6], dtype=np.int32)
+    a = sorted(map(tuple, O.star_join(f1, f2, k1, k2).tolist()))
+    assert a == [(0, 0, 0), (0, 0, 1), (1, 0, 2), (2, 1, 0), (2, 1, 1), (2, 2, 0), (2, 2, 1)]
+    assert O.star_join(f1, f2, k2, k1, count_only=True) == 0
+    b = sorted((r, s1, s2) for r, s2, s1 in O.star_join(f2, f1, k2, k1).tolist())
+    assert b == a
