@@ -75,6 +75,14 @@ typedef struct {
     int32_t s;
 } jn_pair;
 
+/* One result of a star join: (R.payload[m], S1.payload[n1], S2.payload[n2]);
+ * row indices when a payload column is NULL. */
+typedef struct {
+    int32_t r;
+    int32_t s1;
+    int32_t s2;
+} jn_triple;
+
 /* Two-column conjunctive predicate:
  *     (R.key op_a S.key) AND (band >= 0 ? |R.key2 - S.key2| <= band
  *                                       : R.key2 op_k S.key2)
@@ -210,6 +218,23 @@ jn_status jn_aggregate(jn_ctx* ctx, int32_t algo, const jn_table* R, const jn_ta
  *                  JN_ERR_CAPACITY with *n_out = the required count and writes
  *                  nothing.  A host buffer is filled by a copy before return.
  * *n_out (host) receives the number of pairs written. */
+
+/* Star join: the multi-table join Sec. 6 leaves to future work, as two of
+ * this library's hash joins (a left-deep plan).  R carries two join columns,
+ * key (fk1) and key2 (fk2); every row m of R, n1 of S1 and n2 of S2 with
+ * R.key[m] == S1.key[n1] and R.key2[m] == S2.key[n2] gives one triple.
+ *   - All key columns share one key type.  R's key2 and payload must be
+ *     device memory (JN_ERR_INVALID otherwise); S1 and S2 may be host memory.
+ *   - The first join's pair count must stay below 2^31 (JN_ERR_UNSUPPORTED).
+ *   - Output: as the two-table joins (*out NULL: the library allocates the
+ *     exact result, release it with jn_free_triples; otherwise a caller buffer
+ *     of `capacity` triples in device or host memory, JN_ERR_CAPACITY with
+ *     *n_out = the required count when it is too small). */
+jn_status jn_star(jn_ctx* ctx, const jn_table* R, const jn_table* S1, const jn_table* S2, jn_triple** out,
+                  uint64_t capacity, uint64_t* n_out);
+jn_status jn_star_count(jn_ctx* ctx, const jn_table* R, const jn_table* S1, const jn_table* S2,
+                        uint64_t* count);
+void jn_free_triples(jn_ctx* ctx, jn_triple* p);
 
 /* Nested-loop join (Sec. 3.3.1): every (R, S) pair is tested with `pred`
  * (NULL = equality on key).  Tiles of R are staged in shared memory and

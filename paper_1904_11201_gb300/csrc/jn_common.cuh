@@ -43,6 +43,7 @@ enum KernelId {
     K_REGION1,
     K_REGION2,
     K_THETA_GATHER,
+    K_STAR,
     K_COUNT_IDS
 };
 

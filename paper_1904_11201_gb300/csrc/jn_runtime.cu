@@ -18,7 +18,7 @@ static const char* kKernelNames[K_COUNT_IDS] = {
     "cross_emit",   "scan_reduce",  "scan_top",    "scan_down",   "nlj_count",
     "nlj_emit",     "minmax",       "theta_count", "theta_emit",  "gather",
     "batch",        "misc",         "sort_count",  "sort_emit",   "sort_chunks",
-    "chunk_hist",   "region1",      "region2",     "theta_gather"};
+    "chunk_hist",   "region1",      "region2",     "theta_gather", "star"};
 
 const char* kernel_name(int kid) {
     return (kid >= 0 && kid < K_COUNT_IDS) ? kKernelNames[kid] : "?";

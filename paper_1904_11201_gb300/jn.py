@@ -136,6 +136,11 @@ _SIGS = {
                                 ctypes.POINTER(ctypes.c_uint64), ctypes.POINTER(ctypes.c_uint64),
                                 ctypes.POINTER(ctypes.c_uint64)]),
     "jn_free": (None, [_P, _P]),
+    "jn_star": (ctypes.c_int, [_P, ctypes.POINTER(Table), ctypes.POINTER(Table), ctypes.POINTER(Table),
+                               ctypes.POINTER(_P), ctypes.c_uint64, ctypes.POINTER(ctypes.c_uint64)]),
+    "jn_star_count": (ctypes.c_int, [_P, ctypes.POINTER(Table), ctypes.POINTER(Table), ctypes.POINTER(Table),
+                                     ctypes.POINTER(ctypes.c_uint64)]),
+    "jn_free_triples": (None, [_P, _P]),
     "jn_batch_count": (ctypes.c_int, [_P, ctypes.c_int32, ctypes.POINTER(Join), _P, _P]),
     "jn_autotune": (ctypes.c_int, [_P, ctypes.c_int32, ctypes.POINTER(Table), ctypes.POINTER(Table),
                                    ctypes.POINTER(Pred), ctypes.POINTER(Tuning)]),
@@ -299,18 +304,24 @@ def pred(op_a=JN_EQ, op_k=JN_ANY, band=-1) -> Pred:
 
 
 class _DeviceResult:
-    """Library-allocated pairs exposed through __cuda_array_interface__."""
+    """Library-allocated pairs (width 2) or star-join triples (width 3)
+    exposed through __cuda_array_interface__."""
 
-    def __init__(self, ctx, ptr, n):
+    def __init__(self, ctx, ptr, n, width=2):
         self._ctx = ctx
         self._ptr = ptr
-        self.__cuda_array_interface__ = {"shape": (n, 2), "typestr": "<i4", "data": (ptr, False),
+        self._width = width
+        self.__cuda_array_interface__ = {"shape": (n, width), "typestr": "<i4", "data": (ptr, False),
                                          "version": 3, "strides": None, "stream": None}
 
     def __del__(self):
         lib = load()
         ctx = self._ctx
-        lib.jn_free(None if ctx.closed else ctx.handle, _P(self._ptr))
+        h = None if ctx.closed else ctx.handle
+        if self._width == 3:
+            lib.jn_free_triples(h, _P(self._ptr))
+        else:
+            lib.jn_free(h, _P(self._ptr))
 
 
 def _result(ctx, out_ptr, n, user_out):
@@ -360,6 +371,35 @@ def jn_nested_loop(ctx: Context, R: TableRef, S: TableRef, pr: Pred = None, out=
     return _emit(ctx, load().jn_nested_loop,
                  (ctypes.byref(R.t), ctypes.byref(S.t), ctypes.byref(pr) if pr is not None else None),
                  out)
+
+
+def jn_star(ctx: Context, R: TableRef, S1: TableRef, S2: TableRef, out=None):
+    """Star join: R (key = fk1, key2 = fk2) with S1 on fk1 and S2 on fk2;
+    an (n, 3) int32 tensor of (R, S1, S2) payloads."""
+    n = ctypes.c_uint64()
+    if out is None:
+        p, cap = _P(None), 0
+    else:
+        if out.dtype != torch.int32 or out.dim() != 2 or out.shape[1] != 3 or not out.is_contiguous():
+            raise TypeError("out must be a contiguous (cap, 3) int32 tensor")
+        p, cap = _P(out.data_ptr()), out.shape[0]
+    st = load().jn_star(ctx.handle, ctypes.byref(R.t), ctypes.byref(S1.t), ctypes.byref(S2.t), ctypes.byref(p),
+                        cap, ctypes.byref(n))
+    _check(ctx, st, required=int(n.value) if st in (JN_ERR_CAPACITY, JN_ERR_OOM) else None)
+    m = int(n.value)
+    if out is not None:
+        return out[:m]
+    if m == 0 or not p.value:
+        return torch.empty((0, 3), dtype=torch.int32, device="cuda:%d" % ctx.device)
+    return torch.as_tensor(_DeviceResult(ctx, p.value, m, 3), device="cuda:%d" % ctx.device)
+
+
+def jn_star_count(ctx: Context, R: TableRef, S1: TableRef, S2: TableRef) -> int:
+    c = ctypes.c_uint64()
+    st = load().jn_star_count(ctx.handle, ctypes.byref(R.t), ctypes.byref(S1.t), ctypes.byref(S2.t),
+                              ctypes.byref(c))
+    _check(ctx, st)
+    return int(c.value)
 
 
 def jn_hash(ctx: Context, R: TableRef, S: TableRef, out=None):

@@ -48,6 +48,8 @@ def test_library_loads_and_answers_without_gpu(lib_path):
     assert lib.jn_selftest_wait(None, 1, 0, None) == jn.JN_ERR_INVALID
     assert lib.jn_autotune(None, jn.JN_ALGO_SORT, None, None, None, None) == jn.JN_ERR_INVALID
     assert lib.jn_server_wait_any(None, None, None, 0) == jn.JN_ERR_INVALID
+    assert lib.jn_star(None, None, None, None, None, 0, None) == jn.JN_ERR_INVALID
+    assert lib.jn_star_count(None, None, None, None, None) == jn.JN_ERR_INVALID
     # a server configuration is checked before any device is touched: the
     # small-request lane must leave at least one slot for large requests
     srv = ctypes.c_void_p()

@@ -765,3 +765,107 @@ def test_sort_merge_equals_hash_join_zipf(ctx):
     assert a.shape[0] == O.hash_join(r.numpy(), s.numpy(), count_only=True)
     with pytest.raises(jn.JoinError):
         jn.jn_count(ctx, jn.JN_ALGO_SORT, R, S, jn.pred(jn.JN_LT))
+
+
+# ------------------------------------------------------------------ star join
+
+def star_tables(nr, n1, n2, d1, d2, seed, dt, zipf=None):
+    if zipf is None:
+        f1, f2 = keys(nr, 0, d1, seed, 0, dt), keys(nr, 0, d2, seed, 1, dt)
+        k1, k2 = keys(n1, 0, d1, seed, 2, dt), keys(n2, 0, d2, seed, 3, dt)
+    else:
+        f1, f2 = skewed(nr, d1, zipf, seed, 0, dt), skewed(nr, d2, zipf, seed, 1, dt)
+        k1, k2 = skewed(n1, d1, zipf, seed, 2, dt), skewed(n2, d2, zipf, seed, 3, dt)
+    rp = datagen.uniform_int(nr, I32_MIN, I32_MAX, seed, 4)
+    p1 = datagen.uniform_int(n1, I32_MIN, I32_MAX, seed, 5)
+    p2 = datagen.uniform_int(n2, I32_MIN, I32_MAX, seed, 6)
+    return f1, f2, k1, k2, rp, p1, p2
+
+
+def canon3(t):
+    t = t.cpu().numpy() if isinstance(t, torch.Tensor) else t
+    if t.shape[0] == 0:
+        return t.reshape(0, 3)
+    return t[np.lexsort((t[:, 2], t[:, 1], t[:, 0]))]
+
+
+@pytest.mark.parametrize("dt", [torch.int32, torch.int64])
+@pytest.mark.parametrize("zipf", [None, 1.0])
+def test_star_join_matches_oracle(ctx, dt, zipf):
+    # duplicate keys on every side (several S1 and S2 rows per key), several
+    # partitions and tiles; Zipf keys send the frequent ones down the heavy path
+    # (smaller tables there: a frequent key multiplies through both joins)
+    sizes = (20000, 3000, 4000) if zipf is None else (5000, 800, 1000)
+    f1, f2, k1, k2, rp, p1, p2 = star_tables(*sizes, 1000, 1500, 71, dt, zipf)
+    exp = canon3(O.star_join(f1.numpy(), f2.numpy(), k1.numpy(), k2.numpy(), rp.numpy(), p1.numpy(), p2.numpy()))
+    R = jn.table(f1.to(DEV), f2.to(DEV), rp.to(DEV))
+    S1 = jn.table(k1.to(DEV), payload=p1.to(DEV))
+    S2 = jn.table(k2.to(DEV), payload=p2.to(DEV))
+    got = jn.jn_star(ctx, R, S1, S2)
+    assert got.shape == (exp.shape[0], 3)
+    assert np.array_equal(canon3(got), exp)
+    assert jn.jn_star_count(ctx, R, S1, S2) == exp.shape[0]
+
+
+def test_star_join_edges_and_buffers(ctx):
+    f1, f2, k1, k2, rp, p1, p2 = star_tables(3000, 500, 700, 300, 200, 72, torch.int32)
+    R = jn.table(f1.to(DEV), f2.to(DEV))  # payload = row index
+    S1, S2 = jn.table(k1.to(DEV)), jn.table(k2.to(DEV), payload=p2.to(DEV))
+    exp = canon3(O.star_join(f1.numpy(), f2.numpy(), k1.numpy(), k2.numpy(), s2pay=p2.numpy()))
+    m = exp.shape[0]
+    assert m > 0
+    assert np.array_equal(canon3(jn.jn_star(ctx, R, S1, S2)), exp)
+    # caller buffers: device exact, host, too small (nothing written, count returned)
+    dev = torch.full((m, 3), -5, dtype=torch.int32, device=DEV)
+    assert np.array_equal(canon3(jn.jn_star(ctx, R, S1, S2, out=dev)), exp)
+    host = torch.full((m + 3, 3), -5, dtype=torch.int32)
+    got = jn.jn_star(ctx, R, S1, S2, out=host)
+    assert np.array_equal(canon3(got), exp) and (host[m:] == -5).all()
+    small = torch.full((m - 1, 3), -5, dtype=torch.int32, device=DEV)
+    with pytest.raises(jn.JoinError) as e:
+        jn.jn_star(ctx, R, S1, S2, out=small)
+    assert e.value.status == jn.JN_ERR_CAPACITY and e.value.required == m
+    assert (small == -5).all()
+    # empty tables and no matches give nothing
+    empty = torch.empty(0, dtype=torch.int32, device=DEV)
+    assert jn.jn_star(ctx, jn.table(empty, empty), S1, S2).shape == (0, 3)
+    assert jn.jn_star(ctx, R, jn.table(empty), S2).shape == (0, 3)
+    assert jn.jn_star(ctx, R, S1, jn.table(empty)).shape == (0, 3)
+    far = (k2 + 10 ** 6).to(DEV)
+    assert jn.jn_star_count(ctx, R, S1, jn.table(far)) == 0
+    # R's second column and payloads must be on the device
+    with pytest.raises(jn.JoinError) as e:
+        jn.jn_star(ctx, jn.table(f1.to(DEV), f2.pin_memory()), S1, S2)
+    assert e.value.status == jn.JN_ERR_INVALID
+
+
+@pytest.mark.parametrize("dt", [torch.int32, torch.int64])
+def test_star_join_unique_dimensions_closed_form(ctx, dt):
+    # a fact table of 4M rows against two dimension tables with unique keys
+    # (the usual star schema): each fact row gives at most one triple, the
+    # one whose dimension rows hold its keys, so the whole result is known in
+    # closed form without the oracle
+    nr, n1, n2 = 4 << 20, 1 << 18, 3 << 16
+    gen = torch.Generator().manual_seed(73)
+    d1 = torch.randperm(1 << 20, generator=gen)[:n1].to(dt) * 3 + 7    # unique S1 keys
+    d2 = torch.randperm(1 << 19, generator=gen)[:n2].to(dt) * 5 - 11   # unique S2 keys
+    f1 = torch.cat([d1, d1 + 1])[torch.randint(0, 2 * n1, (nr,), generator=gen)]  # half miss S1
+    f2 = torch.cat([d2, d2 + 2])[torch.randint(0, 2 * n2, (nr,), generator=gen)]  # half miss S2
+    R = jn.table(f1.to(DEV), f2.to(DEV))
+    S1 = jn.table(d1.to(DEV))
+    S2 = jn.table(d2.to(DEV))
+    got = canon3(jn.jn_star(ctx, R, S1, S2))
+
+    def lookup(dim, fk):  # row of dim holding each fk, and whether one does
+        order = np.argsort(dim)
+        srt = dim[order]
+        i = np.minimum(np.searchsorted(srt, fk), len(srt) - 1)
+        return order[i], srt[i] == fk
+
+    r1, ok1 = lookup(d1.numpy(), f1.numpy())
+    r2, ok2 = lookup(d2.numpy(), f2.numpy())
+    keep = ok1 & ok2
+    exp = np.stack([np.nonzero(keep)[0], r1[keep], r2[keep]], axis=1).astype(np.int32)
+    assert 0 < exp.shape[0] < nr
+    assert got.shape == exp.shape
+    assert np.array_equal(got, canon3(exp))
