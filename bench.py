@@ -15,7 +15,7 @@ tuples/s ("join tuples/s in+out"), with the inputs already in device memory.
 copies the host columns in and the pairs out inside the timed region.
 
 Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
-                       [--workload hash|hash_int64|sortmerge|band|nlj|nlj_band|batch|serve]
+                       [--workload hash|hash_int64|sortmerge|band|nlj|nlj_band|batch|serve|star]
                        [--theta T] [--sweep]
 Under torchrun (N > 1) every rank runs its own replica of the workload
 (the join does not shard without a collective); value sums all ranks.
@@ -471,6 +471,77 @@ def kernel_table(stats, steps, abytes):
     return kern, roof
 
 
+def star_main(args, world, rank, local, dev, stream, jn, ctx):
+    """A step is one jn_star call: a 64M-row fact table with two foreign keys
+    against two 1M-row dimension tables of unique keys (every fact key found),
+    so the result is one triple per fact row."""
+    from paper_1904_11201_gb300 import datagen as D
+    nf, nd = ((1 << 22), (1 << 16)) if args.small else ((1 << 26), (1 << 20))
+    gen = torch.Generator(device="cpu").manual_seed(0)
+    d1 = (torch.randperm(1 << 24, generator=gen)[:nd].to(torch.int32) * 7 + 1).to(dev)
+    d2 = (torch.randperm(1 << 24, generator=gen)[:nd].to(torch.int32) * 5 + 3).to(dev)
+    f1 = d1[D.uniform_int(nf, 0, nd, 0, 0, dev, torch.int64)]
+    f2 = d2[D.uniform_int(nf, 0, nd, 0, 1, dev, torch.int64)]
+    R = jn.table(f1, f2, D.row_ids(nf, dev))
+    S1 = jn.table(d1, payload=D.row_ids(nd, dev))
+    S2 = jn.table(d2, payload=D.row_ids(nd, dev))
+    torch.cuda.synchronize()
+    clk = ClockSampler(local)
+    clk.start()
+    for _ in range(args.warmup):
+        out = jn.jn_star(ctx, R, S1, S2)
+        m = out.shape[0]
+        del out
+    l0 = ctx.launch_count()
+    barrier(world)
+    torch.cuda.synchronize()
+    tw0 = time.time()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(args.steps):
+        out = jn.jn_star(ctx, R, S1, S2)
+        del out
+    e1.record(stream)
+    torch.cuda.synchronize()
+    clk.mark(tw0, time.time())
+    barrier(world)
+    clocks = clk.stop()
+    launches = ctx.launch_count() - l0
+    ms = max_over_ranks(e0.elapsed_time(e1) / args.steps, world, dev)
+    ctx.reset_stats()
+    ctx.set_profiling(True)
+    out = jn.jn_star(ctx, R, S1, S2)
+    del out
+    torch.cuda.synchronize()
+    stats = ctx.kernel_stats()
+    ctx.set_profiling(False)
+    kern, _ = kernel_table(stats, 1, {})
+    pk, pk_kind = peaks()
+    # read the three tables once (fact: two keys and a payload; dimensions: key
+    # and payload) and write 12 bytes per triple
+    floor = 12 * nf + 8 * 2 * nd + 12 * m
+    units = nf + 2 * nd + m
+    if rank == 0:
+        line = {"metric": "join tuples/s in+out", "value": world * units / (ms * 1e-3), "unit": "tuples/s",
+                "n_gpus": world, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
+                "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "int32",
+                "data": "synthetic",
+                "config": {"workload": "star join: %dM-row fact table (fk1, fk2, payload) x two %dK-row "
+                                       "dimension tables of unique keys, every fact key found"
+                                       % (nf >> 20, nd >> 10),
+                           "fact_rows": nf, "dimension_rows": nd, "result_triples": m,
+                           "algo": "jn_star: two hash joins (left-deep), fk2 gathered between them",
+                           "l2": "inputs larger than L2 (no flush needed)",
+                           "parallelism": "replicas" if world > 1 else "1 GPU"},
+                "join_floor": {"bytes": floor, "definition": "12*|R| + 8*(|S1|+|S2|) + 12*M",
+                               "frac_of_hbm_peak": floor / (ms * 1e-3) / (pk.get("hbm_gbs", 6800.0) * 1e9)},
+                "roofline": None, "cpu_baseline": None, "e2e": None,
+                "e2e_note": "tables stay in device memory", "clocks": clocks, "gpu_launches": launches,
+                "kernels": kern}
+        print(json.dumps(line), flush=True)
+
+
 # --------------------------------------------------------------- serving --
 
 def make_pool(dev, n_i32, n_i64, lo, hi, seed=5):
@@ -896,8 +967,9 @@ def main():
     if args.prefilter != -1 or args.radix_bits or args.theta_groups or args.table_rows:
         ctx.set_tuning(prefilter=args.prefilter, radix_bits=args.radix_bits, theta_groups=args.theta_groups,
                        table_rows=args.table_rows)
-    if args.workload in ("batch", "serve"):
-        (batch_main if args.workload == "batch" else serve_main)(args, world, rank, local, dev, stream, jn, ctx)
+    if args.workload in ("batch", "serve", "star"):
+        {"batch": batch_main, "serve": serve_main, "star": star_main}[args.workload](
+            args, world, rank, local, dev, stream, jn, ctx)
         ctx.close()
         if world > 1:
             import torch.distributed as dist

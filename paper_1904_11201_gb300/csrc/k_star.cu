@@ -14,26 +14,58 @@
 
 namespace jnx {
 
-// t1key[i] = fk2[J1[i].r]: the second join column of each first-join pair's R row.
+constexpr int ST_ILP = 4;  // gathers in flight per thread
+
+// t1key[i] = fk2[J1[i].r]: the second join column of each first-join pair's R
+// row.  A block covers 256 * ST_ILP consecutive pairs; each thread issues its
+// ST_ILP random reads of fk2 before it stores any (the reads are independent).
 template <typename K>
 __global__ void __launch_bounds__(256)
 k_star_keys(const jn_pair* __restrict__ j1, uint64_t m1, const K* __restrict__ fk2, K* __restrict__ t1key) {
-    for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < m1; i += (uint64_t)gridDim.x * blockDim.x)
-        t1key[i] = fk2[j1[i].r];
+    const uint64_t base = (uint64_t)blockIdx.x * (256 * ST_ILP) + threadIdx.x;
+    int32_t r[ST_ILP];
+#pragma unroll
+    for (int u = 0; u < ST_ILP; u++) {
+        const uint64_t i = base + (uint64_t)u * 256;
+        r[u] = i < m1 ? j1[i].r : -1;
+    }
+    K v[ST_ILP];
+#pragma unroll
+    for (int u = 0; u < ST_ILP; u++) v[u] = r[u] >= 0 ? fk2[r[u]] : K(0);
+#pragma unroll
+    for (int u = 0; u < ST_ILP; u++) {
+        const uint64_t i = base + (uint64_t)u * 256;
+        if (i < m1) t1key[i] = v[u];
+    }
 }
 
-// out[i] = (R payload of J1[J2[i].r] (its row index when rpay is NULL), J1[J2[i].r].s, J2[i].s).
+// out[i] = (R payload of J1[J2[i].r] (its row index when rpay is NULL),
+// J1[J2[i].r].s, J2[i].s), with ST_ILP independent gather chains per thread.
 __global__ void __launch_bounds__(256)
 k_star_emit(const jn_pair* __restrict__ j1, const jn_pair* __restrict__ j2, uint64_t m2,
             const int32_t* __restrict__ rpay, jn_triple* __restrict__ out) {
-    for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < m2; i += (uint64_t)gridDim.x * blockDim.x) {
-        const jn_pair b = j2[i];
-        const jn_pair a = j1[b.r];
-        jn_triple t;
-        t.r = rpay ? rpay[a.r] : a.r;
-        t.s1 = a.s;
-        t.s2 = b.s;
-        out[i] = t;
+    const uint64_t base = (uint64_t)blockIdx.x * (256 * ST_ILP) + threadIdx.x;
+    jn_pair b[ST_ILP], a[ST_ILP];
+#pragma unroll
+    for (int u = 0; u < ST_ILP; u++) {
+        const uint64_t i = base + (uint64_t)u * 256;
+        b[u] = i < m2 ? j2[i] : jn_pair{-1, 0};
+    }
+#pragma unroll
+    for (int u = 0; u < ST_ILP; u++) a[u] = b[u].r >= 0 ? j1[b[u].r] : jn_pair{-1, 0};
+    int32_t p[ST_ILP];
+#pragma unroll
+    for (int u = 0; u < ST_ILP; u++) p[u] = (rpay && a[u].r >= 0) ? rpay[a[u].r] : a[u].r;
+#pragma unroll
+    for (int u = 0; u < ST_ILP; u++) {
+        const uint64_t i = base + (uint64_t)u * 256;
+        if (i < m2) {
+            jn_triple t;
+            t.r = p[u];
+            t.s1 = a[u].s;
+            t.s2 = b[u].s;
+            out[i] = t;
+        }
     }
 }
 
@@ -50,11 +82,8 @@ struct Pairs {
     }
 };
 
-unsigned grid_for(jn_ctx* c, uint64_t n) {
-    const uint64_t blocks = (n + 255) / 256;
-    const uint64_t cap = (uint64_t)c->num_sms * 8;
-    return (unsigned)(blocks < cap ? blocks : cap);
-}
+// One block per 256 * ST_ILP elements.
+unsigned grid_for(uint64_t n) { return (unsigned)((n + 256 * ST_ILP - 1) / (256 * ST_ILP)); }
 
 template <typename K>
 jn_status star_typed(jn_ctx* c, const jn_table* R, const jn_table* S1, const jn_table* S2, jn_triple** out,
@@ -72,7 +101,7 @@ jn_status star_typed(jn_ctx* c, const jn_table* R, const jn_table* S1, const jn_
     K* t1key = nullptr;
     if (j1.n) {
         JN_TRY(s.get(&t1key, j1.n));
-        JN_TRY(launch(c, K_STAR, k_star_keys<K>, dim3(grid_for(c, j1.n)), dim3(256), 0, (const jn_pair*)j1.p,
+        JN_TRY(launch(c, K_STAR, k_star_keys<K>, dim3(grid_for(j1.n)), dim3(256), 0, (const jn_pair*)j1.p,
                       j1.n, (const K*)R->key2, t1key));
     }
     jn_table t1;
@@ -102,7 +131,7 @@ jn_status star_typed(jn_ctx* c, const jn_table* R, const jn_table* S1, const jn_
         copy_back = true;
     }
     if (m)
-        JN_TRY(launch(c, K_STAR, k_star_emit, dim3(grid_for(c, m)), dim3(256), 0, (const jn_pair*)j1.p,
+        JN_TRY(launch(c, K_STAR, k_star_emit, dim3(grid_for(m)), dim3(256), 0, (const jn_pair*)j1.p,
                       (const jn_pair*)j2.p, m, (const int32_t*)R->payload, dev));
     if (copy_back) JN_CUDA(c, cudaMemcpyAsync(user, dev, m * sizeof(jn_triple), cudaMemcpyDefault, c->stream));
     JN_CUDA(c, cudaStreamSynchronize(c->stream));
