@@ -124,10 +124,10 @@ typedef struct {
                               18 partition bits are needed                              */
     int32_t table_rows;    /* R rows per shared-memory table of the hash and sort-merge
                               joins (the "bucket" a work item holds): 0 = the key type's
-                              full table (4096 rows for int32 keys, 2048 for int64), or
-                              half of it; a value the join does not support makes it
-                              return JN_ERR_UNSUPPORTED. jn_set_tuning accepts 0, 1024,
-                              2048 and 4096                                             */
+                              full table (4096 rows for int32 keys, 2048 for int64),
+                              otherwise the full table when at least that size, else
+                              half of it (jn_run_info.table_rows reports the size
+                              used). jn_set_tuning accepts 0, 1024, 2048 and 4096     */
     int32_t reserved[4];
 } jn_tuning;
 

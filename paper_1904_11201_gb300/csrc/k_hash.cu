@@ -825,10 +825,10 @@ jn_status run_hash(jn_ctx* c, const Cols<K>& R, const Cols<K>& S, int mode, OutP
     const jn_tuning& tu = c->tune;
     // ---- parameters ----
     // R rows per shared-memory table: the full table or half of it (a smaller
-    // table doubles the partitions for the same rows per partition)
-    const int cap = tu.table_rows ? tu.table_rows : cap_of<K>();
-    if (cap != cap_of<K>() && cap != cap_of<K>() / 2)
-        return fail(c, JN_ERR_UNSUPPORTED, "table_rows must be 0, the key type's table size or half of it");
+    // table doubles the partitions for the same rows per partition); a size
+    // outside the key type's two is taken as the nearer one, so one context
+    // serves both key types
+    const int cap = tu.table_rows == 0 || tu.table_rows >= cap_of<K>() ? cap_of<K>() : cap_of<K>() / 2;
     bool heavy = tu.heavy >= 1 || (tu.heavy == -1 && nr + ns >= (1u << 20));
     const int64_t heavy_rows = tu.heavy >= 2 ? tu.heavy : cap_of<K>() / 4;  // rows that make a key heavy
     // which tables the pre-filter thins: bit 0 S (by R's keys), bit 1 R (by S's keys)
