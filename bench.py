@@ -134,8 +134,8 @@ def run_step(jn, ctx, w, R, S, out=None):
 # ------------------------------------------------------------ roofline --
 
 def algorithmic_bytes(kind, info, nr, ns, m, ksize):
-    """Algorithmic bytes per kernel for one step, as SURVEY 8(d) counts the
-    hash join: the partition step reads every input tuple once and writes
+    """Algorithmic bytes per kernel for one step, as the partitioned join's
+    floor counts them: the partition step reads every input tuple once and writes
     every surviving tuple once; the join reads the partitioned copy once and
     writes 8 bytes per pair.  Intermediate copies (a second partition pass,
     the region path's level-1 rows) are not algorithmic, so where a step is
@@ -143,7 +143,7 @@ def algorithmic_bytes(kind, info, nr, ns, m, ksize):
       two radix passes: the four scatter launches together make one pass;
       region path: level 1 reads the input, level 2 writes the partitioned copy.
     Kernels outside the floor (histograms, the pre-filter's key read, the count
-    pass, which 8(d) counts as overhead) get the bytes they must move at least."""
+    pass, which the floor counts as overhead) get the bytes they must move at least."""
     sr, ss = info["r_survivors"], info["s_survivors"]
     surv = sr + ss
     row = ksize + 4

@@ -9,7 +9,7 @@ import bench
 
 
 def test_hash_algorithmic_bytes():
-    # the partition step reads every input tuple once (8 B, int32)
+    # the floor: the partition step reads every input tuple once (8 B, int32)
     # and writes every surviving tuple once (8 B); the join reads the
     # partitioned copy once and writes 8 B per pair
     nr, ns, m = 1000, 3000, 777
@@ -17,7 +17,7 @@ def test_hash_algorithmic_bytes():
     ab = bench.algorithmic_bytes("hash", info, nr, ns, m, 4)
     surv = 600 + 2100
     assert ab["presence"] == 4 * (nr + ns)  # every key read once
-    # two radix passes: the scatter launches together make one 8(d) pass
+    # two radix passes: the scatter launches together make one partition step
     assert ab["scatter"] == 8 * (nr + ns) + 8 * surv
     # region path: level 1 reads the input, level 2 writes the partitioned copy
     assert ab["region1"] == 8 * (nr + ns)
@@ -27,7 +27,7 @@ def test_hash_algorithmic_bytes():
     assert ab["hash_emit"] == 8 * surv + 8 * (m - 7)
     assert ab["cross_emit"] == 8 * 7
     assert ab["sort_chunks"] == 16 * 600  # R survivors read and written sorted
-    # the whole-join floor of 8(d) is the partition step plus the emit pass
+    # the whole-join floor is the partition step plus the emit pass
     assert ab["scatter"] + ab["hash_emit"] + ab["cross_emit"] == 8 * (nr + ns) + 16 * surv + 8 * m
     ab8 = bench.algorithmic_bytes("hash", info, nr, ns, m, 8)
     assert ab8["presence"] == 8 * (nr + ns) and ab8["hash_count"] == 12 * surv
