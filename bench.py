@@ -713,9 +713,11 @@ def serve_main(args, world, rank, local, dev, stream, jn, ctx):
         by_class = {}
         for name, sel in (("small", lambda i: rows[i] < (1 << 18)), ("large", lambda i: rows[i] >= (1 << 18))):
             lc = sorted(lat[i] for i in ok if sel(i))
+            rc = sorted(run[i] for i in ok if sel(i))
             if lc:
-                by_class[name] = {"n": len(lc), "p50_ms": lc[len(lc) // 2],
-                                  "p99_ms": lc[min(len(lc) - 1, int(0.99 * len(lc)))]}
+                q = min(len(lc) - 1, int(0.99 * len(lc)))
+                by_class[name] = {"n": len(lc), "p50_ms": lc[len(lc) // 2], "p99_ms": lc[q],
+                                  "run_p50_ms": rc[len(rc) // 2], "run_p99_ms": rc[q]}
         return {"offered_req_s": rate, "achieved_req_s": len(ok) / wall, "wall_s": wall, "ok": len(ok),
                 "refused_oom": len(refused), "failed": count - len(ok) - len(refused),
                 "p50_ms": pct(0.5), "p99_ms": pct(0.99), "by_size": by_class,
