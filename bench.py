@@ -638,7 +638,7 @@ def serve_main(args, world, rank, local, dev, stream, jn, ctx):
     cap_rps = n_req / t_one
 
     srv = jn.Server(local, slots=args.serve_slots, coalesce_rows=1 << 18, max_batch=64,
-                    small_slots=args.serve_small_slots,
+                    small_slots=args.serve_small_slots, small_sms=args.serve_small_sms,
                     memory_budget=budget, graphs=False)
     handles = {i: srv.register(eq_t[i]) for i in resident}
 
@@ -705,6 +705,12 @@ def serve_main(args, world, rank, local, dev, stream, jn, ctx):
         ls = sorted(lat[i] for i in ok)
         pct = (lambda p: ls[min(len(ls) - 1, int(p * len(ls)))] if ls else None)
         refused = [i for i in range(count) if status[i] == jn.JN_ERR_OOM]
+        if args.verbose:
+            small_ok = sorted((i for i in ok if rows[i] < (1 << 18)), key=lambda i: -lat[i])[:5]
+            for i in small_ok:
+                q = reqs[i]
+                note("slowest small: %s %d x %d rows, band %d, latency %.2f ms, run %.2f ms, %d pairs"
+                     % (q["kind"], pool[q["r"]]["rows"], pool[q["s"]]["rows"], q["band"], lat[i], run[i], got_m[i]))
         rs = sorted(run[i] for i in ok)
         run_pct = (lambda p: rs[min(len(rs) - 1, int(p * len(rs)))] if rs else None)
         # slowdown: latency over the request's own run time (queueing it saw)
@@ -753,6 +759,7 @@ def serve_main(args, world, rank, local, dev, stream, jn, ctx):
                                        "2^28 ranks, half the requests on resident tables by handle"
                                        % (n_req, 10000, pool_hi(small)),
                            "pool_tables": len(pool), "slots": args.serve_slots, "small_slots": args.serve_small_slots,
+                           "small_sms": args.serve_small_sms,
                            "coalesce_rows": 1 << 18,
                            "memory_budget": budget, "resident_requests": sum(q["resident"] for q in reqs),
                            "l2": "tables up to 64M rows; no flush between requests",
@@ -947,6 +954,8 @@ def main():
     ap.add_argument("--serve-slots", type=int, default=4, help="serve workload: server worker slots")
     ap.add_argument("--serve-small-slots", type=int, default=1,
                     help="serve workload: slots that take only small requests (a lane for them)")
+    ap.add_argument("--serve-small-sms", type=int, default=16,
+                    help="serve workload: SMs the other slots' grids leave free for the small lane")
     ap.add_argument("--verbose", action="store_true", help="progress lines on stderr")
     args = ap.parse_args()
     world, rank, local = dist_setup(args)

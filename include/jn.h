@@ -128,7 +128,10 @@ typedef struct {
                               otherwise the full table when at least that size, else
                               half of it (jn_run_info.table_rows reports the size
                               used). jn_set_tuning accepts 0, 1024, 2048 and 4096     */
-    int32_t reserved[4];
+    int32_t sms;           /* SMs the context's persistent grids are sized for (0 = all;
+                              more than the device has = all).  Fewer leaves room on
+                              the device for another context's kernels              */
+    int32_t reserved[3];
 } jn_tuning;
 
 /* Per-kernel launch statistics (profiling mode). */
@@ -384,6 +387,10 @@ typedef struct {
                                 long (ms, >= 0) for a release, then is refused
                                 (JN_ERR_OOM): bounded, so a client that releases in
                                 submission order cannot deadlock the server          */
+    int32_t small_sms;       /* with small_slots > 0: SMs the other workers' grids
+                                leave free for the small-request lane
+                                (jn_tuning.sms), >= 0                                */
+    int32_t reserved;        /* must be 0                                           */
 } jn_server_config;
 
 typedef struct {

@@ -63,7 +63,8 @@ struct KernelStat {
 
 struct jn_ctx {
     int device = 0;
-    int num_sms = 0;
+    int num_sms = 0;     // SMs the grids are sized for (tuning `sms`, else all)
+    int device_sms = 0;  // SMs of the device
     size_t smem_optin = 0;
     cudaStream_t stream = nullptr;
     cudaMemPool_t pool = nullptr;  // the device's default pool (never destroyed)

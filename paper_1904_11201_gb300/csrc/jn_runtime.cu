@@ -359,7 +359,7 @@ jn_status jn_create(jn_ctx** out, int device, void* stream) {
     if (e == cudaSuccess) {
         cudaDeviceProp prop;
         e = cudaGetDeviceProperties(&prop, device);
-        c->num_sms = prop.multiProcessorCount;
+        c->num_sms = c->device_sms = prop.multiProcessorCount;
         c->smem_optin = prop.sharedMemPerBlockOptin;
     }
     if (e == cudaSuccess) {
@@ -421,15 +421,18 @@ jn_status jn_set_tuning(jn_ctx* c, const jn_tuning* t) {
     if (!c) return JN_ERR_INVALID;
     if (!t) {
         default_tuning(&c->tune);
+        c->num_sms = c->device_sms;
         return JN_OK;
     }
     if (t->prefilter < -1 || t->prefilter > 3 || t->radix_bits < 0 || t->radix_bits > 20 || t->radix_bits1 < 0 || t->radix_bits1 > 10 ||
         t->filter_bits < 0 || t->filter_bits > 30 || t->theta_groups < 0 || t->theta_groups > 10 ||
         t->nlj_tile_r < 0 || (t->nlj_tile_r % 256) != 0 || t->nlj_tile_r > 4096 || t->part_rows < 0 ||
         t->host_io < 0 || t->host_io > 3 || t->hash_path < 0 || t->hash_path > 2 ||
-        (t->table_rows != 0 && t->table_rows != 1024 && t->table_rows != 2048 && t->table_rows != 4096))
+        (t->table_rows != 0 && t->table_rows != 1024 && t->table_rows != 2048 && t->table_rows != 4096) ||
+        t->sms < 0)
         return fail(c, JN_ERR_INVALID, "tuning value out of range");
     c->tune = *t;
+    c->num_sms = t->sms > 0 && t->sms < c->device_sms ? t->sms : c->device_sms;
     return JN_OK;
 }
 

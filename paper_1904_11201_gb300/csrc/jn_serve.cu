@@ -345,6 +345,14 @@ void worker_main(jn_server* s, int slot) {
     jn_tuning t;
     jn_get_tuning(ctx, &t);
     t.graphs = s->cfg.graphs ? 1 : 0;
+    if (slot >= s->cfg.small_slots && s->cfg.small_slots > 0 && s->cfg.small_sms > 0) {
+        // the large-request workers' persistent grids leave small_sms SMs'
+        // worth of room, where the small lane's kernels start at once
+        // instead of waiting for a whole large kernel to end
+        int sms = 0;
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, s->device);
+        t.sms = sms > s->cfg.small_sms ? sms - s->cfg.small_sms : 1;
+    }
     jn_set_tuning(ctx, &t);
     Admit adm;
     adm.s = s;
@@ -397,7 +405,7 @@ extern "C" {
 
 jn_status jn_server_create(jn_server** out, int device, const jn_server_config* cfg) {
     if (!out || !cfg || cfg->slots < 1 || cfg->slots > 16 || cfg->max_batch < 1 || cfg->small_slots < 0 ||
-        cfg->small_slots >= cfg->slots || cfg->hold_wait_ms < 0)
+        cfg->small_slots >= cfg->slots || cfg->hold_wait_ms < 0 || cfg->small_sms < 0 || cfg->reserved != 0)
         return JN_ERR_INVALID;
     int ndev = 0;
     if (cudaGetDeviceCount(&ndev) != cudaSuccess || device < 0 || device >= ndev) {

@@ -46,8 +46,10 @@ jn_status jn_autotune(jn_ctx* c, int32_t algo, const jn_table* R, const jn_table
         std::lock_guard<std::mutex> g(g_mu);
         auto it = g_cache.find(key);
         if (it != g_cache.end()) {
-            c->tune = it->second;
-            if (best) *best = it->second;
+            jn_tuning t = it->second;
+            t.sms = c->tune.sms;  // the SM budget is the context's own, not a tuned knob
+            c->tune = t;
+            if (best) *best = t;
             return JN_OK;
         }
     }
@@ -161,8 +163,10 @@ jn_status jn_autotune_batch(jn_ctx* c, int32_t count, const jn_join* joins, jn_t
         std::lock_guard<std::mutex> g(g_mu);
         auto it = g_cache.find(key);
         if (it != g_cache.end()) {
-            c->tune = it->second;
-            if (best) *best = it->second;
+            jn_tuning t = it->second;
+            t.sms = c->tune.sms;  // the SM budget is the context's own, not a tuned knob
+            c->tune = t;
+            if (best) *best = t;
             return JN_OK;
         }
     }

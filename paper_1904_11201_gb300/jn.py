@@ -50,7 +50,7 @@ class Tuning(ctypes.Structure):
                 ("nlj_tile_r", ctypes.c_int32), ("graphs", ctypes.c_int32),
                 ("part_rows", ctypes.c_int32), ("host_io", ctypes.c_int32),
                 ("hash_path", ctypes.c_int32), ("table_rows", ctypes.c_int32),
-                ("reserved", ctypes.c_int32 * 4)]
+                ("sms", ctypes.c_int32), ("reserved", ctypes.c_int32 * 3)]
 
 
 class Join(ctypes.Structure):
@@ -61,7 +61,7 @@ class Join(ctypes.Structure):
 class ServerConfig(ctypes.Structure):
     _fields_ = [("slots", ctypes.c_int32), ("coalesce_rows", ctypes.c_int32), ("max_batch", ctypes.c_int32),
                 ("graphs", ctypes.c_int32), ("memory_budget", ctypes.c_uint64), ("small_slots", ctypes.c_int32),
-                ("hold_wait_ms", ctypes.c_int32)]
+                ("hold_wait_ms", ctypes.c_int32), ("small_sms", ctypes.c_int32), ("reserved", ctypes.c_int32)]
 
 
 class Request(ctypes.Structure):
@@ -451,10 +451,10 @@ class Server:
     """jn_server: a request loop over the library (see jn.h, serving)."""
 
     def __init__(self, device=0, slots=4, coalesce_rows=1 << 18, max_batch=64, memory_budget=64 << 30,
-                 graphs=False, small_slots=0, hold_wait_ms=2000):
+                 graphs=False, small_slots=0, hold_wait_ms=2000, small_sms=0):
         lib = load()
         cfg = ServerConfig(slots, coalesce_rows, max_batch, 1 if graphs else 0, memory_budget, small_slots,
-                           hold_wait_ms)
+                           hold_wait_ms, small_sms, 0)
         h = _P()
         st = lib.jn_server_create(ctypes.byref(h), device, ctypes.byref(cfg))
         if st != JN_OK:

@@ -54,7 +54,7 @@ def test_library_loads_and_answers_without_gpu(lib_path):
     # small-request lane must leave at least one slot for large requests
     srv = ctypes.c_void_p()
     for slots, small, hold in ((4, 4, 0), (4, -1, 0), (1, 1, 0), (2, 0, -1)):
-        cfg = jn.ServerConfig(slots, 1 << 18, 8, 0, 1 << 30, small, hold)
+        cfg = jn.ServerConfig(slots, 1 << 18, 8, 0, 1 << 30, small, hold, 0, 0)
         assert lib.jn_server_create(ctypes.byref(srv), 0, ctypes.byref(cfg)) == jn.JN_ERR_INVALID
     h = ctypes.c_void_p()
     st = lib.jn_create(ctypes.byref(h), 0, None)

@@ -185,6 +185,25 @@ def test_table_rows_skewed_int64_and_sort_merge(ctx, dt, half):
             assert got.shape[0] == cnt and O.checksum_pairs(got.cpu().numpy()) == chk
 
 
+@pytest.mark.parametrize("sms", [1, 37, 100000])
+def test_sm_budget_never_changes_results(ctx, sms):
+    # grids sized for fewer SMs (or more than the device has) do the same work
+    r = skewed(60000, 1 << 14, 0.8, 81, 0)
+    s = skewed(90000, 1 << 14, 0.8, 81, 1)
+    ra, rk = datagen.band_columns(5000, 14, seed=81, stream=2)
+    sa, sk = datagen.band_columns(9000, 14, seed=81, stream=3)
+    ctx.set_tuning(sms=sms)
+    try:
+        assert ctx.tuning()["sms"] == sms
+        got = jn.jn_hash(ctx, jn.table(r.to(DEV)), jn.table(s.to(DEV)))
+        gotb = jn.jn_theta(ctx, jn.table(ra.to(DEV), rk.to(DEV)), jn.table(sa.to(DEV), sk.to(DEV)), jn.JN_LT, 9)
+    finally:
+        ctx.set_tuning(sms=0)
+    assert np.array_equal(canon(got), canon(O.hash_join(r.numpy(), s.numpy())))
+    assert np.array_equal(canon(gotb), canon(O.band_join_sorted(ra.numpy(), rk.numpy(), sa.numpy(), sk.numpy(),
+                                                                O.LT, 9)))
+
+
 def test_table_rows_rejected_or_taken_as_the_nearer_size(ctx):
     # jn_set_tuning takes 0, 1024, 2048 and 4096; a join takes a size outside
     # its key type's two (full, half) as the nearer one, so one context tuned

@@ -147,12 +147,13 @@ def test_held_results_refuse_after_a_bounded_wait(hold_ms):
         srv.close()
 
 
-@pytest.mark.parametrize("small_slots", [0, 1, 2])
-def test_wait_any_returns_completions_once(small_slots):
-    # with a small-request lane of 1 or 2 of the 3 slots, small and large
-    # requests both complete, each exactly once
+@pytest.mark.parametrize("small_slots,small_sms", [(0, 0), (1, 0), (2, 0), (1, 24)])
+def test_wait_any_returns_completions_once(small_slots, small_sms):
+    # with a small-request lane of 1 or 2 of the 3 slots (and the other
+    # slots' grids leaving it SMs), small and large requests both complete,
+    # each exactly once
     srv = jn.Server(0, slots=3, coalesce_rows=1 << 12, max_batch=8, memory_budget=1 << 30,
-                    small_slots=small_slots)
+                    small_slots=small_slots, small_sms=small_sms)
     try:
         tabs = []
         for i in range(12):
