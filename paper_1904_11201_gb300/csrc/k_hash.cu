@@ -45,7 +45,7 @@ constexpr int HJ_T = JN_HJ_T;        // threads per join block
 constexpr int HJ_CAP = JN_HJ_CAP;    // R rows per shared-memory table (int32 keys)
 constexpr int HJ_SCH = JN_HJ_SCH;    // S rows per staged chunk
 #ifndef JN_HJ_PU
-#define JN_HJ_PU 4
+#define JN_HJ_PU 3  // a 1536-row chunk is three rounds of 512 threads
 #endif
 constexpr int HJ_PU = JN_HJ_PU;      // S rows a thread probes per round
 
