@@ -765,6 +765,8 @@ static jn_status run_theta_t(jn_ctx* c, const Cols<K>& R, const Cols<K>& S, int 
         JN_TRY(s.get(&rec.sdesc, nitems));
         rec.any_wide = reinterpret_cast<unsigned int*>(d_small + 2);
         JN_TRY(zero(c, d_small + 2, 8));
+        // the gather reads the saved payloads as 16-byte words
+        if ((uintptr_t)rec.pay & 15) rec = ThetaRec{nullptr, nullptr, nullptr, nullptr};
     }
     if (nitems) {
         auto kc = pick(cm);
