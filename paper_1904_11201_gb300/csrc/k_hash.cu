@@ -47,7 +47,7 @@ constexpr int HJ_SCH = JN_HJ_SCH;    // S rows per staged chunk
 #ifndef JN_HJ_PU
 #define JN_HJ_PU 3  // a 1536-row chunk is three rounds of 512 threads
 #endif
-constexpr int HJ_PU = JN_HJ_PU;      // S rows a thread probes per round
+constexpr int HJ_PU = JN_HJ_PU;      // S rows a thread probes per round in the emit pass
 
 #ifndef JN_SLICE_PAIRS
 #define JN_SLICE_PAIRS (1ull << 24)  // host outputs of at least this many pairs are copied back in slices
@@ -177,7 +177,10 @@ __device__ __forceinline__ uint32_t oa_slot(uint32_t h, int bits, int ts) {
 //                 lookup however many rows share the key.
 // The partitioned rows are library scratch, 16-byte aligned and padded by
 // HJ_PAD rows, so every widened copy stays inside its allocation.
-template <typename K, int MODE, bool MERGE = false, int CAP = cap_of<K>()>
+// PU: S rows a thread probes per round.  The emit pass overlaps HJ_PU rows'
+// lookups and reserves their output once; the count pass, with no output to
+// reserve, measured fastest with one.
+template <typename K, int MODE, bool MERGE = false, int CAP = cap_of<K>(), int PU = (MODE == MODE_EMIT ? HJ_PU : 1)>
 __global__ void __launch_bounds__(HJ_T, (CAP < cap_of<K>() && MODE != MODE_EMIT) ? 3 : JN_HJ_MINB)
 k_hash_join(const Row<K, false>* __restrict__ rrows, const Row<K, false>* __restrict__ srows,
             const Item* __restrict__ items, const uint64_t* __restrict__ nitems_p, int bits,
@@ -436,15 +439,15 @@ k_hash_join(const Row<K, false>* __restrict__ rrows, const Row<K, false>* __rest
             const int sn = min(HJ_SCH, d.sn - sc * HJ_SCH);
             const R* srow = reinterpret_cast<const R*>((b ? g_s1 : g_s0) + span_off<R>(sbeg));
             const int rounds = (sn + HJ_T - 1) / HJ_T;
-            // HJ_PU S rows per thread per round: their lookups and warp scans
+            // PU S rows per thread per round: their lookups and warp scans
             // overlap and one cursor reservation serves them all, while each
             // row's pairs still go out as one coalesced run per warp
-            for (int r = 0; r < rounds; r += HJ_PU) {
-                R x[HJ_PU];
-                uint32_t m[HJ_PU], beg[HJ_PU];
-                unsigned long long fs[HJ_PU];
+            for (int r = 0; r < rounds; r += PU) {
+                R x[PU];
+                uint32_t m[PU], beg[PU];
+                unsigned long long fs[PU];
 #pragma unroll
-                for (int u = 0; u < HJ_PU; u++) {
+                for (int u = 0; u < PU; u++) {
                     const int j = (r + u) * HJ_T + threadIdx.x;
                     x[u].key = 0;
                     x[u].pay = 0;
@@ -454,7 +457,7 @@ k_hash_join(const Row<K, false>* __restrict__ rrows, const Row<K, false>* __rest
                     if (j < sn) x[u] = srow[j];
                 }
 #pragma unroll
-                for (int u = 0; u < HJ_PU; u++) {
+                for (int u = 0; u < PU; u++) {
                     const int j = (r + u) * HJ_T + threadIdx.x;
                     if (j >= sn) continue;
                     if (MODE == MODE_EMIT) {
@@ -493,9 +496,9 @@ k_hash_join(const Row<K, false>* __restrict__ rrows, const Row<K, false>* __rest
                     }
                 }
                 if (MODE == MODE_EMIT) {
-                    uint32_t incl[HJ_PU], wt[HJ_PU], wsum = 0;
+                    uint32_t incl[PU], wt[PU], wsum = 0;
 #pragma unroll
-                    for (int u = 0; u < HJ_PU; u++) {
+                    for (int u = 0; u < PU; u++) {
                         incl[u] = warp_incl_scan(m[u]);
                         wt[u] = __shfl_sync(0xffffffffu, incl[u], 31);
                         wsum += wt[u];
@@ -504,7 +507,7 @@ k_hash_join(const Row<K, false>* __restrict__ rrows, const Row<K, false>* __rest
                     if (lane == 0 && wsum) base = atomicAdd(&s_cursor, wsum);
                     base = __shfl_sync(0xffffffffu, base, 0);
 #pragma unroll
-                    for (int u = 0; u < HJ_PU; u++) {
+                    for (int u = 0; u < PU; u++) {
                         const uint64_t o = ibase + base + (incl[u] - m[u]);
                         base += wt[u];
                         // a short run is written by its lane (the lanes' first pairs
@@ -524,7 +527,7 @@ k_hash_join(const Row<K, false>* __restrict__ rrows, const Row<K, false>* __rest
                     }
                 } else {
 #pragma unroll
-                    for (int u = 0; u < HJ_PU; u++) {
+                    for (int u = 0; u < PU; u++) {
                         acc += m[u];
                         if (MODE == MODE_AGG && m[u]) csum += fs[u] * chk_g(x[u].pay);
                     }
