@@ -262,10 +262,12 @@ k_hash_join(const Row<K, false>* __restrict__ rrows, const Row<K, false>* __rest
         Item dn;
         if (has_next) dn = items[itn];  // its R rows load once this item's R staging is free
         const int rn = d.rn;
-        // slots this item uses: twice its R rows (at most the table) -- a slot
-        // is picked by multiply-shift, so any count works; the skewed variant
-        // keeps the whole table
-        const int ts = (MERGE || MODE == MODE_EMIT) ? TS : min(TS, max(64, 2 * rn));
+        // slots this item uses: four times its R rows (at most the table) -- a
+        // slot is picked by multiply-shift, so any count works.  At a load of
+        // a quarter, a lookup that misses (most of them in a selective join)
+        // scans about 1.4 slots; at a half, 2.5.  The skewed variant keeps the
+        // whole table
+        const int ts = (MERGE || MODE == MODE_EMIT) ? TS : min(TS, max(64, 4 * rn));
         if (MODE == MODE_EMIT) {
             for (int i = threadIdx.x; i <= TS; i += HJ_T) {
                 e_tab[i].key = KMIN;
